@@ -80,6 +80,7 @@ static void rows_f32(const float a[6], float B[9]) {
 typedef struct {
   float cx, cy, cz;   /* camera-space centre */
   float R, R2;        /* effective radius and its square */
+  float tmin;         /* c_z - R: no point of the sphere is nearer */
   float key;          /* earliest possible intersection depth, +inf when culled */
   int visible;
   int x0, x1, y0, y1; /* inclusive pixel rectangle, valid when visible */
@@ -131,6 +132,7 @@ static void project_f32(const orc_params* P, const float* cam, const float B[9],
   o->visible = 0;
   o->x0 = o->x1 = o->y0 = o->y1 = -1;
   float key = o->cz - R;
+  o->tmin = key;
   float znear = (float)P->znear, zfar = (float)P->zfar;
   if (!(R > 0.0f) || !(key > znear) || !(key < zfar)) return;
   int x0, x1, y0, y1;
@@ -150,7 +152,10 @@ static float ray_coord_f32(int u, int n, float kappa) {
 }
 
 /* Hit predicate and front-hit depth in float32.  Returns 1 and writes t_h
- * when the ray (rx, ry, 1) meets the sphere in front of zfar. */
+ * when the ray (rx, ry, 1) meets the sphere in front of zfar.  The depth is
+ * never taken nearer than c_z - R, which holds exactly in real arithmetic;
+ * in float32 the clamp keeps every hit depth at or beyond the sphere's sort
+ * key, the property that depth-ordered early termination relies on. */
 static int hit_f32(const proj32* s, float rx, float ry, float zfar, float* t_out) {
   float ex = fmaf(s->cz, rx, -s->cx);
   float ey = fmaf(s->cz, ry, -s->cy);
@@ -161,6 +166,7 @@ static int hit_f32(const proj32* s, float rx, float ry, float zfar, float* t_out
   if (!(disc > 0.0f)) return 0;
   float off = fmaf(rx, ex, fmaf(ry, ey, sqrtf(disc))) / rr;
   float t = s->cz - off;
+  if (t < s->tmin) t = s->tmin;
   if (!(t < zfar)) return 0;
   *t_out = t;
   return 1;
