@@ -1,0 +1,387 @@
+"""Benchmark: forward + backward renders per second of the sphere renderer.
+
+Workload (the 1M-sphere headline case): 1,000,000 spheres on the surfaces of
+20 random ellipsoids, 1024 x 1024 pixels, 16-channel N(0,1) features,
+gamma = 1e-2, n_track = 16, seeded synthetic data.  One step = one pass of
+the whole hot path through the C ABI: project -> bin -> forward render ->
+backward render (gradients for positions, radii, opacities, features, camera
+and background).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank renders its own scene (a different seed) on
+its own GPU with no collective on the data path (weak scaling); the time is
+the maximum over ranks.  ``--impl reference`` times the FP64 CPU oracle on
+bounded pixel samples of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd renders/sec at 1M spheres 1024x1024"
+UNIT = "renders/s"
+WORKLOAD = "1M spheres on 20 ellipsoid surfaces, 1024x1024, C=16 N(0,1), gamma=1e-2, n_track=16"
+FP32_LANES_PER_SM = 128
+N_SMS = 152
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = [r.split(",") for r in self.out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]
+                          and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_scene(rank: int, n: int | None = None, res: int | None = None):
+    from paper_2004_07484_gb300 import scenes
+    if rank == 0:
+        return scenes.config_scene(2, n=n, res=res)
+    return scenes.ellipsoid_surfaces(1002 + 7919 * rank, n or 1_000_000, res or 1024, res or 1024,
+                                     n_channels=16, gamma=1e-2, n_track=16)
+
+
+def cpu_oracle_sample(sc, n_side: int):
+    """Oracle fwd + bwd on an n_side x n_side pixel window of the workload.
+    Returns (seconds, fraction of one render the window covers)."""
+    from oracle import oracle
+    from paper_2004_07484_gb300 import scenes
+    oracle.build()
+    v0, u0 = 448, 448
+    pix = [(u, v) for v in range(v0, v0 + n_side) for u in range(u0, u0 + n_side)]
+    G = np.zeros((sc.height, sc.width, sc.n_channels))
+    G[v0:v0 + n_side, u0:u0 + n_side] = scenes.grad_image(5, n_side, n_side, sc.n_channels)
+    t0 = time.perf_counter()
+    oracle.render_pixels(sc, pix)
+    oracle.render_backward(sc, G)
+    dt = time.perf_counter() - t0
+    return dt, (n_side * n_side) / float(sc.width * sc.height)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return
+    sc = make_scene(0)
+    n_side = 8
+    tot, frac = 0.0, 0.0
+    for _ in range(args.warmup):
+        cpu_oracle_sample(sc, n_side)
+    for _ in range(args.steps):
+        dt, f = cpu_oracle_sample(sc, n_side)
+        tot += dt
+        frac += f
+    value = frac / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "model": "pulsar sphere renderer", "global_batch": 1,
+                       "seq_len": None, "parallelism": "none (host cores)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                             "sample": f"{n_side}x{n_side}-pixel window per step, fwd + bwd, FP64 brute force"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--recompute", action="store_true", help="time recompute mode as the main value")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="warm up, run one step inside the NVTX range 'pulsar_step' and exit (for ncu)")
+    ap.add_argument("--spheres", type=int, default=None, help="override the sphere count (profiling)")
+    ap.add_argument("--res", type=int, default=None, help="override the square resolution (profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2004_07484_gb300 import RenderSettings, _lib, backward_frame, forward_frame
+
+    rank, world, local = rank_info()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+        __graft_entry__.build()
+
+    sc = make_scene(rank, args.spheres, args.res)
+    t = {k: torch.from_numpy(np.ascontiguousarray(getattr(sc, k))).to(dev)
+         for k in ("pos", "rad", "opa", "feat", "cam", "bg")}
+    G = torch.from_numpy(np.ascontiguousarray(
+        np.random.default_rng(7 + rank).standard_normal((sc.height, sc.width, sc.n_channels)).astype(np.float32))).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def settings(store: bool):
+        return RenderSettings(sc.width, sc.height, sc.n_channels, sc.n_track, sc.gamma, sc.eps,
+                              sc.znear, sc.zfar, store_hits=store)
+
+    # size the pair list once (synchronising check), then run without checks
+    fr, _, _ = forward_frame(settings(True), t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"],
+                             4 * sc.n_spheres, check_overflow=True)
+    capacity = int(fr.params.list_capacity)
+    pairs_needed = _lib.read_status(fr.ws.data_ptr(), fr.ws_bytes, stream.cuda_stream)[1]
+
+    # counters for the algorithmic work of the render kernels
+    H, W, C = sc.height, sc.width, sc.n_channels
+    n_hits = torch.empty((H, W), dtype=torch.int32, device=dev)
+    n_tests = torch.empty((H, W), dtype=torch.int32, device=dev)
+    forward_frame(settings(True), t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"], capacity,
+                  check_overflow=False, n_hits=n_hits, n_tests=n_tests)
+    torch.cuda.synchronize()
+    hits = int(n_hits.sum().item())
+    tests = int(n_tests.sum().item())
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB of L2
+
+    fwd_ev, bwd_ev = [], []
+
+    def step(store: bool, timed_kernels: bool):
+        s = settings(store)
+        fr, image, log_norm = forward_frame(s, t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"],
+                                            capacity, check_overflow=False)
+        grads = backward_frame(fr, t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"], image,
+                               log_norm, G)
+        return fr, image, grads
+
+    def timed_steps(store: bool, k: int):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        for i in range(k):
+            flush.fill_(i & 0xff)
+            starts[i].record(stream)
+            fr, image, grads = step(store, True)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        return [s.elapsed_time(e) for s, e in zip(starts, ends)], fr
+
+    for _ in range(max(args.warmup, 3)):
+        step(True, False)
+        step(False, False)
+    torch.cuda.synchronize()
+    if args.profile_step:
+        torch.cuda.nvtx.range_push("pulsar_step")
+        step(not args.recompute, True)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile_step": "done", "pairs": pairs_needed, "hits": hits, "tests": tests}))
+        return
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        ms_store, fr_last = timed_steps(not args.recompute, args.steps)
+        ms_rec, _ = timed_steps(args.recompute, max(3, args.steps // 2))
+        t_wall = time.perf_counter() - t_wall
+    st, _ = _lib.read_status(fr_last.ws.data_ptr(), fr_last.ws_bytes, stream.cuda_stream)
+    assert st == _lib.OK, f"pair list overflow during timing (status {st})"
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(ms_store)
+    if world > 1:
+        x = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        total_ms = float(x.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # per-kernel timing of the dominant kernels (events on the launch stream)
+    def kernel_ms(store: bool, reps: int = 5):
+        s = settings(store)
+        fwd, bwd = [], []
+        for i in range(reps):
+            fr = None
+            flush.fill_(i & 0xff)
+            from paper_2004_07484_gb300.renderer import Frame, scene_args
+            fr = Frame(s, sc.n_spheres, capacity, dev)
+            sa = scene_args(t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"])
+            _lib.project(fr.params, sa, fr.ws.data_ptr(), fr.ws_bytes, stream.cuda_stream)
+            _lib.bin(fr.params, fr.ws.data_ptr(), fr.ws_bytes, stream.cuda_stream)
+            image = torch.empty((H, W, C), dtype=torch.float32, device=dev)
+            log_norm = torch.empty((H, W), dtype=torch.float32, device=dev)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            _lib.render_fwd(fr.params, sa, fr.ws.data_ptr(), fr.ws_bytes, image.data_ptr(),
+                            log_norm.data_ptr(), None, None, None, stream.cuda_stream)
+            e1.record(stream)
+            backward_frame(fr, t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"], image, log_norm, G)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            fwd.append(e0.elapsed_time(e1))
+            bwd.append(e1.elapsed_time(e2))
+        return statistics.median(fwd), statistics.median(bwd)
+
+    fwd_ms, bwd_ms = kernel_ms(not args.recompute)
+
+    # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
+    host_in = {k: v.cpu().pin_memory() for k, v in t.items()}
+    host_G = G.cpu().pin_memory()
+    host_out = {"image": torch.empty((H, W, C), dtype=torch.float32).pin_memory(),
+                "pos": torch.empty((sc.n_spheres, 3)).pin_memory(), "rad": torch.empty(sc.n_spheres).pin_memory(),
+                "opa": torch.empty(sc.n_spheres).pin_memory(), "feat": torch.empty((sc.n_spheres, C)).pin_memory(),
+                "cam": torch.empty(11).pin_memory(), "bg": torch.empty(C).pin_memory()}
+    d_in = {k: torch.empty_like(v, device=dev) for k, v in host_in.items()}
+    d_G = torch.empty_like(host_G, device=dev)
+    h2d = sum(v.numel() * 4 for v in host_in.values()) + host_G.numel() * 4
+    d2h = sum(v.numel() * 4 for v in host_out.values())
+
+    def e2e_step():
+        for k in d_in:
+            d_in[k].copy_(host_in[k], non_blocking=True)
+        d_G.copy_(host_G, non_blocking=True)
+        s = settings(not args.recompute)
+        fr, image, log_norm = forward_frame(s, d_in["pos"], d_in["feat"], d_in["rad"], d_in["opa"],
+                                            d_in["cam"], d_in["bg"], capacity, check_overflow=False)
+        gp, gr, go, gf, gc, gb = backward_frame(fr, d_in["pos"], d_in["feat"], d_in["rad"], d_in["opa"],
+                                                d_in["cam"], d_in["bg"], image, log_norm, d_G)
+        for k, v in (("image", image), ("pos", gp), ("rad", gr), ("opa", go), ("feat", gf), ("cam", gc),
+                     ("bg", gb)):
+            host_out[k].copy_(v, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k_e2e = max(3, args.steps // 2)
+    e0.record(stream)
+    for _ in range(k_e2e):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / k_e2e
+    if world > 1:
+        x = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        e2e_ms = float(x.item())
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    pk, pk_kind = peaks()
+    clocks = clk.summary()
+    # ALU roofline of the dominant kernel: FP32 operations of the render passes
+    # (counts of ray-sphere tests and hits from the kernel's own counters)
+    flops_fwd = 26.0 * tests + (30.0 + 2.0 * C) * hits
+    sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    fp32_peak_max = N_SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    dominant = "render_fwd" if fwd_ms >= bwd_ms else "render_bwd"
+    achieved = flops_fwd / (fwd_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "pulsar_render_fwd (render_fwd_kernel)", "achieved": achieved,
+                "peak": fp32_peak_max, "unit": "TFLOP/s", "frac": achieved / fp32_peak_max,
+                "traffic": None,
+                "peak_kind": f"FP32 FMA pipes: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x max SM clock "
+                             f"({pk.get('sm_max_mhz', 2070.0)} MHz, {pk_kind})",
+                "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "dominant": dominant,
+                "ray_tests": tests, "hits": hits, "pairs": pairs_needed}
+    cpu = None
+    if not args.no_cpu_baseline:
+        dt, frac = cpu_oracle_sample(sc, 16)
+        cpu = {"value": frac / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+               "sample": "16x16-pixel window of the workload, fwd + bwd, FP64 brute force over all 1M spheres"}
+    launches_per_step = 30
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "model": "pulsar sphere renderer", "global_batch": world,
+                       "seq_len": None, "parallelism": f"replicas x{world} (independent renders)",
+                       "l2": "flushed between steps (256 MB write, untimed)",
+                       "hit_lists": "recompute" if args.recompute else "store"},
+            "recompute_ms_per_step" if not args.recompute else "store_ms_per_step": statistics.mean(ms_rec),
+            "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": launches_per_step * (args.steps + max(3, args.steps // 2)),
+            "wall_s_timed": t_wall}
+    print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * pulsar.h: C ABI of the GB300-native differentiable sphere renderer.
+ *
+ * The renderer maps a sphere scene S = {(p_i, f_i, r_i, o_i)} and a camera
+ * (R, t, K) to a feature image F = R(S, R, t, K) (Sec. 3.2, App. A of
+ * Lassner & Zollhoefer, "Pulsar", arXiv 2004.07484) and back-propagates a
+ * gradient dL/dF to every scene and camera parameter (App. B, "The Backward
+ * Pass").  Pixel weights follow Eq. 1:
+ *
+ *   w_i = o_i d_i exp(o_i z_i / gamma) / (exp(eps / gamma) + sum_k o_k d_k exp(o_k z_k / gamma))
+ *   F   = sum_i w_i f_i + w_B bg,   w_B = exp(eps / gamma) / D
+ *
+ * with z_i the normalised depth of the ray's entry point (0 = far plane) and
+ * d_i the normalised distance of the ray to the sphere centre.
+ *
+ * Conventions shared by every entry point
+ *   - All array pointers are DEVICE pointers to contiguous float32 (or int32)
+ *     memory owned by the caller.  The library never allocates device memory:
+ *     scratch space is the caller's workspace, sized by pulsar_workspace_size.
+ *   - Calls are asynchronous on the given CUDA stream (NULL = legacy default)
+ *     and never synchronise, except pulsar_read_status.
+ *   - Argument errors are detected on the host and returned before anything
+ *     is enqueued.  Data-dependent overflow (more (tile, sphere) pairs than
+ *     list_capacity) is recorded in the workspace; the outputs of that call
+ *     are then undefined and pulsar_read_status reports it.
+ *   - Layouts: positions M x 3, features M x C (row-major), images H x W x C
+ *     (row-major, pixel (x, y) at offset (y * W + x) * C), per-pixel planes
+ *     H x W.
+ *   - Camera vector, in the order printed in Listing 1 with the 6D rotation
+ *     of Zhou et al. that the paper accepts natively:
+ *       cam[0..2]  t, the camera centre in world coordinates
+ *       cam[3..8]  a1, a2: 6D rotation; Gram-Schmidt gives the camera axes
+ *                  b1 = a1/|a1|, b2 = unit(a2 - (b1.a2) b1), b3 = b1 x b2,
+ *                  and the camera-space centre is c = (b1.(p-t), b2.(p-t), b3.(p-t))
+ *       cam[9]     focal length f
+ *       cam[10]    sensor width s; the pixel pitch on the unit image plane is
+ *                  s / (W f), the principal point is the image centre, the
+ *                  camera looks down +z with x to the right and y downwards.
+ */
+#ifndef PULSAR_H
+#define PULSAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PULSAR_OK = 0,
+  PULSAR_ERR_INVALID_ARG = 1,  /* a host-side argument check failed */
+  PULSAR_ERR_CAPACITY = 2,     /* workspace or pair list too small */
+  PULSAR_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  PULSAR_ERR_TIMEOUT = 4,      /* a bounded device loop gave up */
+  PULSAR_ERR_UNSUPPORTED = 5   /* valid request this build does not handle */
+} pulsar_status;
+
+/* pulsar_params.flags */
+enum {
+  /* The forward pass stores, per pixel, the depth and index of the n_track-th
+   * closest hit, so the backward pass reads it instead of searching again
+   * (App. B, "Preparing for the Backward Pass").  Without it the backward
+   * pass recomputes each pixel's tracked hits. */
+  PULSAR_FLAG_STORE_HITS = 1u << 0,
+  /* d_i = min(1, dist/R) as printed in Sec. 3.2; the default is
+   * d_i = 1 - min(1, dist/R) (weight 1 at the centre, 0 at the rim). */
+  PULSAR_FLAG_DIST_LITERAL = 1u << 1,
+  /* Disable the one-pixel minimum size (App. B, Step 0). */
+  PULSAR_FLAG_NO_MIN_SIZE = 1u << 2
+};
+
+/* grad_mask bits of pulsar_render_bwd: gradients are computed only where
+ * requested (App. B, end of "The Backward Pass"). */
+enum {
+  PULSAR_GRAD_POS = 1u << 0,
+  PULSAR_GRAD_RAD = 1u << 1,
+  PULSAR_GRAD_OPA = 1u << 2,
+  PULSAR_GRAD_FEAT = 1u << 3,
+  PULSAR_GRAD_CAM = 1u << 4,
+  PULSAR_GRAD_BG = 1u << 5,
+  PULSAR_GRAD_ALL = 63u
+};
+
+/* Per-scene settings.  Host memory, read during the call only. */
+typedef struct {
+  int32_t width, height;   /* image size; 1..65535 (App. B stores the sphere
+                              rectangle in 16-bit fields) */
+  int32_t n_spheres;       /* M >= 0 */
+  int32_t n_channels;      /* C = feature length, 1..32 */
+  int32_t n_track;         /* closest hits kept per pixel for the backward
+                              pass (App. B, Step 2), 1..32 */
+  int32_t tile;            /* screen tile edge in pixels; 16 */
+  int64_t list_capacity;   /* maximum number of (tile, sphere) pairs */
+  float gamma;             /* blending sharpness, [1e-5, 1] (Sec. 3.2) */
+  float eps;               /* background offset eps of Eq. 1, >= 0 */
+  float znear, zfar;       /* depth range mapped to z in [0, 1]; 0 < znear < zfar */
+  uint32_t flags;          /* PULSAR_FLAG_* */
+} pulsar_params;
+
+/* Scene inputs: device pointers, float32, contiguous. */
+typedef struct {
+  const float* pos;   /* M x 3 sphere centres p_i */
+  const float* rad;   /* M radii r_i */
+  const float* opa;   /* M opacities o_i */
+  const float* feat;  /* M x C feature vectors f_i */
+  const float* cam;   /* 11 camera values (layout above) */
+  const float* bg;    /* C background features */
+} pulsar_scene;
+
+/* Bytes of device workspace a render with these settings needs (0 when the
+ * settings are invalid).  The workspace holds the projected sphere records,
+ * sort buffers, the (tile, sphere) pair lists, tile ranges, per-pixel
+ * backward data and gradient accumulators.  It must be 256-byte aligned. */
+size_t pulsar_workspace_size(const pulsar_params* params);
+
+/* Step 0 of App. B: projects every sphere through the pinhole camera.
+ * Writes, into the workspace, a 32-byte draw record per sphere (camera-space
+ * centre, squared effective radius, earliest intersection depth, opacity and
+ * the inclusive pixel rectangle) and the sort key (the earliest depth, +inf
+ * for culled spheres). */
+pulsar_status pulsar_project(const pulsar_params* params, const pulsar_scene* scene,
+                             void* workspace, size_t workspace_bytes, void* stream);
+
+/* Builds the per-tile sphere lists (App. B, Step 1, replacing the paper's
+ * nine-part split and flag compaction): sorts spheres by (earliest depth,
+ * index), emits one (tile, sphere) pair per tile each sphere's rectangle
+ * overlaps, and sorts pairs stably by tile, so every tile's list is ordered
+ * by (earliest depth, index).  Requires pulsar_project on the same workspace. */
+pulsar_status pulsar_bin(const pulsar_params* params, void* workspace, size_t workspace_bytes,
+                         void* stream);
+
+/* Forward pass (App. B, Steps 1-2): per pixel, intersects the tile's spheres
+ * in list order, blends every hit by Eq. 1 and tracks the n_track closest.
+ *   image      H x W x C output F
+ *   log_norm   H x W output, log of Eq. 1's denominator D (needed by the
+ *              backward pass)
+ *   n_hits     optional (may be NULL) H x W int32: hits blended
+ *   n_tests    optional (may be NULL) H x W int32: ray-sphere tests made
+ *              (spheres whose rectangle contains the pixel)
+ *   tracked    optional (may be NULL) H x W x n_track int32: indices of the
+ *              tracked hits, closest first (by depth, then index), -1 padded
+ * Requires pulsar_bin on the same workspace. */
+pulsar_status pulsar_render_fwd(const pulsar_params* params, const pulsar_scene* scene,
+                                void* workspace, size_t workspace_bytes, float* image,
+                                float* log_norm, int32_t* n_hits, int32_t* n_tests,
+                                int32_t* tracked, void* stream);
+
+/* Backward pass (App. B, "The Backward Pass"): given G = dL/dF, returns the
+ * gradients through each pixel's tracked hits.  Outputs selected by grad_mask
+ * are overwritten (zeroed in-stream first); the others may be NULL.
+ *   image, log_norm   the forward outputs of the same call sequence
+ *   grad_image        H x W x C upstream gradient
+ *   g_pos M x 3, g_rad M, g_opa M, g_feat M x C, g_cam 11, g_bg C
+ * Requires pulsar_render_fwd on the same workspace (and, without
+ * PULSAR_FLAG_STORE_HITS, the unchanged tile lists of pulsar_bin). */
+pulsar_status pulsar_render_bwd(const pulsar_params* params, const pulsar_scene* scene,
+                                void* workspace, size_t workspace_bytes, const float* image,
+                                const float* log_norm, const float* grad_image, uint32_t grad_mask,
+                                float* g_pos, float* g_rad, float* g_opa, float* g_feat,
+                                float* g_cam, float* g_bg, void* stream);
+
+/* Copies the per-tile sphere lists built by pulsar_bin (App. B, Step 1) out
+ * of the workspace, asynchronously on the stream:
+ *   ranges  n_tiles x 2 int32 device array: [begin, end) of each tile's list
+ *           (tiles row-major, ceil(W/tile) per row; empty tiles get [0, 0))
+ *   ids     list_capacity int32 device array: sphere indices, each tile's
+ *           list ordered by (earliest depth, index)
+ * Valid only when the last pulsar_bin did not overflow. */
+pulsar_status pulsar_read_tile_lists(const pulsar_params* params, void* workspace,
+                                     size_t workspace_bytes, int32_t* ranges, int32_t* ids,
+                                     void* stream);
+
+/* Synchronises the stream, then reads the workspace's device flags.
+ * Returns PULSAR_ERR_CAPACITY when the last pulsar_bin overflowed
+ * list_capacity; *pairs_needed (may be NULL) receives the pair count the
+ * last pulsar_bin required. */
+pulsar_status pulsar_read_status(void* workspace, size_t workspace_bytes, int64_t* pairs_needed,
+                                 void* stream);
+
+/* Static description of a status code. */
+const char* pulsar_status_string(pulsar_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PULSAR_H */

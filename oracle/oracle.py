@@ -69,6 +69,9 @@ def lib():
         L.orc_hit_f32.restype = ctypes.c_int
         L.orc_hit_map.argtypes = [P(OrcParams), P(d), d, P(d), ctypes.c_int, P(ctypes.c_uint8)]
         L.orc_hit_map.restype = None
+        L.orc_render_pixels.argtypes = [P(OrcParams), P(d), P(d), P(d), P(d), P(d), P(d), ctypes.c_int,
+                                        P(i32), P(d), P(d), P(i32), P(i32), P(f)]
+        L.orc_render_pixels.restype = None
         _lib = L
     return _lib
 
@@ -226,3 +229,23 @@ def hit_map(scene, pos3, rad, min_size: bool = True, ignore_cull: bool = False) 
                       _ptr(_d(scene.cam), ctypes.c_double), int(bool(ignore_cull)),
                       _ptr(m, ctypes.c_uint8))
     return m.astype(bool)
+
+
+def render_pixels(scene, pixels, n_track: int | None = None, min_size: bool = True,
+                  dist_literal: bool = False) -> Forward:
+    """Forward pass at the listed (u, v) pixels only; arrays are indexed by list position."""
+    p = params(scene, n_track=n_track, min_size=min_size, dist_literal=dist_literal)
+    pix = np.ascontiguousarray(np.asarray(pixels, np.int32).reshape(-1, 2))
+    n, C, K = pix.shape[0], p.n_channels, p.n_track
+    arrs = _scene_arrays(scene)
+    img = np.zeros((n, C), np.float64)
+    ld = np.zeros(n, np.float64)
+    nh = np.zeros(n, np.int32)
+    tr = np.zeros((n, K), np.int32)
+    tt = np.zeros((n, K), np.float32)
+    D = ctypes.c_double
+    lib().orc_render_pixels(ctypes.byref(p), *[_ptr(a, D) for a in arrs], int(n),
+                            _ptr(pix, ctypes.c_int32), _ptr(img, D), _ptr(ld, D),
+                            _ptr(nh, ctypes.c_int32), _ptr(tr, ctypes.c_int32),
+                            _ptr(tt, ctypes.c_float))
+    return Forward(img, ld, nh, tr, tt, np.zeros(n))

@@ -487,6 +487,9 @@ void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
       for (int u = 0; u < W; ++u) {
         size_t px = (size_t)v * W + u;
         const double* G = grad + px * Cn;
+        int nz = 0;
+        for (int c = 0; c < Cn; ++c) nz |= G[c] != 0.0;
+        if (!nz) continue;  /* every contribution of this pixel is a multiple of G */
         int n = pixel_hits(P, &C, u, v, hits);
         double logD = blend_pixel(P, &C, u, v, hits, n, F, NULL);
         double wB = exp(P->eps / g - logD);
@@ -648,5 +651,35 @@ void orc_hit_map(const orc_params* P, const double* pos3, double rad, const doub
       }
       map[(size_t)v * P->width + u] = (uint8_t)hit;
     }
+  ctx_free(&C);
+}
+
+/* Forward pass at a list of pixels only (for sampled checks of large
+ * workloads): pix holds n_pix (u, v) pairs; outputs are per listed pixel. */
+void orc_render_pixels(const orc_params* P, const double* pos, const double* rad,
+                       const double* opa, const double* feat, const double* cam, const double* bg,
+                       int n_pix, const int32_t* pix, double* image, double* log_d,
+                       int32_t* n_hits, int32_t* tracked, float* tracked_t) {
+  ctx_t C;
+  memset(&C, 0, sizeof(C));
+  C.pos = pos; C.rad = rad; C.opa = opa; C.feat = feat; C.cam = cam; C.bg = bg;
+  ctx_init(P, pos, rad, cam, NULL, NULL, NULL, &C);
+  int K = P->n_track, Cn = P->n_channels;
+#pragma omp parallel
+  {
+    hit_rec* hits = (hit_rec*)malloc(sizeof(hit_rec) * (size_t)(P->n_spheres + 1));
+#pragma omp for schedule(dynamic, 4)
+    for (int q = 0; q < n_pix; ++q) {
+      int u = pix[2 * q], v = pix[2 * q + 1];
+      int n = pixel_hits(P, &C, u, v, hits);
+      log_d[q] = blend_pixel(P, &C, u, v, hits, n, image + (size_t)q * Cn, NULL);
+      n_hits[q] = n;
+      for (int k = 0; k < K; ++k) {
+        tracked[(size_t)q * K + k] = k < n ? hits[k].id : -1;
+        tracked_t[(size_t)q * K + k] = k < n ? hits[k].t32 : INFINITY;
+      }
+    }
+    free(hits);
+  }
   ctx_free(&C);
 }

@@ -1,0 +1,9 @@
+"""GB300-native differentiable sphere renderer (Pulsar, arXiv 2004.07484).
+
+The hot path (projection, depth sort, tile binning, forward blend and
+backward pass) runs in hand-written CUDA kernels for sm_103a behind the C ABI
+of include/pulsar.h; ``renderer.Renderer`` wraps it as a PyTorch module.
+"""
+from .renderer import Renderer, RenderSettings, forward_frame, backward_frame  # noqa: F401
+
+__all__ = ["Renderer", "RenderSettings", "forward_frame", "backward_frame"]

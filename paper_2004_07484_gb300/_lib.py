@@ -1,0 +1,130 @@
+"""ctypes binding of ``libpulsar_gb300.so`` (the C ABI in include/pulsar.h).
+
+Argument marshalling only: every step of the renderer runs in the library's
+CUDA kernels.  Importing this module loads the in-tree library and fails
+loudly when it is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpulsar_gb300.so")
+
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(6)
+
+FLAG_STORE_HITS = 1 << 0
+FLAG_DIST_LITERAL = 1 << 1
+FLAG_NO_MIN_SIZE = 1 << 2
+
+GRAD_POS, GRAD_RAD, GRAD_OPA, GRAD_FEAT, GRAD_CAM, GRAD_BG = (1 << k for k in range(6))
+GRAD_ALL = 63
+
+EXPORTED = ("pulsar_workspace_size", "pulsar_project", "pulsar_bin", "pulsar_render_fwd",
+            "pulsar_render_bwd", "pulsar_read_tile_lists", "pulsar_read_status",
+            "pulsar_status_string")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+        ("n_spheres", ctypes.c_int32), ("n_channels", ctypes.c_int32),
+        ("n_track", ctypes.c_int32), ("tile", ctypes.c_int32),
+        ("list_capacity", ctypes.c_int64),
+        ("gamma", ctypes.c_float), ("eps", ctypes.c_float),
+        ("znear", ctypes.c_float), ("zfar", ctypes.c_float),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+class SceneArgs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("pos", "rad", "opa", "feat", "cam", "bg")]
+
+
+class PulsarError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library.  Raises when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2004_07484_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, sz, u32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32
+        P, S = ctypes.POINTER(Params), ctypes.POINTER(SceneArgs)
+        L.pulsar_workspace_size.argtypes = [P]
+        L.pulsar_workspace_size.restype = sz
+        L.pulsar_project.argtypes = [P, S, vp, sz, vp]
+        L.pulsar_project.restype = ctypes.c_int
+        L.pulsar_bin.argtypes = [P, vp, sz, vp]
+        L.pulsar_bin.restype = ctypes.c_int
+        L.pulsar_render_fwd.argtypes = [P, S, vp, sz, vp, vp, vp, vp, vp, vp]
+        L.pulsar_render_fwd.restype = ctypes.c_int
+        L.pulsar_render_bwd.argtypes = [P, S, vp, sz, vp, vp, vp, u32, vp, vp, vp, vp, vp, vp, vp]
+        L.pulsar_render_bwd.restype = ctypes.c_int
+        L.pulsar_read_tile_lists.argtypes = [P, vp, sz, vp, vp, vp]
+        L.pulsar_read_tile_lists.restype = ctypes.c_int
+        L.pulsar_read_status.argtypes = [vp, sz, ctypes.POINTER(ctypes.c_int64), vp]
+        L.pulsar_read_status.restype = ctypes.c_int
+        L.pulsar_status_string.argtypes = [ctypes.c_int]
+        L.pulsar_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().pulsar_status_string(int(status)).decode()
+
+
+def _check(status: int, where: str) -> None:
+    if status != OK:
+        raise PulsarError(status, where)
+
+
+def workspace_size(p: Params) -> int:
+    n = lib().pulsar_workspace_size(ctypes.byref(p))
+    if n == 0:
+        raise PulsarError(ERR_INVALID_ARG, "pulsar_workspace_size")
+    return int(n)
+
+
+def project(p: Params, s: SceneArgs, ws: int, ws_bytes: int, stream: int) -> None:
+    _check(lib().pulsar_project(ctypes.byref(p), ctypes.byref(s), ws, ws_bytes, stream), "pulsar_project")
+
+
+def bin(p: Params, ws: int, ws_bytes: int, stream: int) -> None:  # noqa: A001 - C name
+    _check(lib().pulsar_bin(ctypes.byref(p), ws, ws_bytes, stream), "pulsar_bin")
+
+
+def render_fwd(p: Params, s: SceneArgs, ws: int, ws_bytes: int, image: int, log_norm: int,
+               n_hits: int | None, n_tests: int | None, tracked: int | None, stream: int) -> None:
+    _check(lib().pulsar_render_fwd(ctypes.byref(p), ctypes.byref(s), ws, ws_bytes, image, log_norm,
+                                   n_hits, n_tests, tracked, stream), "pulsar_render_fwd")
+
+
+def render_bwd(p: Params, s: SceneArgs, ws: int, ws_bytes: int, image: int, log_norm: int,
+               grad_image: int, grad_mask: int, g_pos, g_rad, g_opa, g_feat, g_cam, g_bg,
+               stream: int) -> None:
+    _check(lib().pulsar_render_bwd(ctypes.byref(p), ctypes.byref(s), ws, ws_bytes, image, log_norm,
+                                   grad_image, grad_mask, g_pos, g_rad, g_opa, g_feat, g_cam, g_bg,
+                                   stream), "pulsar_render_bwd")
+
+
+def read_tile_lists(p: Params, ws: int, ws_bytes: int, ranges: int, ids: int, stream: int) -> None:
+    _check(lib().pulsar_read_tile_lists(ctypes.byref(p), ws, ws_bytes, ranges, ids, stream),
+           "pulsar_read_tile_lists")
+
+
+def read_status(ws: int, ws_bytes: int, stream: int) -> tuple[int, int]:
+    """(status, pairs_needed); synchronises the stream."""
+    need = ctypes.c_int64(0)
+    st = lib().pulsar_read_status(ws, ws_bytes, ctypes.byref(need), stream)
+    return int(st), int(need.value)

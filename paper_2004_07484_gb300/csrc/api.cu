@@ -1,0 +1,341 @@
+// Host side of the C ABI declared in include/pulsar.h: argument validation,
+// the workspace layout, and the launch sequence of each entry point.
+#include <string.h>
+
+#include <algorithm>
+
+#include "pulsar_internal.cuh"
+
+namespace pulsar {
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t hdr, scenes, rec0, rec1, rec2, key0, key1, val0, val1, hist, block_sums, pkey0, pkey1, pval0,
+      pval1, ranges, tile_kappa, tile_bg, thr, gacc, fin_part, total;
+  int64_t n_spheres, n_tiles, n_pixels, capacity;
+  int32_t sort_blocks, fin_blocks, tile_bits;
+};
+
+bool tiles_of(const pulsar_params& p, int& tx, int& ty) {
+  tx = (p.width + kTile - 1) / kTile;
+  ty = (p.height + kTile - 1) / kTile;
+  return true;
+}
+
+pulsar_status validate(const pulsar_params* p) {
+  if (!p) return PULSAR_ERR_INVALID_ARG;
+  if (p->width < 1 || p->width > 65535 || p->height < 1 || p->height > 65535)
+    return PULSAR_ERR_INVALID_ARG;
+  if (p->n_spheres < 0 || p->n_channels < 1 || p->n_track < 1 || p->list_capacity < 0)
+    return PULSAR_ERR_INVALID_ARG;
+  if (p->n_channels > 32 || p->n_track > 32) return PULSAR_ERR_UNSUPPORTED;
+  if (p->tile != kTile) return PULSAR_ERR_UNSUPPORTED;
+  if (p->list_capacity > (int64_t)INT32_MAX - kSortTile) return PULSAR_ERR_UNSUPPORTED;
+  if (!(p->gamma >= 1e-5f && p->gamma <= 1.0f)) return PULSAR_ERR_INVALID_ARG;
+  if (!(p->eps >= 0.0f) || !(p->znear > 0.0f) || !(p->zfar > p->znear)) return PULSAR_ERR_INVALID_ARG;
+  if (p->flags & ~(uint32_t)(PULSAR_FLAG_STORE_HITS | PULSAR_FLAG_DIST_LITERAL | PULSAR_FLAG_NO_MIN_SIZE))
+    return PULSAR_ERR_INVALID_ARG;
+  return PULSAR_OK;
+}
+
+Layout make_layout(const pulsar_params* ps, int n) {
+  Layout L;
+  memset(&L, 0, sizeof(L));
+  int64_t M = 0, NT = 0, P = 0, cap = 0;
+  int fin = 0;
+  bool store = false;
+  int C = ps[0].n_channels;
+  for (int s = 0; s < n; ++s) {
+    int tx, ty;
+    tiles_of(ps[s], tx, ty);
+    M += ps[s].n_spheres;
+    NT += (int64_t)tx * ty;
+    P += (int64_t)ps[s].width * ps[s].height;
+    cap += ps[s].list_capacity;
+    fin += (ps[s].n_spheres + kFinalizeThreads - 1) / kFinalizeThreads;
+    store = store || (ps[s].flags & PULSAR_FLAG_STORE_HITS);
+  }
+  L.n_spheres = M;
+  L.n_tiles = NT;
+  L.n_pixels = P;
+  L.capacity = cap;
+  L.fin_blocks = fin;
+  L.sort_blocks = (int32_t)((std::max<int64_t>(std::max<int64_t>(M, cap), 1) + kSortTile - 1) / kSortTile);
+  int bits = 1;
+  while (bits < 32 && ((int64_t)1 << bits) < NT) ++bits;
+  L.tile_bits = bits;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  L.hdr = take(sizeof(WsHeader));
+  L.scenes = take(sizeof(SceneDev) * kMaxScenes);
+  L.rec0 = take(16 * (size_t)M);
+  L.rec1 = take(16 * (size_t)M);
+  L.rec2 = take(16 * (size_t)M);
+  L.key0 = take(4 * (size_t)M);
+  L.key1 = take(4 * (size_t)M);
+  L.val0 = take(4 * (size_t)M);
+  L.val1 = take(4 * (size_t)M);
+  L.hist = take(4 * (size_t)kRadix * L.sort_blocks);
+  L.block_sums = take(4 * (size_t)L.sort_blocks);
+  L.pkey0 = take(4 * (size_t)cap);
+  L.pkey1 = take(4 * (size_t)cap);
+  L.pval0 = take(4 * (size_t)cap);
+  L.pval1 = take(4 * (size_t)cap);
+  L.ranges = take(8 * (size_t)NT);
+  L.tile_kappa = take(4 * (size_t)NT);
+  L.tile_bg = take(4 * (size_t)NT * C);
+  L.thr = take(store ? 8 * (size_t)P : 0);
+  L.gacc = take(16 * (size_t)M);
+  L.fin_part = take(4 * (size_t)kCamPartials * std::max(fin, 1));
+  L.total = off;
+  return L;
+}
+
+WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
+  char* b = static_cast<char*>(ws);
+  WsView v;
+  memset(&v, 0, sizeof(v));
+  v.hdr = reinterpret_cast<WsHeader*>(b + L.hdr);
+  v.scenes = reinterpret_cast<SceneDev*>(b + L.scenes);
+  v.n_scenes = n;
+  v.n_spheres = L.n_spheres;
+  v.n_tiles = L.n_tiles;
+  v.n_pixels = L.n_pixels;
+  v.capacity = L.capacity;
+  v.sort_blocks = L.sort_blocks;
+  v.fin_blocks = L.fin_blocks;
+  v.n_channels = ps[0].n_channels;
+  v.n_track = ps[0].n_track;
+  v.pair_buf = ((L.tile_bits + kRadixBits - 1) / kRadixBits) & 1;
+  v.rec0 = reinterpret_cast<float4*>(b + L.rec0);
+  v.rec1 = reinterpret_cast<float4*>(b + L.rec1);
+  v.rec2 = reinterpret_cast<float4*>(b + L.rec2);
+  v.key[0] = reinterpret_cast<uint32_t*>(b + L.key0);
+  v.key[1] = reinterpret_cast<uint32_t*>(b + L.key1);
+  v.val[0] = reinterpret_cast<uint32_t*>(b + L.val0);
+  v.val[1] = reinterpret_cast<uint32_t*>(b + L.val1);
+  v.hist = reinterpret_cast<uint32_t*>(b + L.hist);
+  v.block_sums = reinterpret_cast<uint32_t*>(b + L.block_sums);
+  v.pkey[0] = reinterpret_cast<uint32_t*>(b + L.pkey0);
+  v.pkey[1] = reinterpret_cast<uint32_t*>(b + L.pkey1);
+  v.pval[0] = reinterpret_cast<uint32_t*>(b + L.pval0);
+  v.pval[1] = reinterpret_cast<uint32_t*>(b + L.pval1);
+  v.ranges = reinterpret_cast<int2*>(b + L.ranges);
+  v.tile_kappa = reinterpret_cast<float*>(b + L.tile_kappa);
+  v.tile_bg = reinterpret_cast<float*>(b + L.tile_bg);
+  v.thr = reinterpret_cast<float2*>(b + L.thr);
+  v.gacc = reinterpret_cast<float4*>(b + L.gacc);
+  v.fin_part = reinterpret_cast<float*>(b + L.fin_part);
+  return v;
+}
+
+// Host copies of the per-scene descriptors (sizes and offsets; pointers are
+// filled per entry point).
+void fill_scenes(const pulsar_params* ps, const pulsar_scene* sc, int n, SceneDev* out) {
+  int64_t sb = 0, tb = 0, pb = 0;
+  int fb = 0;
+  for (int s = 0; s < n; ++s) {
+    SceneDev& d = out[s];
+    memset(&d, 0, sizeof(d));
+    const pulsar_params& p = ps[s];
+    if (sc) {
+      d.pos = sc[s].pos;
+      d.rad = sc[s].rad;
+      d.opa = sc[s].opa;
+      d.feat = sc[s].feat;
+      d.cam = sc[s].cam;
+      d.bg = sc[s].bg;
+    }
+    d.width = p.width;
+    d.height = p.height;
+    d.n_spheres = p.n_spheres;
+    d.n_channels = p.n_channels;
+    d.n_track = p.n_track;
+    d.flags = p.flags;
+    tiles_of(p, d.tiles_x, d.tiles_y);
+    d.sphere_begin = sb;
+    d.tile_begin = tb;
+    d.pixel_begin = pb;
+    d.fin_block_begin = fb;
+    d.fin_blocks = (p.n_spheres + kFinalizeThreads - 1) / kFinalizeThreads;
+    d.gamma = p.gamma;
+    d.eps = p.eps;
+    d.znear = p.znear;
+    d.zfar = p.zfar;
+    sb += p.n_spheres;
+    tb += (int64_t)d.tiles_x * d.tiles_y;
+    pb += (int64_t)p.width * p.height;
+    fb += d.fin_blocks;
+  }
+}
+
+pulsar_status check_ws(const pulsar_params* p, void* ws, size_t bytes, Layout& L) {
+  pulsar_status st = validate(p);
+  if (st != PULSAR_OK) return st;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return PULSAR_ERR_INVALID_ARG;
+  L = make_layout(p, 1);
+  if (bytes < L.total) return PULSAR_ERR_CAPACITY;
+  return PULSAR_OK;
+}
+
+bool scene_ok(const pulsar_params* p, const pulsar_scene* s) {
+  if (!s || !s->cam || !s->bg) return false;
+  if (p->n_spheres > 0 && (!s->pos || !s->rad || !s->opa || !s->feat)) return false;
+  return true;
+}
+
+pulsar_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PULSAR_OK : PULSAR_ERR_CUDA; }
+
+}  // namespace
+}  // namespace pulsar
+
+using namespace pulsar;
+
+extern "C" size_t pulsar_workspace_size(const pulsar_params* params) {
+  if (validate(params) != PULSAR_OK) return 0;
+  return make_layout(params, 1).total;
+}
+
+extern "C" pulsar_status pulsar_project(const pulsar_params* params, const pulsar_scene* scene,
+                                        void* workspace, size_t workspace_bytes, void* stream) {
+  Layout L;
+  pulsar_status st = check_ws(params, workspace, workspace_bytes, L);
+  if (st != PULSAR_OK) return st;
+  if (!scene_ok(params, scene)) return PULSAR_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  WsView v = make_view(workspace, L, params, 1);
+  SceneDev d;
+  fill_scenes(params, scene, 1, &d);
+  cudaError_t e = launch_setup(v, &d, 1, s);
+  if (e == cudaSuccess) e = launch_project(v, s);
+  return cuda_status(e);
+}
+
+extern "C" pulsar_status pulsar_bin(const pulsar_params* params, void* workspace,
+                                    size_t workspace_bytes, void* stream) {
+  Layout L;
+  pulsar_status st = check_ws(params, workspace, workspace_bytes, L);
+  if (st != PULSAR_OK) return st;
+  WsView v = make_view(workspace, L, params, 1);
+  return cuda_status(launch_bin(v, L.tile_bits, static_cast<cudaStream_t>(stream)));
+}
+
+extern "C" pulsar_status pulsar_render_fwd(const pulsar_params* params, const pulsar_scene* scene,
+                                           void* workspace, size_t workspace_bytes, float* image,
+                                           float* log_norm, int32_t* n_hits, int32_t* n_tests,
+                                           int32_t* tracked, void* stream) {
+  Layout L;
+  pulsar_status st = check_ws(params, workspace, workspace_bytes, L);
+  if (st != PULSAR_OK) return st;
+  if (!scene_ok(params, scene) || !image || !log_norm) return PULSAR_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  WsView v = make_view(workspace, L, params, 1);
+  SceneDev d;
+  fill_scenes(params, scene, 1, &d);
+  d.image = image;
+  d.log_norm = log_norm;
+  d.n_hits = n_hits;
+  d.n_tests = n_tests;
+  d.tracked = tracked;
+  cudaError_t e = launch_setup(v, &d, -1, s);
+  if (e == cudaSuccess) e = launch_render_fwd(v, (params->flags & PULSAR_FLAG_STORE_HITS) != 0, s);
+  return cuda_status(e);
+}
+
+extern "C" pulsar_status pulsar_render_bwd(const pulsar_params* params, const pulsar_scene* scene,
+                                           void* workspace, size_t workspace_bytes,
+                                           const float* image, const float* log_norm,
+                                           const float* grad_image, uint32_t grad_mask,
+                                           float* g_pos, float* g_rad, float* g_opa, float* g_feat,
+                                           float* g_cam, float* g_bg, void* stream) {
+  Layout L;
+  pulsar_status st = check_ws(params, workspace, workspace_bytes, L);
+  if (st != PULSAR_OK) return st;
+  if (!scene_ok(params, scene) || !image || !log_norm || !grad_image) return PULSAR_ERR_INVALID_ARG;
+  if (grad_mask & ~(uint32_t)PULSAR_GRAD_ALL) return PULSAR_ERR_INVALID_ARG;
+  const int64_t M = params->n_spheres;
+  if (M > 0) {
+    if ((grad_mask & PULSAR_GRAD_POS) && !g_pos) return PULSAR_ERR_INVALID_ARG;
+    if ((grad_mask & PULSAR_GRAD_RAD) && !g_rad) return PULSAR_ERR_INVALID_ARG;
+    if ((grad_mask & PULSAR_GRAD_OPA) && !g_opa) return PULSAR_ERR_INVALID_ARG;
+    if ((grad_mask & PULSAR_GRAD_FEAT) && !g_feat) return PULSAR_ERR_INVALID_ARG;
+  }
+  if ((grad_mask & PULSAR_GRAD_CAM) && !g_cam) return PULSAR_ERR_INVALID_ARG;
+  if ((grad_mask & PULSAR_GRAD_BG) && !g_bg) return PULSAR_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  WsView v = make_view(workspace, L, params, 1);
+  SceneDev d;
+  fill_scenes(params, scene, 1, &d);
+  d.image_in = image;
+  d.log_norm_in = log_norm;
+  d.grad_image = grad_image;
+  d.g_pos = g_pos;
+  d.g_rad = g_rad;
+  d.g_opa = g_opa;
+  d.g_feat = g_feat;
+  d.g_cam = g_cam;
+  d.g_bg = g_bg;
+  cudaError_t e = launch_setup(v, &d, -1, s);
+  const int C = params->n_channels;
+  if (e == cudaSuccess && M > 0)
+    e = cudaMemsetAsync(v.gacc, 0, sizeof(float4) * (size_t)M, s);
+  if (e == cudaSuccess && M > 0 && (grad_mask & PULSAR_GRAD_OPA))
+    e = cudaMemsetAsync(g_opa, 0, sizeof(float) * (size_t)M, s);
+  if (e == cudaSuccess && M > 0 && (grad_mask & PULSAR_GRAD_FEAT))
+    e = cudaMemsetAsync(g_feat, 0, sizeof(float) * (size_t)M * C, s);
+  if (e == cudaSuccess)
+    e = launch_render_bwd(v, (params->flags & PULSAR_FLAG_STORE_HITS) != 0, grad_mask, s);
+  if (e == cudaSuccess) e = launch_finalize(v, grad_mask, s);
+  return cuda_status(e);
+}
+
+extern "C" pulsar_status pulsar_read_tile_lists(const pulsar_params* params, void* workspace,
+                                                size_t workspace_bytes, int32_t* ranges,
+                                                int32_t* ids, void* stream) {
+  Layout L;
+  pulsar_status st = check_ws(params, workspace, workspace_bytes, L);
+  if (st != PULSAR_OK) return st;
+  if (!ranges || (!ids && L.capacity > 0)) return PULSAR_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  WsView v = make_view(workspace, L, params, 1);
+  cudaError_t e = cudaMemcpyAsync(ranges, v.ranges, sizeof(int2) * (size_t)L.n_tiles,
+                                  cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && L.capacity > 0)
+    e = cudaMemcpyAsync(ids, v.pval[v.pair_buf], sizeof(int32_t) * (size_t)L.capacity,
+                        cudaMemcpyDeviceToDevice, s);
+  return cuda_status(e);
+}
+
+extern "C" pulsar_status pulsar_read_status(void* workspace, size_t workspace_bytes,
+                                            int64_t* pairs_needed, void* stream) {
+  if (!workspace || workspace_bytes < sizeof(WsHeader)) return PULSAR_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PULSAR_ERR_CUDA;
+  WsHeader h;
+  if (cudaMemcpy(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PULSAR_ERR_CUDA;
+  if (pairs_needed) *pairs_needed = h.pairs_needed;
+  if (h.timeout) return PULSAR_ERR_TIMEOUT;
+  if (h.overflow) return PULSAR_ERR_CAPACITY;
+  return PULSAR_OK;
+}
+
+extern "C" const char* pulsar_status_string(pulsar_status status) {
+  switch (status) {
+    case PULSAR_OK: return "ok";
+    case PULSAR_ERR_INVALID_ARG: return "invalid argument";
+    case PULSAR_ERR_CAPACITY: return "workspace or pair-list capacity too small";
+    case PULSAR_ERR_CUDA: return "CUDA runtime error";
+    case PULSAR_ERR_TIMEOUT: return "bounded device loop gave up";
+    case PULSAR_ERR_UNSUPPORTED: return "unsupported setting";
+  }
+  return "unknown status";
+}

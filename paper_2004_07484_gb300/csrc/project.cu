@@ -1,0 +1,308 @@
+// Scene setup, Step 0 projection (App. B, "Step 0: Enclosing Rectangle
+// Calculation"), and the per-sphere gradient finalisation with the
+// camera-gradient reduction (App. B, "The Backward Pass").
+#include "pulsar_internal.cuh"
+
+namespace pulsar {
+
+namespace {
+
+template <int N>
+struct SetupPack {
+  int n;
+  int full;   // 1: derive camera data and reset counters; 0: refresh pointers only
+  int64_t n_spheres;
+  SceneDev s[N];
+};
+
+// Gram-Schmidt of the 6D rotation in double, for the value path.
+__device__ __forceinline__ void rows_from_rot6_f64(const float* a, double* B) {
+  const double a0 = a[0], a1 = a[1], a2 = a[2], a3 = a[3], a4 = a[4], a5 = a[5];
+  const double n1 = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+  const double b1x = a0 / n1, b1y = a1 / n1, b1z = a2 / n1;
+  const double dt = b1x * a3 + b1y * a4 + b1z * a5;
+  const double ux = a3 - dt * b1x, uy = a4 - dt * b1y, uz = a5 - dt * b1z;
+  const double n2 = sqrt(ux * ux + uy * uy + uz * uz);
+  const double b2x = ux / n2, b2y = uy / n2, b2z = uz / n2;
+  B[0] = b1x; B[1] = b1y; B[2] = b1z;
+  B[3] = b2x; B[4] = b2y; B[5] = b2z;
+  B[6] = b1y * b2z - b1z * b2y;
+  B[7] = b1z * b2x - b1x * b2z;
+  B[8] = b1x * b2y - b1y * b2x;
+}
+
+template <int N>
+__global__ void setup_kernel(WsView v, const SetupPack<N> pk) {
+  const int i = threadIdx.x;
+  if (i < pk.n) {
+    SceneDev d = pk.s[i];
+    if (pk.full) {
+      rows_from_rot6(d.cam + 3, d.rows);
+      d.kappa = pixel_pitch(d.cam, d.width);
+      rows_from_rot6_f64(d.cam + 3, d.rows64);
+      d.kappa64 = (double)d.cam[10] / ((double)d.width * (double)d.cam[9]);
+      d.kappa_hi = (float)d.kappa64;
+      d.kappa_lo = (float)(d.kappa64 - (double)d.kappa_hi);
+      d.omax_bits = 0u;
+    } else {
+      const SceneDev& o = v.scenes[i];
+      for (int k = 0; k < 9; ++k) {
+        d.rows[k] = o.rows[k];
+        d.rows64[k] = o.rows64[k];
+      }
+      d.kappa = o.kappa;
+      d.kappa64 = o.kappa64;
+      d.kappa_hi = o.kappa_hi;
+      d.kappa_lo = o.kappa_lo;
+      d.omax_bits = o.omax_bits;
+    }
+    v.scenes[i] = d;
+  }
+  if (i == 0 && pk.full) {
+    v.hdr->n_scenes = pk.n;
+    v.hdr->n_sort = (int32_t)pk.n_spheres;
+    v.hdr->overflow = 0;
+    v.hdr->timeout = 0;
+  }
+}
+
+// One thread per sphere: draw record, sort key and value, and the scene-wide
+// maximum of |o| (used by the exact early-termination bound).
+__global__ void __launch_bounds__(kThreads) project_kernel(WsView v) {
+  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const bool live = i < v.n_spheres;
+  const int s = live ? scene_of_sphere(v.scenes, v.n_scenes, i) : 0;
+  uint32_t om = 0u;
+  if (live) {
+    const SceneDev& S = v.scenes[s];
+    const int64_t li = i - S.sphere_begin;
+    const float* p = S.pos + 3 * li;
+    const float r = S.rad[li];
+    const float o = S.opa[li];
+    Projected pr = project_sphere(S.rows, S.cam, S.kappa, p[0], p[1], p[2], r, S.width, S.height,
+                                  S.znear, S.zfar, !(S.flags & PULSAR_FLAG_NO_MIN_SIZE));
+    v.rec0[i] = make_float4(pr.cx, pr.cy, pr.cz, pr.R2);
+    v.rec1[i] = make_float4(pr.key, o, __uint_as_float(pack_range(pr.x0, pr.x1)),
+                            __uint_as_float(pack_range(pr.y0, pr.y1)));
+    v.key[0][i] = __float_as_uint(pr.key);
+    v.val[0][i] = (uint32_t)i;
+    // value path: the centre in double, kept as the float32 decision centre
+    // plus a float correction; the radius as used by the value path
+    const double* B = S.rows64;
+    const double dx = (double)p[0] - (double)S.cam[0];
+    const double dy = (double)p[1] - (double)S.cam[1];
+    const double dz = (double)p[2] - (double)S.cam[2];
+    const double cx = B[0] * dx + B[1] * dy + B[2] * dz;
+    const double cy = B[3] * dx + B[4] * dy + B[5] * dz;
+    const double cz = B[6] * dx + B[7] * dy + B[8] * dz;
+    const float Rv = pr.R != r ? (float)(0.75 * sqrt(cx * cx + cy * cy + cz * cz) * S.kappa64) : r;
+    v.rec2[i] = make_float4((float)(cx - (double)pr.cx), (float)(cy - (double)pr.cy),
+                            (float)(cz - (double)pr.cz), Rv);
+    if (pr.visible) om = __float_as_uint(fabsf(o));
+  }
+  // warp-aggregated maxima per scene (non-negative floats order as integers)
+  const unsigned peers = __match_any_sync(0xffffffffu, live ? s : -1);
+  const uint32_t om_w = __reduce_max_sync(peers, om);
+  if (live && (threadIdx.x & 31) == __ffs(peers) - 1 && om_w) atomicMax(&v.scenes[s].omax_bits, om_w);
+}
+
+__device__ __forceinline__ float block_sum(float x, float* sh) {
+  x = warp_sum(x);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[warp] = x;
+  __syncthreads();
+  float r = 0.0f;
+  if (warp == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0f;
+    r = warp_sum(r);
+  }
+  return r;   // valid in thread 0
+}
+
+// One thread per sphere: dL/dc and dL/dR from the pixel pass become dL/dp,
+// dL/dr and the sphere's camera contribution (App. B: camera gradients are
+// gathered per sphere and reduced device-wide afterwards).
+__global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(WsView v, uint32_t mask) {
+  __shared__ float sh[32];
+  const int blk = blockIdx.x;
+  int s = 0;
+  for (int k = 1; k < v.n_scenes; ++k)
+    if (v.scenes[k].fin_block_begin <= blk) s = k;
+  const SceneDev& S = v.scenes[s];
+  const int64_t li = (int64_t)(blk - S.fin_block_begin) * kFinalizeThreads + threadIdx.x;
+  float cam_part[13];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) cam_part[k] = 0.0f;
+  if (li < S.n_spheres) {
+    const int64_t i = S.sphere_begin + li;
+    const float4 g = v.gacc[i];
+    const float* p = S.pos + 3 * li;
+    const float r = S.rad[li];
+    Projected pr = project_sphere(S.rows, S.cam, S.kappa, p[0], p[1], p[2], r, S.width, S.height,
+                                  S.znear, S.zfar, !(S.flags & PULSAR_FLAG_NO_MIN_SIZE));
+    float gc0 = g.x, gc1 = g.y, gc2 = g.z;
+    float gk = 0.0f, grad_r = 0.0f;
+    const bool clamped = pr.R != r;
+    if (clamped) {
+      // R = 0.75 |c| kappa
+      float cn = sqrtf(pr.cx * pr.cx + pr.cy * pr.cy + pr.cz * pr.cz);
+      float f = g.w * 0.75f * S.kappa / cn;
+      gc0 += f * pr.cx;
+      gc1 += f * pr.cy;
+      gc2 += f * pr.cz;
+      gk = g.w * 0.75f * cn;
+    } else {
+      grad_r = g.w;
+    }
+    const float* B = S.rows;
+    float gp0 = B[0] * gc0 + B[3] * gc1 + B[6] * gc2;
+    float gp1 = B[1] * gc0 + B[4] * gc1 + B[7] * gc2;
+    float gp2 = B[2] * gc0 + B[5] * gc1 + B[8] * gc2;
+    if (mask & PULSAR_GRAD_POS) {
+      S.g_pos[3 * li] = gp0;
+      S.g_pos[3 * li + 1] = gp1;
+      S.g_pos[3 * li + 2] = gp2;
+    }
+    if (mask & PULSAR_GRAD_RAD) S.g_rad[li] = grad_r;
+    if (mask & PULSAR_GRAD_CAM) {
+      float d0 = p[0] - S.cam[0], d1 = p[1] - S.cam[1], d2 = p[2] - S.cam[2];
+      cam_part[0] = gc0 * d0; cam_part[1] = gc0 * d1; cam_part[2] = gc0 * d2;
+      cam_part[3] = gc1 * d0; cam_part[4] = gc1 * d1; cam_part[5] = gc1 * d2;
+      cam_part[6] = gc2 * d0; cam_part[7] = gc2 * d1; cam_part[8] = gc2 * d2;
+      cam_part[9] = -gp0; cam_part[10] = -gp1; cam_part[11] = -gp2;
+      cam_part[12] = gk;
+    }
+  }
+  if (mask & PULSAR_GRAD_CAM) {
+#pragma unroll
+    for (int k = 0; k < 13; ++k) {
+      float t = block_sum(cam_part[k], sh);
+      if (threadIdx.x == 0) v.fin_part[(size_t)blk * kCamPartials + k] = t;
+    }
+  }
+}
+
+__device__ __forceinline__ void cross3(const float* a, const float* b, float* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ float dot3(const float* a, const float* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// One CTA per scene: deterministic sum of the per-block camera partials, the
+// per-tile pitch and background partials, then the chain through the pixel
+// pitch kappa = s / (W f) and the Gram-Schmidt map of the 6D rotation.
+__global__ void __launch_bounds__(kFinalizeThreads) camera_reduce_kernel(WsView v, uint32_t mask) {
+  __shared__ float sh[32];
+  __shared__ float tot[13];
+  const SceneDev& S = v.scenes[blockIdx.x];
+  const int C = S.n_channels;
+  if (mask & PULSAR_GRAD_CAM) {
+    for (int k = 0; k < 13; ++k) {
+      float x = 0.0f;
+      for (int b = threadIdx.x; b < S.fin_blocks; b += blockDim.x)
+        x += v.fin_part[(size_t)(S.fin_block_begin + b) * kCamPartials + k];
+      if (k == 12) {
+        const int64_t nt = (int64_t)S.tiles_x * S.tiles_y;
+        for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) x += v.tile_kappa[S.tile_begin + t];
+      }
+      float r = block_sum(x, sh);
+      if (threadIdx.x == 0) tot[k] = r;
+    }
+  }
+  if (mask & PULSAR_GRAD_BG) {
+    const int64_t nt = (int64_t)S.tiles_x * S.tiles_y;
+    for (int c = 0; c < C; ++c) {
+      float x = 0.0f;
+      for (int64_t t = threadIdx.x; t < nt; t += blockDim.x)
+        x += v.tile_bg[(size_t)(S.tile_begin + t) * C + c];
+      float r = block_sum(x, sh);
+      if (threadIdx.x == 0) S.g_bg[c] = r;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && (mask & PULSAR_GRAD_CAM)) {
+    const float* a = S.cam + 3;
+    float a1[3] = {a[0], a[1], a[2]}, a2[3] = {a[3], a[4], a[5]};
+    float n1 = sqrtf(dot3(a1, a1));
+    float b1[3] = {a1[0] / n1, a1[1] / n1, a1[2] / n1};
+    float dt = dot3(b1, a2);
+    float u[3] = {a2[0] - dt * b1[0], a2[1] - dt * b1[1], a2[2] - dt * b1[2]};
+    float n2 = sqrtf(dot3(u, u));
+    float b2[3] = {u[0] / n2, u[1] / n2, u[2] / n2};
+    float gB1[3] = {tot[0], tot[1], tot[2]};
+    float gB2[3] = {tot[3], tot[4], tot[5]};
+    float gB3[3] = {tot[6], tot[7], tot[8]};
+    // b3 = b1 x b2
+    float gb1[3], gb2[3], t3[3];
+    cross3(b2, gB3, t3);
+    for (int k = 0; k < 3; ++k) gb1[k] = gB1[k] + t3[k];
+    cross3(gB3, b1, t3);
+    for (int k = 0; k < 3; ++k) gb2[k] = gB2[k] + t3[k];
+    // b2 = u / |u|
+    float pb = dot3(b2, gb2);
+    float gu[3];
+    for (int k = 0; k < 3; ++k) gu[k] = (gb2[k] - b2[k] * pb) / n2;
+    // u = a2 - (b1.a2) b1
+    float ub = dot3(b1, gu);
+    float ga2[3];
+    for (int k = 0; k < 3; ++k) {
+      ga2[k] = gu[k] - b1[k] * ub;
+      gb1[k] += -a2[k] * ub - dt * gu[k];
+    }
+    // b1 = a1 / |a1|
+    float pa = dot3(b1, gb1);
+    float ga1[3];
+    for (int k = 0; k < 3; ++k) ga1[k] = (gb1[k] - b1[k] * pa) / n1;
+    float* out = S.g_cam;
+    out[0] = tot[9]; out[1] = tot[10]; out[2] = tot[11];
+    out[3] = ga1[0]; out[4] = ga1[1]; out[5] = ga1[2];
+    out[6] = ga2[0]; out[7] = ga2[1]; out[8] = ga2[2];
+    const float f = S.cam[9];
+    out[9] = -tot[12] * S.kappa / f;
+    out[10] = tot[12] / ((float)S.width * f);
+  }
+}
+
+template <int N>
+cudaError_t setup_n(const WsView& v, const SceneDev* hs, int n, int full, cudaStream_t st) {
+  SetupPack<N> pk;
+  pk.n = n;
+  pk.full = full;
+  pk.n_spheres = v.n_spheres;
+  for (int i = 0; i < n; ++i) pk.s[i] = hs[i];
+  setup_kernel<N><<<1, N < 32 ? 32 : N, 0, st>>>(v, pk);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_setup(const WsView& v, const SceneDev* hs, int n, cudaStream_t st) {
+  // the sign of n selects the mode: n > 0 full set-up, n < 0 pointer refresh
+  int full = n > 0 ? 1 : 0;
+  int m = n > 0 ? n : -n;
+  if (m <= 1) return setup_n<1>(v, hs, m, full, st);
+  if (m <= 8) return setup_n<8>(v, hs, m, full, st);
+  return setup_n<kMaxScenes>(v, hs, m, full, st);
+}
+
+cudaError_t launch_project(const WsView& v, cudaStream_t st) {
+  if (v.n_spheres == 0) return cudaSuccess;
+  const int64_t blocks = (v.n_spheres + kThreads - 1) / kThreads;
+  project_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const WsView& v, uint32_t mask, cudaStream_t st) {
+  if (v.fin_blocks > 0 && (mask & (PULSAR_GRAD_POS | PULSAR_GRAD_RAD | PULSAR_GRAD_CAM)))
+    finalize_kernel<<<v.fin_blocks, kFinalizeThreads, 0, st>>>(v, mask);
+  if (mask & (PULSAR_GRAD_CAM | PULSAR_GRAD_BG))
+    camera_reduce_kernel<<<v.n_scenes, kFinalizeThreads, 0, st>>>(v, mask);
+  return cudaGetLastError();
+}
+
+}  // namespace pulsar

@@ -1,0 +1,319 @@
+// Internal declarations of the GB300 sphere renderer: device structures,
+// workspace layout, and the float32 decision routines shared by the kernels.
+//
+// Decision routines (camera rows, projection, culling, rectangle, sort key,
+// hit predicate and hit depth) decide discrete outcomes: which tiles list a
+// sphere, in which order, and which hits a pixel tracks.  They are written as
+// fixed sequences of correctly rounded IEEE operations (__fadd_rn, __fmul_rn,
+// __fmaf_rn, __fdiv_rn, __fsqrt_rn), so the compiler cannot fuse or reorder
+// them and every launch decides identically.  The numeric value path (weights,
+// image, gradients) uses ordinary fast float32 arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pulsar.h"
+
+namespace pulsar {
+
+constexpr int kThreads = 256;        // threads per CTA for the per-tile kernels (16 x 16 pixels)
+constexpr int kTile = 16;            // tile edge in pixels
+constexpr int kChunk = 256;          // spheres staged in shared memory per round
+constexpr int kSortItems = 8;        // keys per thread in one radix-sort tile
+constexpr int kSortTile = kThreads * kSortItems;   // 2048 keys per radix-sort CTA
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxScenes = 64;
+constexpr int kFinalizeThreads = 256;
+constexpr int kCamPartials = 16;     // floats per finalize-block camera partial (13 used)
+
+// Per-scene description in the workspace.  The host fills the inputs; the
+// setup kernel derives the camera rows and pixel pitch.
+struct SceneDev {
+  // inputs
+  const float* pos;
+  const float* rad;
+  const float* opa;
+  const float* feat;
+  const float* cam;
+  const float* bg;
+  // forward outputs
+  float* image;
+  float* log_norm;
+  int32_t* n_hits;
+  int32_t* n_tests;
+  int32_t* tracked;
+  // backward inputs / outputs
+  const float* image_in;
+  const float* log_norm_in;
+  const float* grad_image;
+  float* g_pos;
+  float* g_rad;
+  float* g_opa;
+  float* g_feat;
+  float* g_cam;
+  float* g_bg;
+  // sizes
+  int32_t width, height, n_spheres, n_channels, n_track;
+  uint32_t flags;
+  int32_t tiles_x, tiles_y;
+  int64_t sphere_begin;      // first global sphere index of this scene
+  int64_t tile_begin;        // first global tile index
+  int64_t pixel_begin;       // first global pixel index
+  int32_t fin_block_begin;   // first finalize block
+  int32_t fin_blocks;
+  float gamma, eps, znear, zfar;
+  // derived on the device by the setup kernel
+  double rows64[9];          // camera axes in double (value path)
+  double kappa64;            // pixel pitch in double (value path)
+  float rows[9];             // camera axes b1, b2, b3 (world -> camera rows), float32 decisions
+  float kappa;               // pixel pitch on the unit image plane, s / (W f), float32 decisions
+  float kappa_hi, kappa_lo;  // kappa64 split into two floats (value path)
+  uint32_t omax_bits;        // max |o| over visible spheres, float bits
+  uint32_t pad_;             // unused
+};
+
+// Device-side counters and flags at the start of the workspace.
+struct WsHeader {
+  int32_t n_scenes;
+  int32_t overflow;          // 1 when the pair count exceeded list_capacity
+  int64_t pairs_needed;      // pair count the last binning required
+  int32_t n_pairs;           // pairs in the lists (0 after an overflow)
+  int32_t n_sort;            // keys in the sphere sort (= total spheres)
+  int32_t timeout;           // a bounded device loop gave up
+  int32_t pad_[9];
+};
+
+// Raw pointers into one workspace, passed to kernels by value.
+struct WsView {
+  WsHeader* hdr;
+  SceneDev* scenes;
+  int32_t n_scenes;
+  int64_t n_spheres;         // total over scenes
+  int64_t n_tiles;           // total over scenes
+  int64_t n_pixels;          // total over scenes
+  int64_t capacity;          // pair capacity
+  int32_t sort_blocks;       // radix-sort CTAs covering max(n_spheres, capacity)
+  int32_t fin_blocks;        // finalize CTAs over all scenes
+  int32_t n_channels;        // common feature length of the batch
+  int32_t n_track;           // common n_track of the batch
+  int32_t pair_buf;          // ping-pong buffer holding the tile-sorted pairs
+  float4* rec0;              // per sphere: c.x, c.y, c.z, R^2
+  float4* rec1;              // per sphere: key, o, x-range (x0 | x1 << 16), y-range
+  float4* rec2;              // per sphere: c - c.xyz (low-order part of the double centre), R
+  uint32_t* key[2];          // radix sort keys (ping-pong)
+  uint32_t* val[2];          // radix sort values (ping-pong)
+  uint32_t* hist;            // radix histograms [kRadix][sort_blocks]
+  uint32_t* block_sums;      // scan partials [sort_blocks]
+  uint32_t* pkey[2];         // pair tile ids (ping-pong)
+  uint32_t* pval[2];         // pair sphere ids (ping-pong)
+  int2* ranges;              // per tile [begin, end)
+  float* tile_kappa;         // per tile d L / d kappa partial
+  float* tile_bg;            // per tile x C background-gradient partial
+  float2* thr;               // per pixel (t_K, bits of id_K) of the K-th tracked hit
+  float4* gacc;              // per sphere: dL/dc (3), dL/dR
+  float* fin_part;           // per finalize block: camera partials
+};
+
+// ----------------------------------------------------------------------------
+// float32 decision routines
+// ----------------------------------------------------------------------------
+
+__device__ __forceinline__ void rows_from_rot6(const float* a, float* B) {
+  float n1 = __fsqrt_rn(__fmaf_rn(a[0], a[0], __fmaf_rn(a[1], a[1], __fmul_rn(a[2], a[2]))));
+  float b1x = __fdiv_rn(a[0], n1), b1y = __fdiv_rn(a[1], n1), b1z = __fdiv_rn(a[2], n1);
+  float dt = __fmaf_rn(b1x, a[3], __fmaf_rn(b1y, a[4], __fmul_rn(b1z, a[5])));
+  float ux = __fmaf_rn(-dt, b1x, a[3]);
+  float uy = __fmaf_rn(-dt, b1y, a[4]);
+  float uz = __fmaf_rn(-dt, b1z, a[5]);
+  float n2 = __fsqrt_rn(__fmaf_rn(ux, ux, __fmaf_rn(uy, uy, __fmul_rn(uz, uz))));
+  float b2x = __fdiv_rn(ux, n2), b2y = __fdiv_rn(uy, n2), b2z = __fdiv_rn(uz, n2);
+  B[0] = b1x; B[1] = b1y; B[2] = b1z;
+  B[3] = b2x; B[4] = b2y; B[5] = b2z;
+  B[6] = __fmaf_rn(b1y, b2z, -__fmul_rn(b1z, b2y));
+  B[7] = __fmaf_rn(b1z, b2x, -__fmul_rn(b1x, b2z));
+  B[8] = __fmaf_rn(b1x, b2y, -__fmul_rn(b1y, b2x));
+}
+
+__device__ __forceinline__ float pixel_pitch(const float* cam, int width) {
+  return __fdiv_rn(cam[10], __fmul_rn((float)width, cam[9]));
+}
+
+struct Projected {
+  float cx, cy, cz, R, R2, key;
+  bool visible;
+  int x0, x1, y0, y1;
+};
+
+// One axis of the enclosing rectangle: the tangent slopes of the (axis, z)
+// disk seen from the eye, converted to pixel indices and widened by one pixel.
+__device__ __forceinline__ void axis_range(float cx, float cz, float R, float R2, float kappa,
+                                           int n, int& lo, int& hi) {
+  float den = __fmaf_rn(cz, cz, -R2);
+  float disc = __fmaf_rn(cx, cx, den);
+  float root = __fsqrt_rn(disc);
+  float base = __fmul_rn(cx, cz);
+  float rs = __fmul_rn(R, root);
+  float mlo = __fdiv_rn(__fsub_rn(base, rs), den);
+  float mhi = __fdiv_rn(__fadd_rn(base, rs), den);
+  float half = __fmul_rn((float)(n - 1), 0.5f);
+  float flo = __fadd_rn(__fdiv_rn(mlo, kappa), half);
+  float fhi = __fadd_rn(__fdiv_rn(mhi, kappa), half);
+  flo = fmaxf(fminf(flo, (float)n + 2.0f), -4.0f);
+  fhi = fmaxf(fminf(fhi, (float)n + 2.0f), -4.0f);
+  lo = (int)ceilf(flo) - 1;
+  hi = (int)floorf(fhi) + 1;
+}
+
+// Step 0 for one sphere: camera-space centre, effective radius (one-pixel
+// minimum size), culling, rectangle and sort key.
+__device__ __forceinline__ Projected project_sphere(const float* B, const float* cam, float kappa,
+                                                    float px, float py, float pz, float r,
+                                                    int width, int height, float znear, float zfar,
+                                                    bool min_size) {
+  Projected o;
+  float dx = __fsub_rn(px, cam[0]), dy = __fsub_rn(py, cam[1]), dz = __fsub_rn(pz, cam[2]);
+  o.cx = __fmaf_rn(B[0], dx, __fmaf_rn(B[1], dy, __fmul_rn(B[2], dz)));
+  o.cy = __fmaf_rn(B[3], dx, __fmaf_rn(B[4], dy, __fmul_rn(B[5], dz)));
+  o.cz = __fmaf_rn(B[6], dx, __fmaf_rn(B[7], dy, __fmul_rn(B[8], dz)));
+  float R = r;
+  if (min_size) {
+    float cn = __fsqrt_rn(__fmaf_rn(o.cx, o.cx, __fmaf_rn(o.cy, o.cy, __fmul_rn(o.cz, o.cz))));
+    float rmin = __fmul_rn(0.75f, __fmul_rn(cn, kappa));
+    if (rmin > r) R = rmin;
+  }
+  o.R = R;
+  o.R2 = __fmul_rn(R, R);
+  o.key = __int_as_float(0x7f800000);
+  o.visible = false;
+  o.x0 = o.x1 = o.y0 = o.y1 = -1;
+  float key = __fsub_rn(o.cz, R);
+  if (!(R > 0.0f) || !(key > znear) || !(key < zfar)) return o;
+  int x0, x1, y0, y1;
+  axis_range(o.cx, o.cz, R, o.R2, kappa, width, x0, x1);
+  axis_range(o.cy, o.cz, R, o.R2, kappa, height, y0, y1);
+  if (x1 < 0 || x0 > width - 1 || y1 < 0 || y0 > height - 1) return o;
+  o.x0 = max(x0, 0);
+  o.x1 = min(x1, width - 1);
+  o.y0 = max(y0, 0);
+  o.y1 = min(y1, height - 1);
+  o.key = key;
+  o.visible = true;
+  return o;
+}
+
+__device__ __forceinline__ float ray_coord(int u, int n, float kappa) {
+  return __fmul_rn(__fmul_rn((float)(2 * u + 1 - n), 0.5f), kappa);
+}
+
+// Intermediate values of the hit test that the value path reuses.
+struct RayHit {
+  float ex, ey, ez;   // components of (c x r) up to order and sign
+  float cr2;          // |c x r|^2
+  float rr;           // |r|^2
+  float sq;           // sqrt(rr R^2 - |c x r|^2)
+  float off;          // c_z - t_h
+  float t;            // front-hit depth (camera z)
+};
+
+// Hit predicate of the ray (rx, ry, 1) and the sphere record (c, R^2); the
+// hit depth is never taken nearer than tmin = c_z - R (the sort key).
+__device__ __forceinline__ bool ray_hit(float cx, float cy, float cz, float R2, float tmin,
+                                        float rx, float ry, float zfar, RayHit& h) {
+  h.ex = __fmaf_rn(cz, rx, -cx);
+  h.ey = __fmaf_rn(cz, ry, -cy);
+  h.ez = __fmaf_rn(cx, ry, -__fmul_rn(cy, rx));
+  h.cr2 = __fmaf_rn(h.ex, h.ex, __fmaf_rn(h.ey, h.ey, __fmul_rn(h.ez, h.ez)));
+  h.rr = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, 1.0f));
+  float disc = __fmaf_rn(h.rr, R2, -h.cr2);
+  if (!(disc > 0.0f)) return false;
+  h.sq = __fsqrt_rn(disc);
+  h.off = __fdiv_rn(__fmaf_rn(rx, h.ex, __fmaf_rn(ry, h.ey, h.sq)), h.rr);
+  h.t = fmaxf(__fsub_rn(cz, h.off), tmin);
+  return h.t < zfar;
+}
+
+// Value-path ray: the slopes (u + 1/2 - W/2) kappa as hi + lo float pairs.
+struct ValueRay {
+  float rx, rx_lo, ry, ry_lo;
+};
+
+__device__ __forceinline__ ValueRay value_ray(int u, int v, int width, int height, float k_hi,
+                                              float k_lo) {
+  ValueRay r;
+  const float px = (float)(2 * u + 1 - width) * 0.5f;
+  const float py = (float)(2 * v + 1 - height) * 0.5f;
+  r.rx = px * k_hi;
+  r.rx_lo = fmaf(px, k_hi, -r.rx) + px * k_lo;
+  r.ry = py * k_hi;
+  r.ry_lo = fmaf(py, k_hi, -r.ry) + py * k_lo;
+  return r;
+}
+
+// Value-path geometry of a hit.  c = c_hi + c_lo (rec0.xyz + rec2.xyz) and
+// the ray slopes are carried as float pairs, and the ray-to-centre offsets
+// e = c_z r - c are formed with one rounding of the (cancelling) leading
+// terms, so dist, the hit depth and z keep about float precision relative to
+// the sphere radius even where |c| is large.
+struct ValueGeom {
+  float ex, ey, ez;   // c x r = (-ey, ex, ez)
+  float cr2, rr, sq, off, dist;
+};
+
+__device__ __forceinline__ ValueGeom value_geom(const float4& a, const float4& c2, const ValueRay& r) {
+  ValueGeom g;
+  g.ex = fmaf(a.z, r.rx, -a.x) + fmaf(a.z, r.rx_lo, fmaf(c2.z, r.rx, -c2.x));
+  g.ey = fmaf(a.z, r.ry, -a.y) + fmaf(a.z, r.ry_lo, fmaf(c2.z, r.ry, -c2.y));
+  g.ez = (a.x * g.ey - a.y * g.ex) / a.z;
+  g.cr2 = fmaf(g.ex, g.ex, fmaf(g.ey, g.ey, g.ez * g.ez));
+  g.rr = fmaf(r.rx, r.rx, fmaf(r.ry, r.ry, 1.0f));
+  const float R = c2.w;
+  g.sq = sqrtf(fmaxf(fmaf(g.rr, R * R, -g.cr2), 0.0f));
+  g.off = fmaf(r.rx, g.ex, fmaf(r.ry, g.ey, g.sq)) / g.rr;
+  g.dist = sqrtf(g.cr2 / g.rr);
+  return g;
+}
+
+__device__ __forceinline__ uint32_t pack_range(int lo, int hi) {
+  return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+// Scene owning a global index, given the per-scene begin offsets.
+__device__ __forceinline__ int scene_of_tile(const SceneDev* scenes, int n_scenes, int64_t tile) {
+  int s = 0;
+  for (int k = 1; k < n_scenes; ++k)
+    if (scenes[k].tile_begin <= tile) s = k;
+  return s;
+}
+
+__device__ __forceinline__ int scene_of_sphere(const SceneDev* scenes, int n_scenes, int64_t i) {
+  int s = 0;
+  for (int k = 1; k < n_scenes; ++k)
+    if (scenes[k].sphere_begin <= i) s = k;
+  return s;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ----------------------------------------------------------------------------
+// host-side launch helpers (defined in the .cu files)
+// ----------------------------------------------------------------------------
+
+struct SceneHost {
+  pulsar_params p;
+  pulsar_scene s;
+};
+
+cudaError_t launch_setup(const WsView& v, const SceneDev* host_scenes, int n, cudaStream_t st);
+cudaError_t launch_project(const WsView& v, cudaStream_t st);
+cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st);
+cudaError_t launch_render_fwd(const WsView& v, bool store, cudaStream_t st);
+cudaError_t launch_render_bwd(const WsView& v, bool store, uint32_t grad_mask, cudaStream_t st);
+cudaError_t launch_finalize(const WsView& v, uint32_t grad_mask, cudaStream_t st);
+
+}  // namespace pulsar

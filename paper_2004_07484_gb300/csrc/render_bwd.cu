@@ -1,0 +1,351 @@
+// Backward pass (App. B, "The Backward Pass"), parallel over pixels.
+//
+// A hit is tracked when its (depth, index) is at most the pixel's n_track-th
+// tracked hit.  That threshold comes from the forward pass (store mode, App. B
+// "Preparing for the Backward Pass") or is recomputed here by the forward's
+// traversal without blending (recompute mode).  The gradient pass then walks
+// the tile's list again; all lanes of a warp visit the same sphere at the same
+// time, so each sphere's per-pixel contributions are summed across the warp
+// with shuffles before one set of (vector) atomics per warp and sphere.  The
+// walk stops at the first key beyond every pixel's threshold.
+//
+// Derivatives (Eq. 1 with a = o d e^{o z / gamma}, D its denominator, G = dL/dF):
+//   dL/df_i = w_i G,   dL/da_i = G.(f_i - F) / D,
+//   da/do = d e^s (1 + s),  da/dd = o e^s,  da/dz = a o / gamma,  s = o z / gamma,
+//   z = (zfar - t) / (zfar - znear),
+//   t = t_c - sqrt(disc)/|r|^2 (front root), dist = |e|, e = c - t_c r,
+//   dt/dc = r/|r|^2 + e/sqrt(disc),  dt/dR = -R/sqrt(disc),
+//   dt/dr = (e (1 - b/sqrt(disc)) - t r)/|r|^2,  b = r.c,
+//   ddist/dc = e/dist,  ddist/dr = -t_c e/dist.
+// Ray slopes depend on the pixel pitch kappa: dr/dkappa = (u + 1/2 - W/2, v + 1/2 - H/2, 0).
+#include "render_common.cuh"
+
+namespace pulsar {
+
+namespace {
+
+template <int CMAX>
+__device__ __forceinline__ void warp_reduce_and_add(bool tracked, int id_global, int64_t id_local,
+                                                    float gc0, float gc1, float gc2, float gR,
+                                                    float go, const float (&gf)[CMAX], int C,
+                                                    const WsView& v, const SceneDev& S, bool geo,
+                                                    bool opa, bool feat) {
+  const unsigned bal = __ballot_sync(0xffffffffu, tracked);
+  if (bal == 0u) return;
+  const int lane = threadIdx.x & 31;
+  if (__popc(bal) == 1) {
+    if (!tracked) return;
+    if (geo) atomicAdd(&v.gacc[id_global], make_float4(gc0, gc1, gc2, gR));
+    if (opa) atomicAdd(S.g_opa + id_local, go);
+    if (feat) {
+      float* dst = S.g_feat + id_local * C;
+      if ((C & 3) == 0) {
+#pragma unroll
+        for (int c = 0; c < CMAX; c += 4)
+          if (c < C) atomicAdd(reinterpret_cast<float4*>(dst + c), make_float4(gf[c], gf[c + 1], gf[c + 2], gf[c + 3]));
+      } else {
+#pragma unroll
+        for (int c = 0; c < CMAX; ++c)
+          if (c < C) atomicAdd(dst + c, gf[c]);
+      }
+    }
+    return;
+  }
+  // several lanes hit this sphere: butterfly sums (all lanes take part)
+  float r0 = gc0, r1 = gc1, r2 = gc2, r3 = gR, r4 = go;
+  float rf[CMAX];
+#pragma unroll
+  for (int c = 0; c < CMAX; ++c) rf[c] = gf[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    if (geo) {
+      r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+      r1 += __shfl_xor_sync(0xffffffffu, r1, o);
+      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+      r3 += __shfl_xor_sync(0xffffffffu, r3, o);
+    }
+    if (opa) r4 += __shfl_xor_sync(0xffffffffu, r4, o);
+    if (feat) {
+#pragma unroll
+      for (int c = 0; c < CMAX; ++c)
+        if (c < C) rf[c] += __shfl_xor_sync(0xffffffffu, rf[c], o);
+    }
+  }
+  if (lane != __ffs(bal) - 1) return;
+  if (geo) atomicAdd(&v.gacc[id_global], make_float4(r0, r1, r2, r3));
+  if (opa) atomicAdd(S.g_opa + id_local, r4);
+  if (feat) {
+    float* dst = S.g_feat + id_local * C;
+    if ((C & 3) == 0) {
+#pragma unroll
+      for (int c = 0; c < CMAX; c += 4)
+        if (c < C) atomicAdd(reinterpret_cast<float4*>(dst + c), make_float4(rf[c], rf[c + 1], rf[c + 2], rf[c + 3]));
+    } else {
+#pragma unroll
+      for (int c = 0; c < CMAX; ++c)
+        if (c < C) atomicAdd(dst + c, rf[c]);
+    }
+  }
+}
+
+template <int KMAX, int CMAX>
+__global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
+                                                                 const uint32_t* __restrict__ list,
+                                                                 int store, uint32_t mask) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ChunkSmem<CMAX>& sm = *reinterpret_cast<ChunkSmem<CMAX>*>(smem_raw);
+  __shared__ float red[kThreads / 32][CMAX + 1];
+  const int64_t tile = blockIdx.x;
+  const int si = scene_of_tile(v.scenes, v.n_scenes, tile);
+  const SceneDev& S = v.scenes[si];
+  const PixelCtx pc = pixel_ctx(S, tile);
+  const int2 rg = v.ranges[tile];
+  const int C = S.n_channels;
+  const int K = S.n_track;
+  const float gamma = S.gamma, zfar = S.zfar, znear = S.znear;
+  const float inv_gamma = 1.0f / gamma;
+  const float inv_range = 1.0f / (zfar - znear);
+  const bool literal = (S.flags & PULSAR_FLAG_DIST_LITERAL) != 0;
+  const bool geo = (mask & (PULSAR_GRAD_POS | PULSAR_GRAD_RAD | PULSAR_GRAD_CAM)) != 0;
+  const bool opa = (mask & PULSAR_GRAD_OPA) != 0;
+  const bool feat = (mask & PULSAR_GRAD_FEAT) != 0;
+  const bool cam = (mask & PULSAR_GRAD_CAM) != 0;
+  const bool bgw = (mask & PULSAR_GRAD_BG) != 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  for (int e = threadIdx.x; e < kChunk * CMAX; e += kThreads) sm.feat[e] = 0.0f;
+
+  // per-pixel upstream data
+  const int64_t pix = pc.inside ? (int64_t)pc.py * S.width + pc.px : 0;
+  float G[CMAX];
+  float GF = 0.0f, logD = 0.0f;
+#pragma unroll
+  for (int c = 0; c < CMAX; ++c) G[c] = 0.0f;
+  if (pc.inside) {
+    const float* g = S.grad_image + pix * C;
+    const float* F = S.image_in + pix * C;
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c)
+      if (c < C) {
+        G[c] = g[c];
+        GF = fmaf(G[c], F[c], GF);
+      }
+    logD = S.log_norm_in[pix];
+  }
+
+  // background gradient: sum over the tile of w_B G
+  if (bgw) {
+    const float wB = pc.inside ? __expf(S.eps * inv_gamma - logD) : 0.0f;
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c) {
+      float x = warp_sum(wB * G[c]);
+      if (lane == 0 && c < C) red[warp][c] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < C) {
+      float s = 0.0f;
+      for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
+      v.tile_bg[(size_t)tile * C + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+  if (!(geo || opa || feat)) {
+    if (cam && threadIdx.x == 0) v.tile_kappa[tile] = 0.0f;
+    return;
+  }
+
+  // threshold of the tracked set
+  float thr_t = __int_as_float(0x7f800000);
+  int thr_i = 0x7fffffff;
+  if (store) {
+    if (pc.inside) {
+      const float2 th = v.thr[S.pixel_begin + pix];
+      thr_t = th.x;
+      thr_i = __float_as_int(th.y);
+    }
+  } else {
+    float qt[KMAX];
+    int qi[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      qt[k] = __int_as_float(0x7f800000);
+      qi[k] = 0x7fffffff;
+    }
+    bool done = !pc.inside;
+    float kstop = __int_as_float(0x7f800000);
+    for (int base = rg.x; base < rg.y; base += kChunk) {
+      const int n = min(kChunk, rg.y - base);
+      const int cnt = stage_chunk<CMAX>(sm, v, S, list, base, n, pc, false);
+      for (int k = 0; k < cnt; ++k) {
+        if (__all_sync(0xffffffffu, done)) break;
+        const int j = sm.list[warp][k];
+        const float4 a = sm.rec0[j];
+        const float4 b = sm.rec1[j];
+        if (done) continue;
+        if (b.x >= kstop) {
+          done = true;
+          continue;
+        }
+        if (!in_rect(b, pc.px, pc.py)) continue;
+        RayHit h;
+        if (!ray_hit(a.x, a.y, a.z, a.w, b.x, pc.rx, pc.ry, zfar, h)) continue;
+        const int id = sm.id[j];
+        if (hit_less(h.t, id, thr_t, thr_i)) {
+          queue_insert<KMAX>(qt, qi, h.t, id);
+          queue_select<KMAX>(qt, qi, K, thr_t, thr_i);
+          kstop = next_up(thr_t);
+        }
+      }
+      if (__syncthreads_and(done)) break;
+    }
+  }
+
+  // gradient pass
+  const float pxo = (float)(2 * pc.px + 1 - S.width) * 0.5f;
+  const float pyo = (float)(2 * pc.py + 1 - S.height) * 0.5f;
+  const float kstop = next_up(thr_t);
+  bool done = !pc.inside;
+  float gk_sum = 0.0f;
+  for (int base = rg.x; base < rg.y; base += kChunk) {
+    const int n = min(kChunk, rg.y - base);
+    const int cnt = stage_chunk<CMAX>(sm, v, S, list, base, n, pc, true);
+    for (int k = 0; k < cnt; ++k) {
+      if (__all_sync(0xffffffffu, done)) break;
+      const int j = sm.list[warp][k];
+      const float4 a = sm.rec0[j];
+      const float4 b = sm.rec1[j];
+      const int id = sm.id[j];
+      bool tracked = false;
+      float gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, gR = 0.f, go = 0.f;
+      float gf[CMAX];
+#pragma unroll
+      for (int c = 0; c < CMAX; ++c) gf[c] = 0.0f;
+      if (!done) {
+        if (b.x >= kstop) {
+          done = true;
+        } else if (in_rect(b, pc.px, pc.py)) {
+          RayHit h;
+          if (ray_hit(a.x, a.y, a.z, a.w, b.x, pc.rx, pc.ry, zfar, h) &&
+              !hit_less(thr_t, thr_i, h.t, id)) {
+            tracked = true;
+            const float4 c2 = sm.rec2[j];
+            const ValueGeom g = value_geom(a, c2, pc.vr);
+            const float R = c2.w;
+            const float inv_rr = 1.0f / g.rr;
+            const float dist = g.dist;
+            const float qd = dist / R;
+            const float qdc = fminf(qd, 1.0f);
+            const float d = literal ? qdc : 1.0f - qdc;
+            const float z = (((zfar - a.z) - c2.z) + g.off) * inv_range;
+            const float t_val = (a.z - g.off) + c2.z;
+            const float o = b.y;
+            const float s = o * z * inv_gamma;
+            // e^{s} / D; the clamp only matters for zero-weight hits, whose
+            // exponent may exceed log D by any amount
+            const float E = __expf(fminf(s - logD, 80.0f));
+            const float w = o * d * E;
+            const float* f = &sm.feat[j * CMAX];
+            float gdot = -GF;
+#pragma unroll
+            for (int c = 0; c < CMAX; ++c) gdot = fmaf(G[c], f[c], gdot);
+#pragma unroll
+            for (int c = 0; c < CMAX; ++c) gf[c] = w * G[c];
+            go = gdot * d * E * (1.0f + s);
+            const float gd = gdot * o * E;
+            const float gz = gdot * w * o * inv_gamma;
+            const float gt = -gz * inv_range;
+            float gdist = 0.0f;
+            if (qd < 1.0f) {
+              const float sgn = literal ? 1.0f : -1.0f;
+              gdist = sgn * gd / R;
+              gR = -sgn * gd * qd / R;
+            }
+            // e = (r x (c x r)) / |r|^2 with c x r = (-ey, ex, ez)
+            const float rx = pc.vr.rx, ry = pc.vr.ry;
+            const float e0 = (ry * g.ez - g.ex) * inv_rr;
+            const float e1 = (-g.ey - rx * g.ez) * inv_rr;
+            const float e2 = (rx * g.ex + ry * g.ey) * inv_rr;
+            // gt / sqrt(disc): the depth derivatives carry 1/sqrt(disc), which
+            // diverges at the rim, while gt carries d.  With d = 1 - dist/R,
+            // d / sqrt(disc) = sqrt(disc) / (|r|^2 R (R + dist)) exactly, so
+            // the product is formed without dividing by a vanishing sqrt(disc)
+            // (d itself has a float32 floor of ~1e-7 there).  With the
+            // literal d the product diverges in exact arithmetic too.
+            float gt_sq;
+            if (literal) {
+              gt_sq = g.sq > 0.0f ? gt / g.sq : 0.0f;
+            } else {
+              const float d_over_sq = g.sq * inv_rr / (R * (R + dist));
+              gt_sq = -gdot * o * E * o * inv_gamma * inv_range * d_over_sq;
+            }
+            const float tc = t_val + g.sq * inv_rr;   // closest-approach parameter
+            const float b_ = tc * g.rr;               // r . c
+            gc0 = gt * rx * inv_rr + gt_sq * e0;
+            gc1 = gt * ry * inv_rr + gt_sq * e1;
+            gc2 = gt * inv_rr + gt_sq * e2;
+            gR += -R * gt_sq;
+            float grx = (gt * e0 - gt_sq * b_ * e0 - gt * t_val * rx) * inv_rr;
+            float gry = (gt * e1 - gt_sq * b_ * e1 - gt * t_val * ry) * inv_rr;
+            if (dist > 0.0f) {
+              const float gi = gdist / dist;
+              gc0 += gi * e0;
+              gc1 += gi * e1;
+              gc2 += gi * e2;
+              grx += -gi * tc * e0;
+              gry += -gi * tc * e1;
+            }
+            gk_sum += grx * pxo + gry * pyo;
+          }
+        }
+      }
+      warp_reduce_and_add<CMAX>(tracked, id, (int64_t)id - S.sphere_begin, gc0, gc1, gc2, gR, go,
+                                gf, C, v, S, geo, opa, feat);
+    }
+    if (__syncthreads_and(done)) break;
+  }
+  if (cam) {
+    const float x = warp_sum(gk_sum);
+    __syncthreads();
+    if (lane == 0) red[warp][0] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float s = 0.0f;
+      for (int w = 0; w < kThreads / 32; ++w) s += red[w][0];
+      v.tile_kappa[tile] = s;
+    }
+  }
+}
+
+template <int KMAX, int CMAX>
+cudaError_t launch_bwd_t(const WsView& v, const uint32_t* list, bool store, uint32_t mask,
+                         cudaStream_t st) {
+  const size_t smem = sizeof(ChunkSmem<CMAX>);
+  auto kern = render_bwd_kernel<KMAX, CMAX>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)v.n_tiles, kThreads, smem, st>>>(v, list, store ? 1 : 0, mask);
+  return cudaGetLastError();
+}
+
+template <int KMAX>
+cudaError_t launch_bwd_k(const WsView& v, const uint32_t* list, bool store, uint32_t mask,
+                         cudaStream_t st) {
+  const int C = v.n_channels;
+  if (C <= 4) return launch_bwd_t<KMAX, 4>(v, list, store, mask, st);
+  if (C <= 8) return launch_bwd_t<KMAX, 8>(v, list, store, mask, st);
+  if (C <= 16) return launch_bwd_t<KMAX, 16>(v, list, store, mask, st);
+  return launch_bwd_t<KMAX, 32>(v, list, store, mask, st);
+}
+
+}  // namespace
+
+cudaError_t launch_render_bwd(const WsView& v, bool store, uint32_t mask, cudaStream_t st) {
+  if (v.n_tiles == 0) return cudaSuccess;
+  const uint32_t* list = v.pval[v.pair_buf];
+  const int K = v.n_track;
+  if (K <= 8) return launch_bwd_k<8>(v, list, store, mask, st);
+  if (K <= 16) return launch_bwd_k<16>(v, list, store, mask, st);
+  return launch_bwd_k<32>(v, list, store, mask, st);
+}
+
+}  // namespace pulsar

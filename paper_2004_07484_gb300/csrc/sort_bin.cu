@@ -1,0 +1,339 @@
+// Binning (App. B, Step 0 sort and Step 1 region culling, re-designed):
+//   1. stable LSD radix sort of (earliest depth, sphere index),
+//   2. exclusive scan of each sorted sphere's tile count,
+//   3. emission of one (tile, sphere) pair per overlapped tile, in depth order,
+//   4. stable LSD radix sort of the pairs by tile,
+//   5. per-tile [begin, end) ranges.
+// A stable sort of pairs that arrive in depth order keeps every tile's list in
+// (earliest depth, index) order, the order the paper's intersection search
+// relies on for early termination (Sec. 3.2, App. B Step 0).
+#include "pulsar_internal.cuh"
+
+namespace pulsar {
+
+namespace {
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ int read_count(const int32_t* n_dev, int n_host) {
+  return n_dev ? *n_dev : n_host;
+}
+
+// Per-CTA digit histogram of one radix pass (warp-aggregated shared atomics).
+__global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __restrict__ keys,
+                                                          const int32_t* n_dev, int n_host, int shift,
+                                                          uint32_t mask, uint32_t* __restrict__ hist,
+                                                          int stride) {
+  __shared__ uint32_t h[kRadix];
+  const int n = read_count(n_dev, n_host);
+  const int base = blockIdx.x * kSortTile;
+  if (base >= n) return;
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    int idx = base + warp * (kSortItems * 32) + k * 32 + lane;
+    bool valid = idx < n;
+    uint32_t d = valid ? (keys[idx] >> shift) & mask : 0xffffffffu;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  hist[threadIdx.x * stride + blockIdx.x] = h[threadIdx.x];
+}
+
+// Block-wide exclusive scan of one value per thread (kThreads or 1024 threads).
+template <int NT>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot,
+                                                         uint32_t& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < NT / 32 ? warp_tot[lane] : 0;
+    uint32_t s = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < NT / 32) warp_tot[lane] = s - w;
+    if (lane == NT / 32 - 1) warp_tot[32] = s;
+  }
+  __syncthreads();
+  uint32_t r = warp_tot[warp] + x - v;
+  total = warp_tot[32];
+  __syncthreads();
+  return r;
+}
+
+// Exclusive scan, in place, of rows x cols entries stored at data[r * stride + c],
+// in row-major logical order; cols = ceil(n / kSortTile).  One CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) scan_table(uint32_t* __restrict__ data, int rows,
+                                                   const int32_t* n_dev, int n_host, int stride) {
+  __shared__ uint32_t warp_tot[33];
+  const int n = read_count(n_dev, n_host);
+  const int cols = (n + kSortTile - 1) / kSortTile;
+  const int total = rows * cols;
+  if (total == 0) return;
+  const int per = (total + 1023) / 1024;
+  const int beg = threadIdx.x * per;
+  const int end = min(beg + per, total);
+  uint32_t s = 0;
+  for (int e = beg; e < end; ++e) {
+    int r = e / cols, c = e - r * cols;
+    s += data[r * stride + c];
+  }
+  uint32_t tot;
+  uint32_t run = block_exclusive_scan<1024>(s, warp_tot, tot);
+  for (int e = beg; e < end; ++e) {
+    int r = e / cols, c = e - r * cols;
+    uint32_t x = data[r * stride + c];
+    data[r * stride + c] = run;
+    run += x;
+  }
+}
+
+// Stable scatter of one radix pass.  Keys are ranked within each warp with
+// match.any in index order; warps are combined in warp order; items are first
+// placed in shared memory in their CTA-local sorted order and then written out
+// in coalesced runs per digit.
+__global__ void __launch_bounds__(kThreads) radix_downsweep(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int32_t* n_dev,
+    int n_host, int shift, uint32_t mask, const uint32_t* __restrict__ hist, int stride) {
+  __shared__ uint32_t s_keys[kSortTile];
+  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t warp_cnt[kThreads / 32][kRadix];
+  __shared__ uint32_t digit_local[kRadix];
+  __shared__ uint32_t digit_global[kRadix];
+  __shared__ uint32_t warp_tot[33];
+  const int n = read_count(n_dev, n_host);
+  const int base = blockIdx.x * kSortTile;
+  if (base >= n) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int w = 0; w < kThreads / 32; ++w) warp_cnt[w][threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t k_reg[kSortItems], v_reg[kSortItems], rank[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    int idx = base + warp * (kSortItems * 32) + k * 32 + lane;
+    bool valid = idx < n;
+    k_reg[k] = valid ? keys_in[idx] : 0u;
+    v_reg[k] = valid ? vals_in[idx] : 0u;
+    uint32_t d = valid ? (k_reg[k] >> shift) & mask : 0xffffffffu;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = 0;
+    if (valid) before = warp_cnt[warp][d];
+    rank[k] = before + __popc(peers & lanemask_lt());
+    __syncwarp();
+    if (valid && (peers & lanemask_lt()) == 0) warp_cnt[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: exclusive prefix over warps, then over digits
+  {
+    const int d = threadIdx.x;
+    uint32_t tot = 0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      uint32_t c = warp_cnt[w][d];
+      warp_cnt[w][d] = tot;
+      tot += c;
+    }
+    uint32_t all;
+    uint32_t ex = block_exclusive_scan<kThreads>(tot, warp_tot, all);
+    digit_local[d] = ex;
+    digit_global[d] = hist[d * stride + blockIdx.x];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    int idx = base + warp * (kSortItems * 32) + k * 32 + lane;
+    if (idx < n) {
+      uint32_t d = (k_reg[k] >> shift) & mask;
+      uint32_t pos = digit_local[d] + warp_cnt[warp][d] + rank[k];
+      s_keys[pos] = k_reg[k];
+      s_vals[pos] = v_reg[k];
+    }
+  }
+  __syncthreads();
+  const int count = min(kSortTile, n - base);
+  for (int lp = threadIdx.x; lp < count; lp += kThreads) {
+    uint32_t key = s_keys[lp];
+    uint32_t d = (key >> shift) & mask;
+    uint32_t out = digit_global[d] + (lp - digit_local[d]);
+    keys_out[out] = key;
+    vals_out[out] = s_vals[lp];
+  }
+}
+
+__device__ __forceinline__ uint32_t tile_count(const float4& r1, bool visible) {
+  if (!visible) return 0u;
+  uint32_t bx = __float_as_uint(r1.z), by = __float_as_uint(r1.w);
+  int tx0 = (int)(bx & 0xffffu) / kTile, tx1 = (int)(bx >> 16) / kTile;
+  int ty0 = (int)(by & 0xffffu) / kTile, ty1 = (int)(by >> 16) / kTile;
+  return (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+}
+
+// Sum of the tile counts of each 2048-key tile of the depth-sorted spheres.
+__global__ void __launch_bounds__(kThreads) count_reduce(WsView v) {
+  __shared__ uint32_t warp_tot[33];
+  const int n = (int)v.n_spheres;
+  const int base = blockIdx.x * kSortTile;
+  uint32_t s = 0;
+  for (int k = 0; k < kSortItems; ++k) {
+    int j = base + threadIdx.x * kSortItems + k;
+    if (j < n) {
+      uint32_t key = v.key[0][j];
+      bool visible = key != 0x7f800000u;
+      if (visible) s += tile_count(v.rec1[v.val[0][j]], true);
+    }
+  }
+  uint32_t tot;
+  block_exclusive_scan<kThreads>(s, warp_tot, tot);
+  if (threadIdx.x == 0) v.block_sums[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the block sums; records the pair total and the overflow flag.
+__global__ void __launch_bounds__(1024) count_scan(WsView v, int n_blocks) {
+  __shared__ uint32_t warp_tot[33];
+  __shared__ unsigned long long s_total;
+  if (threadIdx.x == 0) s_total = 0;
+  __syncthreads();
+  unsigned long long carry = 0;
+  for (int b0 = 0; b0 < n_blocks; b0 += 1024) {
+    int b = b0 + threadIdx.x;
+    uint32_t x = b < n_blocks ? v.block_sums[b] : 0u;
+    uint32_t tot;
+    uint32_t ex = block_exclusive_scan<1024>(x, warp_tot, tot);
+    if (b < n_blocks) v.block_sums[b] = (uint32_t)(carry + ex);
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    long long total = (long long)carry;
+    v.hdr->pairs_needed = total;
+    bool over = total > v.capacity;
+    v.hdr->overflow = over ? 1 : 0;
+    v.hdr->n_pairs = over ? 0 : (int32_t)total;
+  }
+}
+
+// Emits the (tile, sphere) pairs of each depth-sorted sphere at its scanned offset.
+__global__ void __launch_bounds__(kThreads) emit_pairs(WsView v) {
+  __shared__ uint32_t warp_tot[33];
+  const int n = (int)v.n_spheres;
+  if (v.hdr->overflow) return;
+  const int base = blockIdx.x * kSortTile;
+  uint32_t cnt[kSortItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    int j = base + threadIdx.x * kSortItems + k;
+    cnt[k] = 0;
+    if (j < n) {
+      uint32_t key = v.key[0][j];
+      if (key != 0x7f800000u) cnt[k] = tile_count(v.rec1[v.val[0][j]], true);
+    }
+    s += cnt[k];
+  }
+  uint32_t tot;
+  uint32_t off = block_exclusive_scan<kThreads>(s, warp_tot, tot) + v.block_sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    if (cnt[k] == 0) continue;
+    int j = base + threadIdx.x * kSortItems + k;
+    uint32_t i = v.val[0][j];
+    float4 r1 = v.rec1[i];
+    int sc = scene_of_sphere(v.scenes, v.n_scenes, i);
+    const SceneDev& S = v.scenes[sc];
+    uint32_t bx = __float_as_uint(r1.z), by = __float_as_uint(r1.w);
+    int tx0 = (int)(bx & 0xffffu) / kTile, tx1 = (int)(bx >> 16) / kTile;
+    int ty0 = (int)(by & 0xffffu) / kTile, ty1 = (int)(by >> 16) / kTile;
+    uint32_t tb = (uint32_t)S.tile_begin;
+    for (int ty = ty0; ty <= ty1; ++ty)
+      for (int tx = tx0; tx <= tx1; ++tx) {
+        v.pkey[0][off] = tb + (uint32_t)(ty * S.tiles_x + tx);
+        v.pval[0][off] = i;
+        ++off;
+      }
+  }
+}
+
+// Tile ranges from the tile-sorted pairs (ranges are zeroed beforehand).
+__global__ void __launch_bounds__(kThreads) tile_ranges(WsView v, int buf) {
+  const int n = v.hdr->n_pairs;
+  const uint32_t* keys = v.pkey[buf];
+  for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+    uint32_t t = keys[i];
+    if (i == 0 || keys[i - 1] != t) v.ranges[t].x = i;
+    if (i == n - 1 || keys[i + 1] != t) v.ranges[t].y = i + 1;
+  }
+}
+
+cudaError_t radix_sort(const WsView& v, uint32_t* keys[2], uint32_t* vals[2], const int32_t* n_dev,
+                       int n_host, int max_items, int bits, int& buf, cudaStream_t st) {
+  const int blocks = (max_items + kSortTile - 1) / kSortTile;
+  if (blocks == 0) return cudaSuccess;
+  for (int shift = 0; shift < bits; shift += kRadixBits) {
+    uint32_t mask = (uint32_t)((1u << min(kRadixBits, bits - shift)) - 1u);
+    radix_upsweep<<<blocks, kThreads, 0, st>>>(keys[buf], n_dev, n_host, shift, mask, v.hist,
+                                               v.sort_blocks);
+    scan_table<<<1, 1024, 0, st>>>(v.hist, kRadix, n_dev, n_host, v.sort_blocks);
+    radix_downsweep<<<blocks, kThreads, 0, st>>>(keys[buf], vals[buf], keys[buf ^ 1], vals[buf ^ 1],
+                                                 n_dev, n_host, shift, mask, v.hist, v.sort_blocks);
+    buf ^= 1;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Returns, through `tile_bits`, nothing; the pair buffer holding the final
+// order is recorded by the caller from the pass count.
+cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st) {
+  cudaError_t e;
+  const int M = (int)v.n_spheres;
+  // 1. spheres by earliest depth (float bits of positive keys sort as integers)
+  int buf = 0;
+  if (M > 0) {
+    uint32_t* k[2] = {v.key[0], v.key[1]};
+    uint32_t* val[2] = {v.val[0], v.val[1]};
+    e = radix_sort(v, k, val, nullptr, M, M, 32, buf, st);
+    if (e != cudaSuccess) return e;
+  }
+  // 32 bits = 4 passes: the result is back in buffer 0
+  const int nb = (M + kSortTile - 1) / kSortTile;
+  if (nb > 0) count_reduce<<<nb, kThreads, 0, st>>>(v);
+  count_scan<<<1, 1024, 0, st>>>(v, nb);
+  if (nb > 0) emit_pairs<<<nb, kThreads, 0, st>>>(v);
+  // 4. pairs by tile
+  int pbuf = 0;
+  if (v.capacity > 0) {
+    uint32_t* k[2] = {v.pkey[0], v.pkey[1]};
+    uint32_t* val[2] = {v.pval[0], v.pval[1]};
+    e = radix_sort(v, k, val, &v.hdr->n_pairs, 0, (int)v.capacity, tile_bits, pbuf, st);
+    if (e != cudaSuccess) return e;
+  }
+  // 5. ranges
+  e = cudaMemsetAsync(v.ranges, 0, sizeof(int2) * (size_t)v.n_tiles, st);
+  if (e != cudaSuccess) return e;
+  if (v.capacity > 0) {
+    const int64_t want = (v.capacity + kThreads - 1) / kThreads;
+    const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+    tile_ranges<<<blocks, kThreads, 0, st>>>(v, pbuf);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace pulsar

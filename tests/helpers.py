@@ -1,0 +1,103 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI
+and compare it with the oracle."""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_2004_07484_gb300.scenes import Scene
+
+GRAD_NAMES = ("pos", "rad", "opa", "feat", "cam", "bg")
+
+
+def to_dev(scene: Scene):
+    import torch
+    d = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k))).cuda()
+         for k in ("pos", "rad", "opa", "feat", "cam", "bg")}
+    return d
+
+
+def settings_of(scene: Scene, store=True, dist_literal=False, min_size=True, n_track=None):
+    from paper_2004_07484_gb300 import RenderSettings
+    return RenderSettings(scene.width, scene.height, scene.n_channels,
+                          n_track or scene.n_track, float(scene.gamma), float(scene.eps),
+                          float(scene.znear), float(scene.zfar), store, dist_literal, min_size)
+
+
+def gpu_forward(scene: Scene, store=True, dist_literal=False, min_size=True, capacity=None,
+                n_track=None, dev=None):
+    import torch
+    from paper_2004_07484_gb300 import forward_frame
+    dev = dev or to_dev(scene)
+    s = settings_of(scene, store, dist_literal, min_size, n_track)
+    H, W, K = scene.height, scene.width, s.n_track
+    n_hits = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    tracked = torch.empty((H, W, K), dtype=torch.int32, device="cuda")
+    cap = capacity or max(8 * scene.n_spheres, 1 << 16)
+    fr, image, log_norm = forward_frame(s, dev["pos"], dev["feat"], dev["rad"], dev["opa"], dev["cam"],
+                                        dev["bg"], cap, check_overflow=True, n_hits=n_hits,
+                                        tracked=tracked)
+    torch.cuda.synchronize()
+    return dict(frame=fr, dev=dev, image=image, log_norm=log_norm, n_hits=n_hits, tracked=tracked)
+
+
+def gpu_tile_lists(fr):
+    import torch
+    from paper_2004_07484_gb300 import _lib
+    s = fr.settings
+    nt = ((s.width + 15) // 16) * ((s.height + 15) // 16)
+    ranges = torch.empty((nt, 2), dtype=torch.int32, device="cuda")
+    cap = max(int(fr.params.list_capacity), 1)
+    ids = torch.empty((cap,), dtype=torch.int32, device="cuda")
+    _lib.read_tile_lists(fr.params, fr.ws.data_ptr(), fr.ws_bytes, ranges.data_ptr(), ids.data_ptr(),
+                         torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return ranges.cpu().numpy(), ids.cpu().numpy()
+
+
+def gpu_backward(out, G: np.ndarray, mask=None):
+    import torch
+    from paper_2004_07484_gb300 import backward_frame, _lib
+    d = out["dev"]
+    g = torch.from_numpy(np.ascontiguousarray(G.astype(np.float32))).cuda()
+    res = backward_frame(out["frame"], d["pos"], d["feat"], d["rad"], d["opa"], d["cam"], d["bg"],
+                         out["image"], out["log_norm"], g, _lib.GRAD_ALL if mask is None else mask)
+    torch.cuda.synchronize()
+    return {k: (None if v is None else v.cpu().numpy().astype(np.float64)) for k, v in zip(GRAD_NAMES, res)}
+
+
+def assert_tile_lists_equal(ranges, ids, off, oids):
+    nt = len(off) - 1
+    assert ranges.shape[0] == nt
+    for t in range(nt):
+        b, e = ranges[t]
+        got = ids[b:e] if e > b else ids[:0]
+        want = oids[off[t]:off[t + 1]]
+        assert np.array_equal(got, want), (t, got[:10], want[:10], len(got), len(want))
+
+
+def grad_error(g: np.ndarray, ref: np.ndarray):
+    """(max-norm relative error, worst elementwise ratio to the 1e-3 bound)."""
+    g = np.asarray(g, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    scale = float(np.abs(ref).max()) if ref.size else 0.0
+    if scale == 0.0:
+        return float(np.abs(g).max()) if g.size else 0.0, 0.0
+    rel = float(np.abs(g - ref).max()) / scale
+    bound = 1e-3 * (np.abs(ref) + 1e-3 * scale)
+    worst = float((np.abs(g - ref) / bound).max())
+    return rel, worst
+
+
+def assert_grads_close(got: dict, ref, names=GRAD_NAMES, rtol=1e-3):
+    for n in names:
+        g = got[n]
+        r = getattr(ref, n)
+        rel, worst = grad_error(g, r)
+        if not (rel <= rtol and worst <= 1.0):
+            gg, rr = np.asarray(g, np.float64).ravel(), np.asarray(r, np.float64).ravel()
+            scale = np.abs(rr).max()
+            ratio = np.abs(gg - rr) / (1e-3 * (np.abs(rr) + 1e-3 * scale))
+            idx = np.argsort(ratio)[::-1][:5]
+            detail = [(int(i), float(gg[i]), float(rr[i]), float(ratio[i])) for i in idx]
+            raise AssertionError(f"{n}: max-norm rel {rel:.3e}, worst elementwise ratio {worst:.2f}; "
+                                 f"scale {scale:.3e}; worst (index, got, want, ratio): {detail}")

@@ -1,0 +1,158 @@
+"""Edge cases and the PyTorch front end of the CUDA path."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2004_07484_gb300 import scenes as S
+from helpers import assert_grads_close, gpu_backward, gpu_forward, gpu_tile_lists, assert_tile_lists_equal
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2004_07484_gb300 import build
+    build.build()
+
+
+def _scene(pos, rad, opa, feat, W, H, gamma=0.1, K=5, bg=None, cam=None):
+    feat = np.atleast_2d(np.asarray(feat, np.float32)).reshape(len(rad), -1) if len(rad) else \
+        np.zeros((0, len(bg) if bg is not None else 3), np.float32)
+    C = feat.shape[1]
+    return S.Scene(np.asarray(pos, np.float32).reshape(-1, 3), np.asarray(rad, np.float32).ravel(),
+                   np.asarray(opa, np.float32).ravel(), np.ascontiguousarray(feat),
+                   S.make_cam() if cam is None else cam,
+                   np.zeros(C, np.float32) if bg is None else np.asarray(bg, np.float32), W, H, gamma, K)
+
+
+def _full_check(orc, sc, **kw):
+    ref = orc.render(sc, **{k: v for k, v in kw.items() if k in ("min_size", "dist_literal")})
+    gpu = gpu_forward(sc, **kw)
+    assert np.abs(gpu["image"].cpu().numpy() - ref.image).max() <= 1e-4
+    np.testing.assert_array_equal(gpu["tracked"].cpu().numpy(), ref.tracked)
+    off, oids = orc.tile_lists(sc)
+    assert_tile_lists_equal(*gpu_tile_lists(gpu["frame"]), off, oids)
+    G = S.grad_image(11, sc.height, sc.width, sc.n_channels)
+    want = orc.render_backward(sc, G)
+    assert_grads_close(gpu_backward(gpu, G), want)
+    return gpu, ref
+
+
+def test_empty_scene_is_background(orc):
+    sc = _scene(np.zeros((0, 3)), [], [], np.zeros((0, 4)), 40, 24, bg=[0.1, 0.2, 0.3, 0.4])
+    gpu = gpu_forward(sc)
+    img = gpu["image"].cpu().numpy()
+    assert np.allclose(img, np.array([0.1, 0.2, 0.3, 0.4], np.float32)[None, None, :])
+    G = S.grad_image(1, 24, 40, 4)
+    got = gpu_backward(gpu, G)
+    np.testing.assert_allclose(got["bg"], G.astype(np.float64).sum(axis=(0, 1)), rtol=1e-4)
+    assert np.all(got["cam"] == 0)
+
+
+def test_all_spheres_culled(orc):
+    g = np.random.default_rng(0)
+    pos = np.stack([g.uniform(-1, 1, 50), g.uniform(-1, 1, 50), g.uniform(-5, 0.5, 50)], 1)
+    sc = _scene(pos, g.uniform(0.1, 0.3, 50), np.ones(50), g.uniform(0, 1, (50, 3)), 32, 32)
+    gpu, ref = _full_check(orc, sc)
+    assert gpu["n_hits"].cpu().numpy().sum() == 0
+
+
+def test_single_sphere_on_axis_closed_form(orc):
+    W = H = 33
+    Z, r, o = 6.0, 2.0, 0.8
+    f = np.array([0.3, 0.7, 0.2], np.float32)
+    sc = _scene([0, 0, Z], [r], [o], f, W, H, gamma=0.1, bg=[0.1, 0.2, 0.9])
+    gpu, _ = _full_check(orc, sc)
+    z = (20.0 - (Z - r)) / 19.0
+    a = float(np.float32(o)) * math.exp(float(np.float32(o)) * z / float(np.float32(0.1)))
+    B = math.exp(float(np.float32(1e-5)) / float(np.float32(0.1)))
+    want = (a * f.astype(np.float64) + B * np.array([0.1, 0.2, 0.9], np.float32)) / (B + a)
+    np.testing.assert_allclose(gpu["image"].cpu().numpy()[16, 16], want, atol=1e-5)
+
+
+@pytest.mark.parametrize("C,K", [(1, 1), (2, 3), (5, 9), (32, 32), (12, 17), (8, 8)])
+def test_channel_and_track_counts(orc, C, K):
+    sc = S.gaussian_mixture(2000 + C * 33 + K, 2500, 48, 40, n_channels=C, gamma=0.05, n_track=K,
+                            mean_xy=(-0.7, 0.7), feat="normal")
+    _full_check(orc, sc)
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (17, 1), (1, 31), (33, 47), (16, 16)])
+def test_ragged_and_tiny_images(orc, W, H):
+    sc = S.uniform_cloud(3000 + W * 7 + H, 400, W, H, n_channels=3, gamma=0.1, n_track=5,
+                         xy=(-0.6, 0.6), rad=(0.05, 0.5))
+    _full_check(orc, sc)
+
+
+def test_capacity_overflow_is_reported_and_recovered(orc):
+    import torch
+    from paper_2004_07484_gb300 import _lib, forward_frame
+    from helpers import settings_of, to_dev
+    sc = S.config_scene(0)
+    dev = to_dev(sc)
+    s = settings_of(sc)
+    fr, _, _ = forward_frame(s, dev["pos"], dev["feat"], dev["rad"], dev["opa"], dev["cam"], dev["bg"],
+                             16, check_overflow=False)
+    st, need = _lib.read_status(fr.ws.data_ptr(), fr.ws_bytes, torch.cuda.current_stream().cuda_stream)
+    assert st == _lib.ERR_CAPACITY and need > 16
+    fr2, img, _ = forward_frame(s, dev["pos"], dev["feat"], dev["rad"], dev["opa"], dev["cam"], dev["bg"],
+                                16, check_overflow=True)
+    assert fr2.params.list_capacity >= need
+    ref = orc.render(sc)
+    assert np.abs(img.cpu().numpy() - ref.image).max() <= 1e-4
+
+
+def test_decisions_are_deterministic(orc):
+    sc = S.config_scene(1, n=20000, res=128)
+    a = gpu_forward(sc)
+    b = gpu_forward(sc)
+    assert np.array_equal(a["tracked"].cpu().numpy(), b["tracked"].cpu().numpy())
+    ra, ia = gpu_tile_lists(a["frame"])
+    rb, ib = gpu_tile_lists(b["frame"])
+    assert np.array_equal(ra, rb)
+    n = int(ra[:, 1].max())
+    assert np.array_equal(ia[:n], ib[:n])
+
+
+def test_module_autograd_matches_oracle(orc):
+    import torch
+    from paper_2004_07484_gb300 import Renderer
+    sc = S.config_scene(0)
+    r = Renderer(sc.width, sc.height, sc.n_spheres, n_channels=3, n_track=sc.n_track, gamma=sc.gamma)
+    t = {k: torch.from_numpy(getattr(sc, k)).cuda().requires_grad_(True)
+         for k in ("pos", "feat", "rad", "opa", "cam", "bg")}
+    img = r(t["pos"], t["feat"], t["rad"], t["cam"], opa=t["opa"], bg=t["bg"])
+    G = S.grad_image(12, sc.height, sc.width, 3)
+    (img * torch.from_numpy(G).cuda()).sum().backward()
+    want = orc.render_backward(sc, G)
+    got = {k: t[k].grad.cpu().numpy().astype(np.float64) for k in t}
+    assert_grads_close(got, want)
+    # only what autograd asks for is computed
+    t2 = {k: torch.from_numpy(getattr(sc, k)).cuda() for k in ("pos", "feat", "rad", "opa", "cam", "bg")}
+    t2["feat"].requires_grad_(True)
+    img2 = r(t2["pos"], t2["feat"], t2["rad"], t2["cam"], opa=t2["opa"], bg=t2["bg"])
+    (img2 * torch.from_numpy(G).cuda()).sum().backward()
+    np.testing.assert_allclose(t2["feat"].grad.cpu().numpy(), want.feat, atol=1e-5)
+
+
+def test_listing1_example_runs():
+    """The ten-sphere, 1024 x 1024 example of Listing 1 (identity rotation)."""
+    import torch
+    from paper_2004_07484_gb300 import Renderer
+    g = np.random.default_rng(1)
+    pos = g.uniform(0, 1, (10, 3)) * 10.0
+    pos[:, 2] += 25.0
+    pos[:, :2] -= 5.0
+    r = Renderer(1024, 1024, 10, n_channels=3)
+    cam = torch.tensor([0, 0, 0, 1, 0, 0, 0, 1, 0, 5.0, 2.0], dtype=torch.float32, device="cuda")
+    pos_t = torch.tensor(pos, dtype=torch.float32, device="cuda", requires_grad=True)
+    col = torch.tensor(g.uniform(0, 1, (10, 3)), dtype=torch.float32, device="cuda")
+    rad = torch.tensor(g.uniform(0, 1, 10), dtype=torch.float32, device="cuda")
+    img = r(pos_t, col, rad, cam, gamma=0.1, max_depth=45.0)
+    img.abs().sum().backward()
+    assert torch.isfinite(img).all() and (img.sum(-1) > 0).any()
+    assert torch.isfinite(pos_t.grad).all()
