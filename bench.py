@@ -199,8 +199,9 @@ def main():
     # size the pair list once (synchronising check), then run without checks
     fr, _, _ = forward_frame(settings(True), t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"],
                              4 * sc.n_spheres, check_overflow=True)
-    capacity = int(fr.params.list_capacity)
     pairs_needed = _lib.read_status(fr.ws.data_ptr(), fr.ws_bytes, stream.cuda_stream)[1]
+    capacity = int(pairs_needed * 1.25) + 4096   # the Renderer's growth policy after an overflow
+    del fr
 
     # counters for the algorithmic work of the render kernels
     H, W, C = sc.height, sc.width, sc.n_channels

@@ -15,9 +15,10 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t hdr, scenes, rec0, rec1, rec2, key0, key1, val0, val1, hist, block_sums, pkey0, pkey1, pval0,
-      pval1, ranges, tile_kappa, tile_bg, thr, gacc, fin_part, total;
-  int64_t n_spheres, n_tiles, n_pixels, capacity;
-  int32_t sort_blocks, fin_blocks, tile_bits;
+      pval1, ranges, item_begin, item_tile, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
+      gacc, fin_part, total;
+  int64_t n_spheres, n_tiles, n_pixels, capacity, max_items;
+  int32_t sort_blocks, fin_blocks, tile_bits, segment, part_fields;
 };
 
 bool tiles_of(const pulsar_params& p, int& tx, int& ty) {
@@ -47,8 +48,8 @@ Layout make_layout(const pulsar_params* ps, int n) {
   memset(&L, 0, sizeof(L));
   int64_t M = 0, NT = 0, P = 0, cap = 0;
   int fin = 0;
-  bool store = false;
-  int C = ps[0].n_channels;
+  const int C = ps[0].n_channels;
+  const int K = ps[0].n_track;
   for (int s = 0; s < n; ++s) {
     int tx, ty;
     tiles_of(ps[s], tx, ty);
@@ -57,7 +58,6 @@ Layout make_layout(const pulsar_params* ps, int n) {
     P += (int64_t)ps[s].width * ps[s].height;
     cap += ps[s].list_capacity;
     fin += (ps[s].n_spheres + kFinalizeThreads - 1) / kFinalizeThreads;
-    store = store || (ps[s].flags & PULSAR_FLAG_STORE_HITS);
   }
   L.n_spheres = M;
   L.n_tiles = NT;
@@ -68,6 +68,9 @@ Layout make_layout(const pulsar_params* ps, int n) {
   int bits = 1;
   while (bits < 32 && ((int64_t)1 << bits) < NT) ++bits;
   L.tile_bits = bits;
+  L.segment = kDefaultSegment;
+  L.max_items = NT + (cap + L.segment - 1) / L.segment;
+  L.part_fields = 6 + C + 2 * K;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -90,9 +93,14 @@ Layout make_layout(const pulsar_params* ps, int n) {
   L.pval0 = take(4 * (size_t)cap);
   L.pval1 = take(4 * (size_t)cap);
   L.ranges = take(8 * (size_t)NT);
-  L.tile_kappa = take(4 * (size_t)NT);
+  L.item_begin = take(4 * (size_t)(NT + 1));
+  L.item_tile = take(4 * (size_t)L.max_items);
+  L.tile_done = take(4 * (size_t)NT);
+  L.partial = take(4 * (size_t)L.max_items * kThreads * L.part_fields);
+  L.item_kappa = take(4 * (size_t)L.max_items);
   L.tile_bg = take(4 * (size_t)NT * C);
-  L.thr = take(store ? 8 * (size_t)P : 0);
+  L.pix_aux = take(16 * (size_t)P);
+  L.fres = take(4 * (size_t)P * C);
   L.gacc = take(16 * (size_t)M);
   L.fin_part = take(4 * (size_t)kCamPartials * std::max(fin, 1));
   L.total = off;
@@ -115,6 +123,9 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.n_channels = ps[0].n_channels;
   v.n_track = ps[0].n_track;
   v.pair_buf = ((L.tile_bits + kRadixBits - 1) / kRadixBits) & 1;
+  v.segment = L.segment;
+  v.max_items = (int32_t)L.max_items;
+  v.part_fields = L.part_fields;
   v.rec0 = reinterpret_cast<float4*>(b + L.rec0);
   v.rec1 = reinterpret_cast<float4*>(b + L.rec1);
   v.rec2 = reinterpret_cast<float4*>(b + L.rec2);
@@ -129,9 +140,14 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.pval[0] = reinterpret_cast<uint32_t*>(b + L.pval0);
   v.pval[1] = reinterpret_cast<uint32_t*>(b + L.pval1);
   v.ranges = reinterpret_cast<int2*>(b + L.ranges);
-  v.tile_kappa = reinterpret_cast<float*>(b + L.tile_kappa);
+  v.item_begin = reinterpret_cast<int32_t*>(b + L.item_begin);
+  v.item_tile = reinterpret_cast<int32_t*>(b + L.item_tile);
+  v.tile_done = reinterpret_cast<int32_t*>(b + L.tile_done);
+  v.partial = reinterpret_cast<float*>(b + L.partial);
+  v.item_kappa = reinterpret_cast<float*>(b + L.item_kappa);
   v.tile_bg = reinterpret_cast<float*>(b + L.tile_bg);
-  v.thr = reinterpret_cast<float2*>(b + L.thr);
+  v.pix_aux = reinterpret_cast<float4*>(b + L.pix_aux);
+  v.fres = reinterpret_cast<float*>(b + L.fres);
   v.gacc = reinterpret_cast<float4*>(b + L.gacc);
   v.fin_part = reinterpret_cast<float*>(b + L.fin_part);
   return v;
@@ -291,8 +307,10 @@ extern "C" pulsar_status pulsar_render_bwd(const pulsar_params* params, const pu
     e = cudaMemsetAsync(g_opa, 0, sizeof(float) * (size_t)M, s);
   if (e == cudaSuccess && M > 0 && (grad_mask & PULSAR_GRAD_FEAT))
     e = cudaMemsetAsync(g_feat, 0, sizeof(float) * (size_t)M * C, s);
-  if (e == cudaSuccess)
-    e = launch_render_bwd(v, (params->flags & PULSAR_FLAG_STORE_HITS) != 0, grad_mask, s);
+  const bool geo_or_values = (grad_mask & ~(uint32_t)PULSAR_GRAD_BG) != 0;
+  if (e == cudaSuccess && geo_or_values && !(params->flags & PULSAR_FLAG_STORE_HITS))
+    e = launch_track_pass(v, s);
+  if (e == cudaSuccess) e = launch_render_bwd(v, grad_mask, s);
   if (e == cudaSuccess) e = launch_finalize(v, grad_mask, s);
   return cuda_status(e);
 }

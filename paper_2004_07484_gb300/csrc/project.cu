@@ -194,32 +194,33 @@ __device__ __forceinline__ float dot3(const float* a, const float* b) {
 }
 
 // One CTA per scene: deterministic sum of the per-block camera partials, the
-// per-tile pitch and background partials, then the chain through the pixel
-// pitch kappa = s / (W f) and the Gram-Schmidt map of the 6D rotation.
-__global__ void __launch_bounds__(kFinalizeThreads) camera_reduce_kernel(WsView v, uint32_t mask) {
+// per-item pitch partials and the per-tile background partials, then the
+// chain through the pixel pitch kappa = s / (W f) and the Gram-Schmidt map of
+// the 6D rotation.
+__global__ void __launch_bounds__(1024) camera_reduce_kernel(WsView v, uint32_t mask) {
   __shared__ float sh[32];
   __shared__ float tot[13];
   const SceneDev& S = v.scenes[blockIdx.x];
   const int C = S.n_channels;
+  const int64_t nt = (int64_t)S.tiles_x * S.tiles_y;
   if (mask & PULSAR_GRAD_CAM) {
     for (int k = 0; k < 13; ++k) {
       float x = 0.0f;
       for (int b = threadIdx.x; b < S.fin_blocks; b += blockDim.x)
         x += v.fin_part[(size_t)(S.fin_block_begin + b) * kCamPartials + k];
       if (k == 12) {
-        const int64_t nt = (int64_t)S.tiles_x * S.tiles_y;
-        for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) x += v.tile_kappa[S.tile_begin + t];
+        const int i0 = v.item_begin[S.tile_begin], i1 = v.item_begin[S.tile_begin + nt];
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) x += v.item_kappa[i];
       }
       float r = block_sum(x, sh);
       if (threadIdx.x == 0) tot[k] = r;
     }
   }
   if (mask & PULSAR_GRAD_BG) {
-    const int64_t nt = (int64_t)S.tiles_x * S.tiles_y;
     for (int c = 0; c < C; ++c) {
+      const float* row = v.tile_bg + (size_t)c * v.n_tiles + S.tile_begin;
       float x = 0.0f;
-      for (int64_t t = threadIdx.x; t < nt; t += blockDim.x)
-        x += v.tile_bg[(size_t)(S.tile_begin + t) * C + c];
+      for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) x += row[t];
       float r = block_sum(x, sh);
       if (threadIdx.x == 0) S.g_bg[c] = r;
     }
@@ -301,7 +302,7 @@ cudaError_t launch_finalize(const WsView& v, uint32_t mask, cudaStream_t st) {
   if (v.fin_blocks > 0 && (mask & (PULSAR_GRAD_POS | PULSAR_GRAD_RAD | PULSAR_GRAD_CAM)))
     finalize_kernel<<<v.fin_blocks, kFinalizeThreads, 0, st>>>(v, mask);
   if (mask & (PULSAR_GRAD_CAM | PULSAR_GRAD_BG))
-    camera_reduce_kernel<<<v.n_scenes, kFinalizeThreads, 0, st>>>(v, mask);
+    camera_reduce_kernel<<<v.n_scenes, 1024, 0, st>>>(v, mask);
   return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxScenes = 64;
 constexpr int kFinalizeThreads = 256;
 constexpr int kCamPartials = 16;     // floats per finalize-block camera partial (13 used)
+constexpr int kDefaultSegment = 1024;  // list entries one CTA processes per work item
 
 // Per-scene description in the workspace.  The host fills the inputs; the
 // setup kernel derives the camera rows and pixel pitch.
@@ -82,7 +83,8 @@ struct WsHeader {
   int32_t n_pairs;           // pairs in the lists (0 after an overflow)
   int32_t n_sort;            // keys in the sphere sort (= total spheres)
   int32_t timeout;           // a bounded device loop gave up
-  int32_t pad_[9];
+  int32_t n_items;           // (tile, segment) work items of the render passes
+  int32_t pad_[8];
 };
 
 // Raw pointers into one workspace, passed to kernels by value.
@@ -99,6 +101,9 @@ struct WsView {
   int32_t n_channels;        // common feature length of the batch
   int32_t n_track;           // common n_track of the batch
   int32_t pair_buf;          // ping-pong buffer holding the tile-sorted pairs
+  int32_t segment;           // list entries per work item (a multiple of kChunk)
+  int32_t max_items;         // bound on work items: n_tiles + capacity / segment
+  int32_t part_fields;       // floats per pixel of a partial forward state
   float4* rec0;              // per sphere: c.x, c.y, c.z, R^2
   float4* rec1;              // per sphere: key, o, x-range (x0 | x1 << 16), y-range
   float4* rec2;              // per sphere: c - c.xyz (low-order part of the double centre), R
@@ -109,9 +114,14 @@ struct WsView {
   uint32_t* pkey[2];         // pair tile ids (ping-pong)
   uint32_t* pval[2];         // pair sphere ids (ping-pong)
   int2* ranges;              // per tile [begin, end)
-  float* tile_kappa;         // per tile d L / d kappa partial
-  float* tile_bg;            // per tile x C background-gradient partial
-  float2* thr;               // per pixel (t_K, bits of id_K) of the K-th tracked hit
+  int32_t* item_begin;       // per tile (+1): first work item
+  int32_t* item_tile;        // per work item: its tile
+  int32_t* tile_done;        // per tile: finished segments (last-finisher merge)
+  float* partial;            // per work item: partial forward state, [field][pixel]
+  float* item_kappa;         // per work item: d L / d kappa partial
+  float* tile_bg;            // channel-major: [c][tile] background-gradient partial
+  float4* pix_aux;           // per pixel: (t_K, id_K bits, reference sphere bits, 0)
+  float* fres;               // per pixel x C: F - f_ref, the image relative to its reference feature
   float4* gacc;              // per sphere: dL/dc (3), dL/dR
   float* fin_part;           // per finalize block: camera partials
 };
@@ -261,16 +271,24 @@ struct ValueGeom {
   float cr2, rr, sq, off, dist;
 };
 
+// Value-path square root and quotient: hardware approximations (about 2 ulp),
+// well inside the value path's tolerance.
+__device__ __forceinline__ float vsqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ float vdiv(float a, float b) { return __fdividef(a, b); }
+
 __device__ __forceinline__ ValueGeom value_geom(const float4& a, const float4& c2, const ValueRay& r) {
   ValueGeom g;
   g.ex = fmaf(a.z, r.rx, -a.x) + fmaf(a.z, r.rx_lo, fmaf(c2.z, r.rx, -c2.x));
   g.ey = fmaf(a.z, r.ry, -a.y) + fmaf(a.z, r.ry_lo, fmaf(c2.z, r.ry, -c2.y));
-  g.ez = (a.x * g.ey - a.y * g.ex) / a.z;
+  // d = 1 - dist/R is ill-conditioned at the rim, where a sphere blending
+  // with what lies behind it makes the image change like 1/d: the terms that
+  // set dist use correctly rounded division and square root.
+  g.ez = fmaf(a.x, g.ey, -a.y * g.ex) / a.z;
   g.cr2 = fmaf(g.ex, g.ex, fmaf(g.ey, g.ey, g.ez * g.ez));
   g.rr = fmaf(r.rx, r.rx, fmaf(r.ry, r.ry, 1.0f));
   const float R = c2.w;
-  g.sq = sqrtf(fmaxf(fmaf(g.rr, R * R, -g.cr2), 0.0f));
-  g.off = fmaf(r.rx, g.ex, fmaf(r.ry, g.ey, g.sq)) / g.rr;
+  g.sq = vsqrt(fmaf(g.rr, R * R, -g.cr2));
+  g.off = vdiv(fmaf(r.rx, g.ex, fmaf(r.ry, g.ey, g.sq)), g.rr);
   g.dist = sqrtf(g.cr2 / g.rr);
   return g;
 }
@@ -313,7 +331,8 @@ cudaError_t launch_setup(const WsView& v, const SceneDev* host_scenes, int n, cu
 cudaError_t launch_project(const WsView& v, cudaStream_t st);
 cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st);
 cudaError_t launch_render_fwd(const WsView& v, bool store, cudaStream_t st);
-cudaError_t launch_render_bwd(const WsView& v, bool store, uint32_t grad_mask, cudaStream_t st);
+cudaError_t launch_track_pass(const WsView& v, cudaStream_t st);
+cudaError_t launch_render_bwd(const WsView& v, uint32_t grad_mask, cudaStream_t st);
 cudaError_t launch_finalize(const WsView& v, uint32_t grad_mask, cudaStream_t st);
 
 }  // namespace pulsar

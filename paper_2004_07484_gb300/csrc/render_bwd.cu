@@ -1,13 +1,15 @@
 // Backward pass (App. B, "The Backward Pass"), parallel over pixels.
 //
 // A hit is tracked when its (depth, index) is at most the pixel's n_track-th
-// tracked hit.  That threshold comes from the forward pass (store mode, App. B
-// "Preparing for the Backward Pass") or is recomputed here by the forward's
-// traversal without blending (recompute mode).  The gradient pass then walks
-// the tile's list again; all lanes of a warp visit the same sphere at the same
-// time, so each sphere's per-pixel contributions are summed across the warp
-// with shuffles before one set of (vector) atomics per warp and sphere.  The
-// walk stops at the first key beyond every pixel's threshold.
+// tracked hit.  That threshold is kept per pixel by the forward pass (store
+// mode, App. B "Preparing for the Backward Pass") or recomputed before this
+// pass by the forward traversal without blending (recompute mode).  Work is
+// split into the same (tile, segment) items as the forward pass; gradients
+// are sums, so segments need no merge.  All lanes of a warp visit the same
+// sphere at the same time, so each sphere's per-pixel contributions are
+// summed across the warp with shuffles before one set of (vector) atomics per
+// warp and sphere.  A segment stops at the first key beyond every pixel's
+// threshold.
 //
 // Derivatives (Eq. 1 with a = o d e^{o z / gamma}, D its denominator, G = dL/dF):
 //   dL/df_i = w_i G,   dL/da_i = G.(f_i - F) / D,
@@ -18,6 +20,9 @@
 //   dt/dr = (e (1 - b/sqrt(disc)) - t r)/|r|^2,  b = r.c,
 //   ddist/dc = e/dist,  ddist/dr = -t_c e/dist.
 // Ray slopes depend on the pixel pitch kappa: dr/dkappa = (u + 1/2 - W/2, v + 1/2 - H/2, 0).
+// G.(f_i - F) is formed as G.(f_i - f_ref) - G.(F - f_ref) from the forward's
+// reference feature, exactly -G.(F - f_ref) for the reference hit itself,
+// which keeps it accurate where one hit carries nearly all the weight.
 #include "render_common.cuh"
 
 namespace pulsar {
@@ -33,42 +38,26 @@ __device__ __forceinline__ void warp_reduce_and_add(bool tracked, int id_global,
   const unsigned bal = __ballot_sync(0xffffffffu, tracked);
   if (bal == 0u) return;
   const int lane = threadIdx.x & 31;
-  if (__popc(bal) == 1) {
-    if (!tracked) return;
-    if (geo) atomicAdd(&v.gacc[id_global], make_float4(gc0, gc1, gc2, gR));
-    if (opa) atomicAdd(S.g_opa + id_local, go);
-    if (feat) {
-      float* dst = S.g_feat + id_local * C;
-      if ((C & 3) == 0) {
-#pragma unroll
-        for (int c = 0; c < CMAX; c += 4)
-          if (c < C) atomicAdd(reinterpret_cast<float4*>(dst + c), make_float4(gf[c], gf[c + 1], gf[c + 2], gf[c + 3]));
-      } else {
-#pragma unroll
-        for (int c = 0; c < CMAX; ++c)
-          if (c < C) atomicAdd(dst + c, gf[c]);
-      }
-    }
-    return;
-  }
-  // several lanes hit this sphere: butterfly sums (all lanes take part)
   float r0 = gc0, r1 = gc1, r2 = gc2, r3 = gR, r4 = go;
   float rf[CMAX];
 #pragma unroll
   for (int c = 0; c < CMAX; ++c) rf[c] = gf[c];
+  if (__popc(bal) > 1) {
+    // several lanes hit this sphere: butterfly sums (all lanes take part)
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    if (geo) {
-      r0 += __shfl_xor_sync(0xffffffffu, r0, o);
-      r1 += __shfl_xor_sync(0xffffffffu, r1, o);
-      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-      r3 += __shfl_xor_sync(0xffffffffu, r3, o);
-    }
-    if (opa) r4 += __shfl_xor_sync(0xffffffffu, r4, o);
-    if (feat) {
+    for (int o = 16; o > 0; o >>= 1) {
+      if (geo) {
+        r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+        r1 += __shfl_xor_sync(0xffffffffu, r1, o);
+        r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+        r3 += __shfl_xor_sync(0xffffffffu, r3, o);
+      }
+      if (opa) r4 += __shfl_xor_sync(0xffffffffu, r4, o);
+      if (feat) {
 #pragma unroll
-      for (int c = 0; c < CMAX; ++c)
-        if (c < C) rf[c] += __shfl_xor_sync(0xffffffffu, rf[c], o);
+        for (int c = 0; c < CMAX; ++c)
+          if (c < C) rf[c] += __shfl_xor_sync(0xffffffffu, rf[c], o);
+      }
     }
   }
   if (lane != __ffs(bal) - 1) return;
@@ -79,7 +68,8 @@ __device__ __forceinline__ void warp_reduce_and_add(bool tracked, int id_global,
     if ((C & 3) == 0) {
 #pragma unroll
       for (int c = 0; c < CMAX; c += 4)
-        if (c < C) atomicAdd(reinterpret_cast<float4*>(dst + c), make_float4(rf[c], rf[c + 1], rf[c + 2], rf[c + 3]));
+        if (c < C)
+          atomicAdd(reinterpret_cast<float4*>(dst + c), make_float4(rf[c], rf[c + 1], rf[c + 2], rf[c + 3]));
     } else {
 #pragma unroll
       for (int c = 0; c < CMAX; ++c)
@@ -88,20 +78,19 @@ __device__ __forceinline__ void warp_reduce_and_add(bool tracked, int id_global,
   }
 }
 
-template <int KMAX, int CMAX>
+template <int CMAX>
 __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
                                                                  const uint32_t* __restrict__ list,
-                                                                 int store, uint32_t mask) {
+                                                                 uint32_t mask) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ChunkSmem<CMAX>& sm = *reinterpret_cast<ChunkSmem<CMAX>*>(smem_raw);
   __shared__ float red[kThreads / 32][CMAX + 1];
-  const int64_t tile = blockIdx.x;
-  const int si = scene_of_tile(v.scenes, v.n_scenes, tile);
+  ItemCtx it;
+  if (!item_ctx(v, it)) return;
+  const int si = scene_of_tile(v.scenes, v.n_scenes, it.tile);
   const SceneDev& S = v.scenes[si];
-  const PixelCtx pc = pixel_ctx(S, tile);
-  const int2 rg = v.ranges[tile];
+  const PixelCtx pc = pixel_ctx(S, it.tile);
   const int C = S.n_channels;
-  const int K = S.n_track;
   const float gamma = S.gamma, zfar = S.zfar, znear = S.znear;
   const float inv_gamma = 1.0f / gamma;
   const float inv_range = 1.0f / (zfar - znear);
@@ -117,24 +106,33 @@ __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
 
   // per-pixel upstream data
   const int64_t pix = pc.inside ? (int64_t)pc.py * S.width + pc.px : 0;
+  const int64_t gpix = S.pixel_begin + pix;
   float G[CMAX];
-  float GF = 0.0f, logD = 0.0f;
+  float logD = 0.0f, GFres = 0.0f, Gref = 0.0f;
+  float thr_t = __int_as_float(0x7f800000);
+  int thr_i = 0x7fffffff, dom = -1;
 #pragma unroll
   for (int c = 0; c < CMAX; ++c) G[c] = 0.0f;
   if (pc.inside) {
     const float* g = S.grad_image + pix * C;
-    const float* F = S.image_in + pix * C;
+    const float* fr = v.fres + gpix * C;
+    const float4 aux = v.pix_aux[gpix];
+    thr_t = aux.x;
+    thr_i = __float_as_int(aux.y);
+    dom = __float_as_int(aux.z);
+    const float* fref = dom < 0 ? S.bg : S.feat + (int64_t)(dom - S.sphere_begin) * C;
 #pragma unroll
     for (int c = 0; c < CMAX; ++c)
       if (c < C) {
         G[c] = g[c];
-        GF = fmaf(G[c], F[c], GF);
+        GFres = fmaf(G[c], fr[c], GFres);
+        Gref = fmaf(G[c], fref[c], Gref);
       }
     logD = S.log_norm_in[pix];
   }
 
-  // background gradient: sum over the tile of w_B G
-  if (bgw) {
+  // background gradient: sum over the tile of w_B G (first segment only)
+  if (bgw && it.seg == 0) {
     const float wB = pc.inside ? __expf(S.eps * inv_gamma - logD) : 0.0f;
 #pragma unroll
     for (int c = 0; c < CMAX; ++c) {
@@ -145,69 +143,20 @@ __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
     if (threadIdx.x < C) {
       float s = 0.0f;
       for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
-      v.tile_bg[(size_t)tile * C + threadIdx.x] = s;
+      v.tile_bg[(size_t)threadIdx.x * v.n_tiles + it.tile] = s;
     }
     __syncthreads();
   }
   if (!(geo || opa || feat)) {
-    if (cam && threadIdx.x == 0) v.tile_kappa[tile] = 0.0f;
+    if (cam && threadIdx.x == 0) v.item_kappa[it.item] = 0.0f;
     return;
   }
 
-  // threshold of the tracked set
-  float thr_t = __int_as_float(0x7f800000);
-  int thr_i = 0x7fffffff;
-  if (store) {
-    if (pc.inside) {
-      const float2 th = v.thr[S.pixel_begin + pix];
-      thr_t = th.x;
-      thr_i = __float_as_int(th.y);
-    }
-  } else {
-    float qt[KMAX];
-    int qi[KMAX];
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-      qt[k] = __int_as_float(0x7f800000);
-      qi[k] = 0x7fffffff;
-    }
-    bool done = !pc.inside;
-    float kstop = __int_as_float(0x7f800000);
-    for (int base = rg.x; base < rg.y; base += kChunk) {
-      const int n = min(kChunk, rg.y - base);
-      const int cnt = stage_chunk<CMAX>(sm, v, S, list, base, n, pc, false);
-      for (int k = 0; k < cnt; ++k) {
-        if (__all_sync(0xffffffffu, done)) break;
-        const int j = sm.list[warp][k];
-        const float4 a = sm.rec0[j];
-        const float4 b = sm.rec1[j];
-        if (done) continue;
-        if (b.x >= kstop) {
-          done = true;
-          continue;
-        }
-        if (!in_rect(b, pc.px, pc.py)) continue;
-        RayHit h;
-        if (!ray_hit(a.x, a.y, a.z, a.w, b.x, pc.rx, pc.ry, zfar, h)) continue;
-        const int id = sm.id[j];
-        if (hit_less(h.t, id, thr_t, thr_i)) {
-          queue_insert<KMAX>(qt, qi, h.t, id);
-          queue_select<KMAX>(qt, qi, K, thr_t, thr_i);
-          kstop = next_up(thr_t);
-        }
-      }
-      if (__syncthreads_and(done)) break;
-    }
-  }
-
-  // gradient pass
-  const float pxo = (float)(2 * pc.px + 1 - S.width) * 0.5f;
-  const float pyo = (float)(2 * pc.py + 1 - S.height) * 0.5f;
   const float kstop = next_up(thr_t);
   bool done = !pc.inside;
   float gk_sum = 0.0f;
-  for (int base = rg.x; base < rg.y; base += kChunk) {
-    const int n = min(kChunk, rg.y - base);
+  for (int base = it.b0; base < it.b1; base += kChunk) {
+    const int n = min(kChunk, it.b1 - base);
     const int cnt = stage_chunk<CMAX>(sm, v, S, list, base, n, pc, true);
     for (int k = 0; k < cnt; ++k) {
       if (__all_sync(0xffffffffu, done)) break;
@@ -231,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
             const float4 c2 = sm.rec2[j];
             const ValueGeom g = value_geom(a, c2, pc.vr);
             const float R = c2.w;
-            const float inv_rr = 1.0f / g.rr;
+            const float inv_rr = vdiv(1.0f, g.rr);
             const float dist = g.dist;
             const float qd = dist / R;
             const float qdc = fminf(qd, 1.0f);
@@ -245,9 +194,14 @@ __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
             const float E = __expf(fminf(s - logD, 80.0f));
             const float w = o * d * E;
             const float* f = &sm.feat[j * CMAX];
-            float gdot = -GF;
+            float gdot;   // G.(f_i - F)
+            if (id == dom) {
+              gdot = -GFres;
+            } else {
+              gdot = -Gref - GFres;
 #pragma unroll
-            for (int c = 0; c < CMAX; ++c) gdot = fmaf(G[c], f[c], gdot);
+              for (int c = 0; c < CMAX; ++c) gdot = fmaf(G[c], f[c], gdot);
+            }
 #pragma unroll
             for (int c = 0; c < CMAX; ++c) gf[c] = w * G[c];
             go = gdot * d * E * (1.0f + s);
@@ -257,8 +211,8 @@ __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
             float gdist = 0.0f;
             if (qd < 1.0f) {
               const float sgn = literal ? 1.0f : -1.0f;
-              gdist = sgn * gd / R;
-              gR = -sgn * gd * qd / R;
+              gdist = sgn * vdiv(gd, R);
+              gR = -sgn * gd * vdiv(qd, R);
             }
             // e = (r x (c x r)) / |r|^2 with c x r = (-ey, ex, ez)
             const float rx = pc.vr.rx, ry = pc.vr.ry;
@@ -273,9 +227,9 @@ __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
             // literal d the product diverges in exact arithmetic too.
             float gt_sq;
             if (literal) {
-              gt_sq = g.sq > 0.0f ? gt / g.sq : 0.0f;
+              gt_sq = g.sq > 0.0f ? vdiv(gt, g.sq) : 0.0f;
             } else {
-              const float d_over_sq = g.sq * inv_rr / (R * (R + dist));
+              const float d_over_sq = vdiv(g.sq * inv_rr, R * (R + dist));
               gt_sq = -gdot * o * E * o * inv_gamma * inv_range * d_over_sq;
             }
             const float tc = t_val + g.sq * inv_rr;   // closest-approach parameter
@@ -287,13 +241,15 @@ __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
             float grx = (gt * e0 - gt_sq * b_ * e0 - gt * t_val * rx) * inv_rr;
             float gry = (gt * e1 - gt_sq * b_ * e1 - gt * t_val * ry) * inv_rr;
             if (dist > 0.0f) {
-              const float gi = gdist / dist;
+              const float gi = vdiv(gdist, dist);
               gc0 += gi * e0;
               gc1 += gi * e1;
               gc2 += gi * e2;
               grx += -gi * tc * e0;
               gry += -gi * tc * e1;
             }
+            const float pxo = (float)(2 * pc.px + 1 - S.width) * 0.5f;
+            const float pyo = (float)(2 * pc.py + 1 - S.height) * 0.5f;
             gk_sum += grx * pxo + gry * pyo;
           }
         }
@@ -311,41 +267,31 @@ __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
     if (threadIdx.x == 0) {
       float s = 0.0f;
       for (int w = 0; w < kThreads / 32; ++w) s += red[w][0];
-      v.tile_kappa[tile] = s;
+      v.item_kappa[it.item] = s;
     }
   }
 }
 
-template <int KMAX, int CMAX>
-cudaError_t launch_bwd_t(const WsView& v, const uint32_t* list, bool store, uint32_t mask,
-                         cudaStream_t st) {
+template <int CMAX>
+cudaError_t launch_bwd_t(const WsView& v, const uint32_t* list, uint32_t mask, cudaStream_t st) {
   const size_t smem = sizeof(ChunkSmem<CMAX>);
-  auto kern = render_bwd_kernel<KMAX, CMAX>;
+  auto kern = render_bwd_kernel<CMAX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)v.n_tiles, kThreads, smem, st>>>(v, list, store ? 1 : 0, mask);
+  kern<<<(unsigned)v.max_items, kThreads, smem, st>>>(v, list, mask);
   return cudaGetLastError();
-}
-
-template <int KMAX>
-cudaError_t launch_bwd_k(const WsView& v, const uint32_t* list, bool store, uint32_t mask,
-                         cudaStream_t st) {
-  const int C = v.n_channels;
-  if (C <= 4) return launch_bwd_t<KMAX, 4>(v, list, store, mask, st);
-  if (C <= 8) return launch_bwd_t<KMAX, 8>(v, list, store, mask, st);
-  if (C <= 16) return launch_bwd_t<KMAX, 16>(v, list, store, mask, st);
-  return launch_bwd_t<KMAX, 32>(v, list, store, mask, st);
 }
 
 }  // namespace
 
-cudaError_t launch_render_bwd(const WsView& v, bool store, uint32_t mask, cudaStream_t st) {
-  if (v.n_tiles == 0) return cudaSuccess;
+cudaError_t launch_render_bwd(const WsView& v, uint32_t mask, cudaStream_t st) {
+  if (v.max_items == 0) return cudaSuccess;
   const uint32_t* list = v.pval[v.pair_buf];
-  const int K = v.n_track;
-  if (K <= 8) return launch_bwd_k<8>(v, list, store, mask, st);
-  if (K <= 16) return launch_bwd_k<16>(v, list, store, mask, st);
-  return launch_bwd_k<32>(v, list, store, mask, st);
+  const int C = v.n_channels;
+  if (C <= 4) return launch_bwd_t<4>(v, list, mask, st);
+  if (C <= 8) return launch_bwd_t<8>(v, list, mask, st);
+  if (C <= 16) return launch_bwd_t<16>(v, list, mask, st);
+  return launch_bwd_t<32>(v, list, mask, st);
 }
 
 }  // namespace pulsar

@@ -31,6 +31,30 @@ struct ChunkSmem {
   uint8_t list[kThreads / 32][kChunk];
 };
 
+// One work item: a segment of at most `segment` entries of one tile's list.
+struct ItemCtx {
+  int item;          // work-item index (also the partial-state slot)
+  int64_t tile;      // global tile index
+  int seg, nseg;     // segment index and segment count of the tile
+  int first;         // first work item of the tile
+  int b0, b1;        // list range [b0, b1) of this segment
+};
+
+// Returns false for grid slots beyond the number of work items.
+__device__ __forceinline__ bool item_ctx(const WsView& v, ItemCtx& c) {
+  c.item = blockIdx.x;
+  if (c.item >= v.hdr->n_items) return false;
+  c.tile = v.item_tile[c.item];
+  c.first = v.item_begin[c.tile];
+  c.nseg = v.item_begin[c.tile + 1] - c.first;
+  c.seg = c.item - c.first;
+  const int2 rg = v.ranges[c.tile];
+  c.b0 = rg.x + c.seg * v.segment;
+  c.b1 = min(rg.x + (c.seg + 1) * v.segment, rg.y);
+  if (c.b1 < c.b0) c.b1 = c.b0;
+  return true;
+}
+
 // Geometry of the pixel a thread renders.
 struct PixelCtx {
   int tile_x0, tile_y0;   // first pixel of the tile

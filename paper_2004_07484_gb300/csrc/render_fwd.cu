@@ -1,35 +1,96 @@
 // Forward pass: App. B, Step 1 (intersection search) and Step 2 (draw).
 //
-// Per pixel, hits are blended by Eq. 1 in the order of the tile's list, with a
-// running maximum of the exponents o z / gamma divided out of numerator and
-// denominator (the online form of the weighted softmax), and the n_track
-// closest hits are kept in a register queue (App. B, Step 2).
+// Work decomposition.  A tile's depth-ordered list is cut into segments of
+// at most `segment` entries and every (tile, segment) work item gets its own
+// CTA, so a few very long lists no longer serialise the launch.  Eq. 1 is a
+// commutative sum (App. A) and the n_track closest hits of a union are the
+// closest of the per-part closest, so segments are combined afterwards: the
+// CTA that finishes a tile's segments last (a per-tile atomic counter) merges
+// the partial states the others left in the workspace and writes the pixel.
 //
-// Early termination (Sec. 3.2, App. B Step 2) in an exact form: a pixel stops
-// at the first listed sphere whose key (earliest depth) is
+// Per pixel, hits are blended in list order with the largest exponent
+// o z / gamma divided out of numerator and denominator, and the numerator is
+// kept relative to a reference feature: the feature of the hit with the
+// largest weight so far (initially the background), i.e. the state is
+//   den = e^{eps/g - m} + sum_k a_k e^{-m},
+//   res = sum_k a_k e^{-m} (f_k - f_ref) + e^{eps/g - m} (bg - f_ref),
+//   F   = f_ref + res / den.
+// F - f_ref is thereby kept to float precision even where one hit carries
+// nearly all the weight; the backward pass needs exactly that difference.
+//
+// The n_track closest hits (by float32 depth, then index) are kept in a
+// register queue (App. B, Step 2).  Early termination (Sec. 3.2, App. B
+// Step 2), exact: a pixel stops at the first listed sphere whose key
+// (earliest depth) is
 //   (i)  beyond the depth of its n_track-th tracked hit, so no later sphere
 //        can enter the tracked set (every hit depth is >= its sphere's key), and
-//   (ii) so far that the largest total weight all remaining spheres could
-//        still add, N_rem |o|max exp(|o|max z(key) / gamma), is at most 1e-7 of
-//        the current denominator.
-// A CTA stops once every pixel has stopped (a barrier vote over all threads).
+//   (ii) so far that the largest total weight all remaining spheres of the
+//        segment could still add, N_rem |o|max exp(|o|max z(key) / gamma), is
+//        at most 1e-7 of the segment's own denominator (a lower bound of the
+//        pixel's).
+// Both tests only use the segment's own state, so they stay exact when the
+// segments are merged.  A CTA stops once every pixel has stopped.
 #include "render_common.cuh"
 
 namespace pulsar {
 
 namespace {
 
-template <int KMAX, int CMAX>
-__global__ void __launch_bounds__(kThreads, 2) render_fwd_kernel(const WsView v,
-                                                                 const uint32_t* __restrict__ list,
-                                                                 int store) {
+// Fields of a partial forward state, each a plane of kThreads floats.
+enum : int { kPM = 0, kPDen = 1, kPAdom = 2, kPDom = 3, kPHits = 4, kPTests = 5, kPRes = 6 };
+
+template <int CMAX>
+struct BlendState {
+  float m, den, adom;
+  int dom;            // global index of the reference sphere, -1 = background
+  float fref[CMAX];
+  float res[CMAX];
+};
+
+template <int CMAX>
+__device__ __forceinline__ void blend_hit(BlendState<CMAX>& b, float s, float od, const float* f, int id) {
+  if (s > b.m) {
+    const float sc = __expf(b.m - s);
+    b.den *= sc;
+    b.adom *= sc;
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c) b.res[c] *= sc;
+    b.m = s;
+  }
+  const float ap = od * __expf(s - b.m);
+  if (ap > b.adom) {
+    // the new hit becomes the reference: re-express the numerator
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c) {
+      b.res[c] = fmaf(b.den, b.fref[c] - f[c], b.res[c]);
+      b.fref[c] = f[c];
+    }
+    b.adom = ap;
+    b.dom = id;
+  } else {
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c) b.res[c] = fmaf(ap, f[c] - b.fref[c], b.res[c]);
+  }
+  b.den += ap;
+}
+
+// Reference feature of a sphere index (-1 = background).
+__device__ __forceinline__ const float* ref_feature(const SceneDev& S, int dom) {
+  return dom < 0 ? S.bg : S.feat + (int64_t)(dom - S.sphere_begin) * S.n_channels;
+}
+
+template <int KMAX, int CMAX, bool BLEND>
+__global__ void __launch_bounds__(kThreads, 2) traverse_kernel(const WsView v,
+                                                               const uint32_t* __restrict__ list,
+                                                               int store) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ChunkSmem<CMAX>& sm = *reinterpret_cast<ChunkSmem<CMAX>*>(smem_raw);
-  const int64_t tile = blockIdx.x;
-  const int si = scene_of_tile(v.scenes, v.n_scenes, tile);
+  __shared__ int s_last;
+  ItemCtx it;
+  if (!item_ctx(v, it)) return;
+  const int si = scene_of_tile(v.scenes, v.n_scenes, it.tile);
   const SceneDev& S = v.scenes[si];
-  const PixelCtx pc = pixel_ctx(S, tile);
-  const int2 rg = v.ranges[tile];
+  const PixelCtx pc = pixel_ctx(S, it.tile);
   const int C = S.n_channels;
   const int K = S.n_track;
   const float gamma = S.gamma, zfar = S.zfar, znear = S.znear;
@@ -37,16 +98,22 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_kernel(const WsView v,
   const float range = zfar - znear, inv_range = 1.0f / range;
   const float omax = __uint_as_float(S.omax_bits);
   const bool literal = (S.flags & PULSAR_FLAG_DIST_LITERAL) != 0;
+  const int tid = threadIdx.x;
 
-  for (int e = threadIdx.x; e < kChunk * CMAX; e += kThreads) sm.feat[e] = 0.0f;
+  if (BLEND)
+    for (int e = tid; e < kChunk * CMAX; e += kThreads) sm.feat[e] = 0.0f;
 
-  // Eq. 1 state, scaled by e^{-m}: m = running maximum exponent (starting with
-  // the background's eps / gamma), den = e^{eps/g - m} + sum a_k e^{-m}.
-  float m = S.eps * inv_gamma;
-  float den = 1.0f;
-  float acc[CMAX];
+  // the background term e^{eps/g - m} belongs to the first segment only
+  BlendState<CMAX> bs;
+  bs.m = S.eps * inv_gamma;
+  bs.den = it.seg == 0 ? 1.0f : 0.0f;
+  bs.adom = bs.den;
+  bs.dom = -1;
 #pragma unroll
-  for (int c = 0; c < CMAX; ++c) acc[c] = c < C ? S.bg[c] : 0.0f;
+  for (int c = 0; c < CMAX; ++c) {
+    bs.fref[c] = (BLEND && c < C) ? S.bg[c] : 0.0f;
+    bs.res[c] = 0.0f;
+  }
   float qt[KMAX];
   int qi[KMAX];
 #pragma unroll
@@ -60,19 +127,19 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_kernel(const WsView v,
   bool done = !pc.inside;
   float kstop1 = __int_as_float(0x7f800000);   // tracked-set bound (i)
   float kstop = kstop1;
-  const int warp = threadIdx.x >> 5;
+  const int warp = tid >> 5;
 
-  for (int base = rg.x; base < rg.y; base += kChunk) {
-    const int n = min(kChunk, rg.y - base);
+  for (int base = it.b0; base < it.b1; base += kChunk) {
+    const int n = min(kChunk, it.b1 - base);
     // remaining-mass bound (ii), from the state at the start of this chunk
     float kstop2 = -__int_as_float(0x7f800000);
-    if (!done && omax > 0.0f) {
-      const float lr = m + __logf(1e-7f * den / ((float)(rg.y - base) * omax));
+    if (BLEND && !done && omax > 0.0f) {
+      const float lr = bs.m + __logf(1e-7f * bs.den / ((float)(it.b1 - base) * omax));
       const float zthr = lr * gamma / omax;
       kstop2 = zthr >= 1.0f ? -__int_as_float(0x7f800000) : zfar - range * zthr;
     }
     kstop = fmaxf(kstop1, kstop2);
-    const int cnt = stage_chunk<CMAX>(sm, v, S, list, base, n, pc, true);
+    const int cnt = stage_chunk<CMAX>(sm, v, S, list, base, n, pc, BLEND);
     for (int k = 0; k < cnt; ++k) {
       if (__all_sync(0xffffffffu, done)) break;
       const int j = sm.list[warp][k];
@@ -88,29 +155,18 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_kernel(const WsView v,
       RayHit h;
       if (!ray_hit(a.x, a.y, a.z, a.w, b.x, pc.rx, pc.ry, zfar, h)) continue;
       ++nhit;
-      // value path
-      const float4 c2 = sm.rec2[j];
-      const ValueGeom vg = value_geom(a, c2, pc.vr);
-      const float qd = fminf(vg.dist / c2.w, 1.0f);
-      const float d = literal ? qd : 1.0f - qd;
-      const float z = (((zfar - a.z) - c2.z) + vg.off) * inv_range;
-      const float o = b.y;
-      if (o * d != 0.0f) {   // a zero weight adds nothing and must not move the shift
-        const float s = o * z * inv_gamma;
-        if (s > m) {
-          const float sc = __expf(m - s);
-          den *= sc;
-#pragma unroll
-          for (int c = 0; c < CMAX; ++c) acc[c] *= sc;
-          m = s;
-        }
-        const float w = o * d * __expf(s - m);
-        den += w;
-        const float* f = &sm.feat[j * CMAX];
-#pragma unroll
-        for (int c = 0; c < CMAX; ++c) acc[c] = fmaf(w, f[c], acc[c]);
-      }
       const int id = sm.id[j];
+      if (BLEND) {
+        const float4 c2 = sm.rec2[j];
+        const ValueGeom vg = value_geom(a, c2, pc.vr);
+        const float qd = fminf(vg.dist / c2.w, 1.0f);
+        const float d = literal ? qd : 1.0f - qd;
+        const float od = b.y * d;
+        if (od != 0.0f) {   // a zero weight adds nothing and must not move the shift
+          const float z = (((zfar - a.z) - c2.z) + vg.off) * inv_range;
+          blend_hit<CMAX>(bs, b.y * z * inv_gamma, od, &sm.feat[j * CMAX], id);
+        }
+      }
       if (hit_less(h.t, id, thr_t, thr_i)) {
         queue_insert<KMAX>(qt, qi, h.t, id);
         queue_select<KMAX>(qt, qi, K, thr_t, thr_i);
@@ -121,53 +177,159 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_kernel(const WsView v,
     if (__syncthreads_and(done)) break;
   }
 
-  if (!pc.inside) return;
-  const int64_t pix = (int64_t)pc.py * S.width + pc.px;
-  const float inv = 1.0f / den;
-  float* out = S.image + pix * C;
+  if (it.nseg > 1) {
+    // leave this segment's state, then let the tile's last segment merge
+    const int F = v.part_fields;
+    const int q0 = kPRes + C;
+    float* P = v.partial + (size_t)it.item * F * kThreads + tid;
+    if (BLEND) {
+      P[kPM * kThreads] = bs.m;
+      P[kPDen * kThreads] = bs.den;
+      P[kPAdom * kThreads] = bs.adom;
+      P[kPDom * kThreads] = __int_as_float(bs.dom);
+      P[kPTests * kThreads] = __int_as_float(ntest);
 #pragma unroll
-  for (int c = 0; c < CMAX; ++c)
-    if (c < C) out[c] = acc[c] * inv;
-  S.log_norm[pix] = m + __logf(den);
-  if (S.n_hits) S.n_hits[pix] = nhit;
-  if (S.n_tests) S.n_tests[pix] = ntest;
-  if (S.tracked) {
-    int32_t* tr = S.tracked + pix * K;
+      for (int c = 0; c < CMAX; ++c)
+        if (c < C) P[(kPRes + c) * kThreads] = bs.res[c];
+    }
+    P[kPHits * kThreads] = __int_as_float(nhit);
 #pragma unroll
     for (int k = 0; k < KMAX; ++k)
-      if (k < K) tr[k] = qi[k] == 0x7fffffff ? -1 : (int32_t)(qi[k] - S.sphere_begin);
+      if (k < K) {
+        P[(q0 + k) * kThreads] = qt[k];
+        P[(q0 + K + k) * kThreads] = __int_as_float(qi[k]);
+      }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&v.tile_done[it.tile], 1) == it.nseg - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int o = it.first; o < it.first + it.nseg; ++o) {
+      if (o == it.item) continue;
+      const float* Q = v.partial + (size_t)o * F * kThreads + tid;
+      if (BLEND) {
+        const float mB = __ldcg(Q + kPM * kThreads);
+        float denB = __ldcg(Q + kPDen * kThreads);
+        float adomB = __ldcg(Q + kPAdom * kThreads);
+        const int domB = __float_as_int(__ldcg(Q + kPDom * kThreads));
+        ntest += __float_as_int(__ldcg(Q + kPTests * kThreads));
+        const float m = fmaxf(bs.m, mB);
+        const float sa = __expf(bs.m - m), sb = __expf(mB - m);
+        bs.den *= sa;
+        bs.adom *= sa;
+        denB *= sb;
+        adomB *= sb;
+        const float* fB = ref_feature(S, domB);
+        if (adomB > bs.adom) {
+          // the other segment's reference carries more weight: re-express ours
+#pragma unroll
+          for (int c = 0; c < CMAX; ++c)
+            if (c < C) {
+              const float fb = fB[c];
+              bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * kThreads),
+                               fmaf(bs.den, bs.fref[c] - fb, bs.res[c] * sa));
+              bs.fref[c] = fb;
+            }
+          bs.adom = adomB;
+          bs.dom = domB;
+        } else {
+#pragma unroll
+          for (int c = 0; c < CMAX; ++c)
+            if (c < C)
+              bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * kThreads),
+                               fmaf(denB, fB[c] - bs.fref[c], bs.res[c] * sa));
+        }
+        bs.den += denB;
+        bs.m = m;
+      }
+      nhit += __float_as_int(__ldcg(Q + kPHits * kThreads));
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+        if (k < K) {
+          const float t = __ldcg(Q + (q0 + k) * kThreads);
+          const int id = __float_as_int(__ldcg(Q + (q0 + K + k) * kThreads));
+          if (hit_less(t, id, thr_t, thr_i)) {
+            queue_insert<KMAX>(qt, qi, t, id);
+            queue_select<KMAX>(qt, qi, K, thr_t, thr_i);
+          }
+        }
+    }
+    if (tid == 0) v.tile_done[it.tile] = 0;   // ready for the next launch
   }
-  if (store) v.thr[S.pixel_begin + pix] = make_float2(thr_t, __int_as_float(thr_i));
+
+  if (!pc.inside) return;
+  const int64_t pix = (int64_t)pc.py * S.width + pc.px;
+  const int64_t gpix = S.pixel_begin + pix;
+  if (BLEND) {
+    const float inv = 1.0f / bs.den;
+    float* out = S.image + pix * C;
+    float* fr = v.fres + gpix * C;
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c)
+      if (c < C) {
+        const float r = bs.res[c] * inv;
+        out[c] = bs.fref[c] + r;
+        fr[c] = r;
+      }
+    S.log_norm[pix] = bs.m + __logf(bs.den);
+    if (S.n_hits) S.n_hits[pix] = nhit;
+    if (S.n_tests) S.n_tests[pix] = ntest;
+    if (S.tracked) {
+      int32_t* tr = S.tracked + pix * K;
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+        if (k < K) tr[k] = qi[k] == 0x7fffffff ? -1 : (int32_t)(qi[k] - S.sphere_begin);
+    }
+    v.pix_aux[gpix] = make_float4(thr_t, __int_as_float(thr_i), __int_as_float(bs.dom), 0.0f);
+  } else {
+    reinterpret_cast<float2*>(v.pix_aux)[2 * gpix] = make_float2(thr_t, __int_as_float(thr_i));
+  }
 }
 
-template <int KMAX, int CMAX>
-cudaError_t launch_fwd_t(const WsView& v, const uint32_t* list, bool store, cudaStream_t st) {
+template <int KMAX, int CMAX, bool BLEND>
+cudaError_t launch_t(const WsView& v, const uint32_t* list, bool store, cudaStream_t st) {
   const size_t smem = sizeof(ChunkSmem<CMAX>);
-  auto kern = render_fwd_kernel<KMAX, CMAX>;
+  auto kern = traverse_kernel<KMAX, CMAX, BLEND>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)v.n_tiles, kThreads, smem, st>>>(v, list, store ? 1 : 0);
+  kern<<<(unsigned)v.max_items, kThreads, smem, st>>>(v, list, store ? 1 : 0);
   return cudaGetLastError();
 }
 
-template <int KMAX>
-cudaError_t launch_fwd_k(const WsView& v, const uint32_t* list, bool store, cudaStream_t st) {
+template <int KMAX, bool BLEND>
+cudaError_t launch_k(const WsView& v, const uint32_t* list, bool store, cudaStream_t st) {
   const int C = v.n_channels;
-  if (C <= 4) return launch_fwd_t<KMAX, 4>(v, list, store, st);
-  if (C <= 8) return launch_fwd_t<KMAX, 8>(v, list, store, st);
-  if (C <= 16) return launch_fwd_t<KMAX, 16>(v, list, store, st);
-  return launch_fwd_t<KMAX, 32>(v, list, store, st);
+  if constexpr (!BLEND) {
+    return launch_t<KMAX, 4, false>(v, list, store, st);
+  } else {
+    if (C <= 4) return launch_t<KMAX, 4, true>(v, list, store, st);
+    if (C <= 8) return launch_t<KMAX, 8, true>(v, list, store, st);
+    if (C <= 16) return launch_t<KMAX, 16, true>(v, list, store, st);
+    return launch_t<KMAX, 32, true>(v, list, store, st);
+  }
+}
+
+template <bool BLEND>
+cudaError_t launch_any(const WsView& v, bool store, cudaStream_t st) {
+  if (v.max_items == 0) return cudaSuccess;
+  const uint32_t* list = v.pval[v.pair_buf];
+  const int K = v.n_track;
+  if (K <= 8) return launch_k<8, BLEND>(v, list, store, st);
+  if (K <= 16) return launch_k<16, BLEND>(v, list, store, st);
+  return launch_k<32, BLEND>(v, list, store, st);
 }
 
 }  // namespace
 
 cudaError_t launch_render_fwd(const WsView& v, bool store, cudaStream_t st) {
-  if (v.n_tiles == 0) return cudaSuccess;
-  const uint32_t* list = v.pval[v.pair_buf];
-  const int K = v.n_track;
-  if (K <= 8) return launch_fwd_k<8>(v, list, store, st);
-  if (K <= 16) return launch_fwd_k<16>(v, list, store, st);
-  return launch_fwd_k<32>(v, list, store, st);
+  return launch_any<true>(v, store, st);
+}
+
+// Recomputes each pixel's n_track-th tracked hit (the backward pass's
+// threshold) by the forward traversal without blending.
+cudaError_t launch_track_pass(const WsView& v, cudaStream_t st) {
+  return launch_any<false>(v, false, st);
 }
 
 }  // namespace pulsar

@@ -79,29 +79,44 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
 }
 
 // Exclusive scan, in place, of rows x cols entries stored at data[r * stride + c],
-// in row-major logical order; cols = ceil(n / kSortTile).  One CTA of 1024 threads.
+// in row-major logical order; cols = ceil(n / kSortTile).  One CTA of 1024
+// threads: warps first total the rows (coalesced), the row totals are scanned,
+// then every warp scans its rows 32 entries at a time.
 __global__ void __launch_bounds__(1024) scan_table(uint32_t* __restrict__ data, int rows,
                                                    const int32_t* n_dev, int n_host, int stride) {
+  __shared__ uint32_t row_base[kRadix];
   __shared__ uint32_t warp_tot[33];
   const int n = read_count(n_dev, n_host);
   const int cols = (n + kSortTile - 1) / kSortTile;
-  const int total = rows * cols;
-  if (total == 0) return;
-  const int per = (total + 1023) / 1024;
-  const int beg = threadIdx.x * per;
-  const int end = min(beg + per, total);
-  uint32_t s = 0;
-  for (int e = beg; e < end; ++e) {
-    int r = e / cols, c = e - r * cols;
-    s += data[r * stride + c];
+  if (cols == 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = warp; r < rows; r += 32) {
+    uint32_t s = 0;
+    for (int c = lane; c < cols; c += 32) s += data[(size_t)r * stride + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) row_base[r] = s;
   }
+  __syncthreads();
+  const uint32_t mine = threadIdx.x < rows ? row_base[threadIdx.x] : 0u;
   uint32_t tot;
-  uint32_t run = block_exclusive_scan<1024>(s, warp_tot, tot);
-  for (int e = beg; e < end; ++e) {
-    int r = e / cols, c = e - r * cols;
-    uint32_t x = data[r * stride + c];
-    data[r * stride + c] = run;
-    run += x;
+  const uint32_t ex = block_exclusive_scan<1024>(mine, warp_tot, tot);
+  if (threadIdx.x < rows) row_base[threadIdx.x] = ex;
+  __syncthreads();
+  for (int r = warp; r < rows; r += 32) {
+    uint32_t carry = row_base[r];
+    for (int c0 = 0; c0 < cols; c0 += 32) {
+      const int c = c0 + lane;
+      const uint32_t x = c < cols ? data[(size_t)r * stride + c] : 0u;
+      uint32_t inc = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (c < cols) data[(size_t)r * stride + c] = carry + inc - x;
+      carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
   }
 }
 
@@ -281,6 +296,39 @@ __global__ void __launch_bounds__(kThreads) tile_ranges(WsView v, int buf) {
   }
 }
 
+// Work items of the render passes: every tile's list is cut into segments of
+// at most v.segment entries (an empty tile is one item, so its pixels are
+// still written).  Writes item_begin (n_tiles + 1), item_tile, the item count,
+// and clears the per-tile merge counters.
+__global__ void __launch_bounds__(1024) make_items(WsView v) {
+  __shared__ uint32_t warp_tot[33];
+  const int64_t nt = v.n_tiles;
+  const int64_t per = (nt + 1023) / 1024;
+  const int64_t t0 = (int64_t)threadIdx.x * per;
+  const int64_t t1 = t0 + per < nt ? t0 + per : nt;
+  uint32_t s = 0;
+  for (int64_t t = t0; t < t1; ++t) {
+    const int2 rg = v.ranges[t];
+    const int len = rg.y - rg.x;
+    s += len > 0 ? (uint32_t)((len + v.segment - 1) / v.segment) : 1u;
+  }
+  uint32_t tot;
+  uint32_t base = block_exclusive_scan<1024>(s, warp_tot, tot);
+  for (int64_t t = t0; t < t1; ++t) {
+    const int2 rg = v.ranges[t];
+    const int len = rg.y - rg.x;
+    const uint32_t ns = len > 0 ? (uint32_t)((len + v.segment - 1) / v.segment) : 1u;
+    v.item_begin[t] = (int32_t)base;
+    for (uint32_t k = 0; k < ns; ++k) v.item_tile[base + k] = (int32_t)t;
+    v.tile_done[t] = 0;
+    base += ns;
+  }
+  if (threadIdx.x == 0) {
+    v.item_begin[nt] = (int32_t)tot;
+    v.hdr->n_items = (int32_t)tot;
+  }
+}
+
 cudaError_t radix_sort(const WsView& v, uint32_t* keys[2], uint32_t* vals[2], const int32_t* n_dev,
                        int n_host, int max_items, int bits, int& buf, cudaStream_t st) {
   const int blocks = (max_items + kSortTile - 1) / kSortTile;
@@ -333,6 +381,8 @@ cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st) {
     const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
     tile_ranges<<<blocks, kThreads, 0, st>>>(v, pbuf);
   }
+  // 6. work items of the render passes
+  if (v.n_tiles > 0) make_items<<<1, 1024, 0, st>>>(v);
   return cudaGetLastError();
 }
 

@@ -63,11 +63,13 @@ def test_workspace_size_validates_settings(lib):
         assert lib.lib().pulsar_workspace_size(ctypes.byref(_params(lib, **b))) == 0, b
 
 
-def test_workspace_grows_with_capacity_and_store_mode(lib):
+def test_workspace_grows_with_capacity_channels_and_track(lib):
     a = lib.lib().pulsar_workspace_size(ctypes.byref(_params(lib)))
     b = lib.lib().pulsar_workspace_size(ctypes.byref(_params(lib, list_capacity=100000)))
     c = lib.lib().pulsar_workspace_size(ctypes.byref(_params(lib, flags=0)))
-    assert b > a and c < a
+    d = lib.lib().pulsar_workspace_size(ctypes.byref(_params(lib, n_channels=16, n_track=16)))
+    assert b > a and d > a
+    assert c == a   # the per-pixel backward data is kept in both modes
 
 
 def test_entry_points_reject_bad_arguments_before_any_launch(lib):

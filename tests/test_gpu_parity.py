@@ -161,8 +161,7 @@ def test_gradients_match_central_differences(orc):
     sph = np.random.default_rng(2).choice(seen, 8, replace=False)
     base = {k: getattr(sc, k).astype(np.float64) for k in ("pos", "rad", "opa", "feat", "cam", "bg")}
 
-    def fd(name, idx):
-        h = 1e-5 * max(1.0, abs(float(base[name].reshape(-1)[idx])))
+    def fd(name, idx, h):
         vals = []
         for s in (1, -1, 2, -2):
             arr = {k: v.copy() for k, v in base.items()}
@@ -173,10 +172,17 @@ def test_gradients_match_central_differences(orc):
     checks = [("pos", 3 * i + k) for i in sph for k in range(3)] + [("opa", i) for i in sph] + \
              [("rad", i) for i in sph] + [("feat", 3 * i) for i in sph[:3]] + [("cam", k) for k in range(11)]
     scale = {n: max(np.abs(got[n]).max(), 1e-12) for n in got}
+    checked = 0
     for name, idx in checks:
-        want = fd(name, idx)
+        h = 2e-6 * max(1.0, abs(float(base[name].reshape(-1)[idx])))
+        want, want2 = fd(name, idx, h), fd(name, idx, h / 2)
+        tol = 1e-3 * (abs(want) + 1e-3 * scale[name]) + 1e-7
+        if abs(want - want2) > 1e-2 * tol:
+            continue   # the stencil crosses a kink of d (a sphere's rim or centre): not differentiable
         g = got[name].reshape(-1)[idx]
-        assert abs(g - want) <= 1e-3 * (abs(want) + 1e-3 * scale[name]) + 1e-7, (name, idx, g, want)
+        assert abs(g - want) <= tol, (name, idx, g, want)
+        checked += 1
+    assert checked >= int(0.8 * len(checks)), (checked, len(checks))
 
 
 @pytest.mark.parametrize("gamma", [1e-3, 1e-2, 0.1, 1.0])
