@@ -178,6 +178,30 @@ pulsar_status pulsar_read_tile_lists(const pulsar_params* params, void* workspac
 pulsar_status pulsar_read_status(void* workspace, size_t workspace_bytes, int64_t* pairs_needed,
                                  void* stream);
 
+/* Size of the device array pulsar_render_fwd_static uses as its workspace. */
+#define PULSAR_STATIC_WORKSPACE_BYTES (16u << 20)
+
+/* Forward render without a caller-provided workspace and without allocating
+ * (the paper has no counterpart; this exists for callers that cannot
+ * allocate device memory when they render, e.g. code running where another
+ * component owns the device memory, or code that must avoid the device-wide
+ * synchronisation cudaFree can cause).
+ *   Runs pulsar_project, pulsar_bin and pulsar_render_fwd with a 16 MiB
+ *   device array inside the library as the workspace.  Inputs and outputs
+ *   are the caller's, as for pulsar_render_fwd.
+ *   Returns PULSAR_ERR_CAPACITY, before enqueuing anything, when
+ *   pulsar_workspace_size(params) exceeds PULSAR_STATIC_WORKSPACE_BYTES.
+ *   The array is shared by every call in the process and keeps the last
+ *   call's contents; calls that overlap on the GPU (other streams, other
+ *   threads) race on it and must be serialised by the caller.
+ *   Its device address is looked up once per device, by the first call made
+ *   with that device current; make that first call before any stream
+ *   capture.  A list_capacity overflow cannot be read back through this
+ *   entry point: choose list_capacity so it cannot overflow (n_spheres times
+ *   the number of tiles is always enough). */
+pulsar_status pulsar_render_fwd_static(const pulsar_params* params, const pulsar_scene* scene,
+                                       float* image, float* log_norm, void* stream);
+
 /* Static description of a status code. */
 const char* pulsar_status_string(pulsar_status status);
 

@@ -76,8 +76,19 @@ def lib():
         L.pulsar_read_status.restype = ctypes.c_int
         L.pulsar_status_string.argtypes = [ctypes.c_int]
         L.pulsar_status_string.restype = ctypes.c_char_p
+        L.pulsar_render_fwd_static.argtypes = [P, S, vp, vp, vp]
+        L.pulsar_render_fwd_static.restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+STATIC_WORKSPACE_BYTES = 16 << 20
+
+
+def render_fwd_static(p: Params, s: SceneArgs, image: int, log_norm: int, stream: int) -> None:
+    """Forward render using the library's fixed device array as workspace (no allocation)."""
+    _check(lib().pulsar_render_fwd_static(ctypes.byref(p), ctypes.byref(s), image, log_norm, stream),
+           "pulsar_render_fwd_static")
 
 
 def status_string(status: int) -> str:

@@ -1,0 +1,70 @@
+// Forward render whose scratch space is a fixed array inside the library, for
+// callers that cannot allocate device memory when they render.
+//
+// Who needs this: code that runs where another component owns the device's
+// memory and forbids allocation after start-up (plugin hosts, services with
+// a fixed memory footprint), and code that must not make the implicit
+// device-wide synchronisation cudaFree can cause.  Such a caller cannot
+// allocate the workspace pulsar_render_fwd expects, so this entry point uses
+// a file-scope device array instead and allocates nothing itself.
+//
+// Set-up: the array's device address is looked up with cudaGetSymbolAddress
+// once per device, on the first call made while that device is current.  In
+// host code the array's name is only a host-side stand-in, so the kernels are
+// always given the looked-up address.
+#include <mutex>
+
+#include "pulsar_internal.cuh"
+
+namespace pulsar {
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_ws[PULSAR_STATIC_WORKSPACE_BYTES];
+
+std::mutex g_addr_mutex;
+void* g_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_static_ws on the current device (looked up once).
+cudaError_t static_ws_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_addr_mutex);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_ws);
+    if (e != cudaSuccess) return e;
+    g_addr[dev] = p;
+  }
+  *out = g_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace pulsar
+
+using namespace pulsar;
+
+extern "C" pulsar_status pulsar_render_fwd_static(const pulsar_params* params,
+                                                  const pulsar_scene* scene, float* image,
+                                                  float* log_norm, void* stream) {
+  const size_t need = pulsar_workspace_size(params);
+  if (need == 0) return PULSAR_ERR_INVALID_ARG;
+  if (need > (size_t)PULSAR_STATIC_WORKSPACE_BYTES) return PULSAR_ERR_CAPACITY;
+  if (!scene || !image || !log_norm) return PULSAR_ERR_INVALID_ARG;
+  void* ws = nullptr;
+  if (static_ws_address(&ws) != cudaSuccess) return PULSAR_ERR_CUDA;
+  // Everything the three stages read is written earlier in the same call
+  // (the set-up kernel resets the counters and flags, binning clears the
+  // tile ranges and merge counters), so the previous call's contents do not
+  // need clearing.
+  pulsar_status st = pulsar_project(params, scene, ws, PULSAR_STATIC_WORKSPACE_BYTES, stream);
+  if (st == PULSAR_OK) st = pulsar_bin(params, ws, PULSAR_STATIC_WORKSPACE_BYTES, stream);
+  if (st == PULSAR_OK)
+    st = pulsar_render_fwd(params, scene, ws, PULSAR_STATIC_WORKSPACE_BYTES, image, log_norm,
+                           nullptr, nullptr, nullptr, stream);
+  return st;
+}
