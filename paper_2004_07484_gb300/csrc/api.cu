@@ -95,10 +95,11 @@ Layout make_layout(const pulsar_params* ps, int n) {
   L.ranges = take(8 * (size_t)NT);
   L.item_begin = take(4 * (size_t)(NT + 1));
   L.item_tile = take(4 * (size_t)L.max_items);
-  L.tile_done = take(4 * (size_t)NT);
-  L.partial = take(4 * (size_t)L.max_items * kThreads * L.part_fields);
-  L.item_kappa = take(4 * (size_t)L.max_items);
-  L.tile_bg = take(4 * (size_t)NT * C);
+  // per (tile or work item) x 8 pixel blocks of 32 pixels
+  L.tile_done = take(4 * 8 * (size_t)NT);
+  L.partial = take(4 * 8 * (size_t)L.max_items * 32 * L.part_fields);
+  L.item_kappa = take(4 * 8 * (size_t)L.max_items);
+  L.tile_bg = take(4 * 8 * (size_t)NT * C);
   L.pix_aux = take(16 * (size_t)P);
   L.fres = take(4 * (size_t)P * C);
   L.gacc = take(16 * (size_t)M);

@@ -208,8 +208,8 @@ __global__ void __launch_bounds__(1024) camera_reduce_kernel(WsView v, uint32_t 
       float x = 0.0f;
       for (int b = threadIdx.x; b < S.fin_blocks; b += blockDim.x)
         x += v.fin_part[(size_t)(S.fin_block_begin + b) * kCamPartials + k];
-      if (k == 12) {
-        const int i0 = v.item_begin[S.tile_begin], i1 = v.item_begin[S.tile_begin + nt];
+      if (k == 12) {   // per (work item, pixel block) slots of this scene
+        const int i0 = 8 * v.item_begin[S.tile_begin], i1 = 8 * v.item_begin[S.tile_begin + nt];
         for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) x += v.item_kappa[i];
       }
       float r = block_sum(x, sh);
@@ -217,10 +217,10 @@ __global__ void __launch_bounds__(1024) camera_reduce_kernel(WsView v, uint32_t 
     }
   }
   if (mask & PULSAR_GRAD_BG) {
-    for (int c = 0; c < C; ++c) {
-      const float* row = v.tile_bg + (size_t)c * v.n_tiles + S.tile_begin;
+    for (int c = 0; c < C; ++c) {   // per (tile, pixel block) partials
+      const float* row = v.tile_bg + (size_t)c * v.n_tiles * 8 + S.tile_begin * 8;
       float x = 0.0f;
-      for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) x += row[t];
+      for (int64_t t = threadIdx.x; t < 8 * nt; t += blockDim.x) x += row[t];
       float r = block_sum(x, sh);
       if (threadIdx.x == 0) S.g_bg[c] = r;
     }

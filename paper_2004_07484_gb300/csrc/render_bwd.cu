@@ -4,8 +4,8 @@
 // tracked hit.  That threshold is kept per pixel by the forward pass (store
 // mode, App. B "Preparing for the Backward Pass") or recomputed before this
 // pass by the forward traversal without blending (recompute mode).  Work is
-// split into the same (tile, segment) items as the forward pass; gradients
-// are sums, so segments need no merge.  All lanes of a warp visit the same
+// split into the same one-warp (segment, pixel block) CTAs as the forward
+// pass; gradients are sums, so segments need no merge.  All lanes of a warp visit the same
 // sphere at the same time, so each sphere's per-pixel contributions are
 // summed across the warp with shuffles before one set of (vector) atomics per
 // warp and sphere.  A segment stops at the first key beyond every pixel's
@@ -79,17 +79,16 @@ __device__ __forceinline__ void warp_reduce_and_add(bool tracked, int id_global,
 }
 
 template <int CMAX>
-__global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
-                                                                 const uint32_t* __restrict__ list,
-                                                                 uint32_t mask) {
+__global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v,
+                                                            const uint32_t* __restrict__ list,
+                                                            uint32_t mask) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ChunkSmem<CMAX>& sm = *reinterpret_cast<ChunkSmem<CMAX>*>(smem_raw);
-  __shared__ float red[kThreads / 32][CMAX + 1];
+  WarpStage<CMAX>& st = *reinterpret_cast<WarpStage<CMAX>*>(smem_raw);
   ItemCtx it;
   if (!item_ctx(v, it)) return;
   const int si = scene_of_tile(v.scenes, v.n_scenes, it.tile);
   const SceneDev& S = v.scenes[si];
-  const PixelCtx pc = pixel_ctx(S, it.tile);
+  const PixelCtx pc = pixel_ctx(S, it.tile, it.block);
   const int C = S.n_channels;
   const float gamma = S.gamma, zfar = S.zfar, znear = S.znear;
   const float inv_gamma = 1.0f / gamma;
@@ -100,9 +99,10 @@ __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
   const bool feat = (mask & PULSAR_GRAD_FEAT) != 0;
   const bool cam = (mask & PULSAR_GRAD_CAM) != 0;
   const bool bgw = (mask & PULSAR_GRAD_BG) != 0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
 
-  for (int e = threadIdx.x; e < kChunk * CMAX; e += kThreads) sm.feat[e] = 0.0f;
+  for (int e = lane; e < 32 * CMAX; e += 32) st.feat[e] = 0.0f;   // channels beyond C stay zero
+  __syncwarp();
 
   // per-pixel upstream data
   const int64_t pix = pc.inside ? (int64_t)pc.py * S.width + pc.px : 0;
@@ -131,39 +131,33 @@ __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
     logD = S.log_norm_in[pix];
   }
 
-  // background gradient: sum over the tile of w_B G (first segment only)
+  // background gradient: sum over the block of w_B G (first segment only)
   if (bgw && it.seg == 0) {
     const float wB = pc.inside ? __expf(S.eps * inv_gamma - logD) : 0.0f;
+    const size_t nb = (size_t)v.n_tiles * kBlocksPerTile;
 #pragma unroll
     for (int c = 0; c < CMAX; ++c) {
-      float x = warp_sum(wB * G[c]);
-      if (lane == 0 && c < C) red[warp][c] = x;
+      const float x = warp_sum(wB * G[c]);
+      if (lane == 0 && c < C) v.tile_bg[(size_t)c * nb + it.tile * kBlocksPerTile + it.block] = x;
     }
-    __syncthreads();
-    if (threadIdx.x < C) {
-      float s = 0.0f;
-      for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
-      v.tile_bg[(size_t)threadIdx.x * v.n_tiles + it.tile] = s;
-    }
-    __syncthreads();
   }
   if (!(geo || opa || feat)) {
-    if (cam && threadIdx.x == 0) v.item_kappa[it.item] = 0.0f;
+    if (cam && lane == 0) v.item_kappa[it.slot] = 0.0f;
     return;
   }
 
   const float kstop = next_up(thr_t);
   bool done = !pc.inside;
   float gk_sum = 0.0f;
-  for (int base = it.b0; base < it.b1; base += kChunk) {
-    const int n = min(kChunk, it.b1 - base);
-    const int cnt = stage_chunk<CMAX>(sm, v, S, list, base, n, pc, true);
+  const WarpRect wr = warp_rect(pc, it.block);
+  for (int base = it.b0; base < it.b1; base += 32) {
+    if (__all_sync(0xffffffffu, done)) break;
+    const int cnt = stage_warp<CMAX>(st, v, S, list, base, it.b1, wr, true, true);
     for (int k = 0; k < cnt; ++k) {
       if (__all_sync(0xffffffffu, done)) break;
-      const int j = sm.list[warp][k];
-      const float4 a = sm.rec0[j];
-      const float4 b = sm.rec1[j];
-      const int id = sm.id[j];
+      const float4 a = st.rec0[k];
+      const float4 b = st.rec1[k];
+      const int id = st.id[k];
       bool tracked = false;
       float gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, gR = 0.f, go = 0.f;
       float gf[CMAX];
@@ -177,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
           if (ray_hit(a.x, a.y, a.z, a.w, b.x, pc.rx, pc.ry, zfar, h) &&
               !hit_less(thr_t, thr_i, h.t, id)) {
             tracked = true;
-            const float4 c2 = sm.rec2[j];
+            const float4 c2 = st.rec2[k];
             const ValueGeom g = value_geom(a, c2, pc.vr);
             const float R = c2.w;
             const float inv_rr = vdiv(1.0f, g.rr);
@@ -193,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
             // exponent may exceed log D by any amount
             const float E = __expf(fminf(s - logD, 80.0f));
             const float w = o * d * E;
-            const float* f = &sm.feat[j * CMAX];
+            const float* f = &st.feat[k * CMAX];
             float gdot;   // G.(f_i - F)
             if (id == dom) {
               gdot = -GFres;
@@ -257,28 +251,18 @@ __global__ void __launch_bounds__(kThreads, 2) render_bwd_kernel(const WsView v,
       warp_reduce_and_add<CMAX>(tracked, id, (int64_t)id - S.sphere_begin, gc0, gc1, gc2, gR, go,
                                 gf, C, v, S, geo, opa, feat);
     }
-    if (__syncthreads_and(done)) break;
   }
   if (cam) {
     const float x = warp_sum(gk_sum);
-    __syncthreads();
-    if (lane == 0) red[warp][0] = x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float s = 0.0f;
-      for (int w = 0; w < kThreads / 32; ++w) s += red[w][0];
-      v.item_kappa[it.item] = s;
-    }
+    if (lane == 0) v.item_kappa[it.slot] = x;
   }
 }
 
 template <int CMAX>
 cudaError_t launch_bwd_t(const WsView& v, const uint32_t* list, uint32_t mask, cudaStream_t st) {
-  const size_t smem = sizeof(ChunkSmem<CMAX>);
+  const size_t smem = sizeof(WarpStage<CMAX>);
   auto kern = render_bwd_kernel<CMAX>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)v.max_items, kThreads, smem, st>>>(v, list, mask);
+  kern<<<(unsigned)v.max_items * kBlocksPerTile, 32, smem, st>>>(v, list, mask);
   return cudaGetLastError();
 }
 

@@ -1,12 +1,15 @@
 // Tile traversal shared by the forward and backward render kernels.
 //
-// One CTA renders one 16 x 16 screen tile; each warp owns an 8 x 4 pixel
-// block and each thread one pixel, so parallelism is over pixels as the paper
-// prescribes (Sec. 3.2, App. B).  The tile's depth-ordered sphere list is
-// streamed in chunks of 256 spheres: each thread stages one draw record, the
-// CTA stages the feature vectors, and every warp compacts the staged spheres
-// whose rectangles overlap its pixel block with a ballot + popcount scan
-// (App. B, Step 1: block-wise intersection search with cooperative filtering).
+// A 16 x 16 screen tile is rendered as eight 8 x 4 pixel blocks, one warp
+// each, and each thread renders one pixel, so parallelism is over pixels as
+// the paper prescribes (Sec. 3.2, App. B).  Every warp is its own CTA and
+// walks one segment of its tile's depth-ordered sphere list independently:
+// it reads 32 list entries at a time, keeps those whose pixel rectangle
+// overlaps its block (a ballot over the lanes, compacted with a popcount
+// scan) and stages their draw records and features in shared memory (App. B,
+// Step 1: block-wise intersection search with cooperative filtering).  A
+// warp with few candidates therefore never waits for a busy neighbour and
+// frees its slot as soon as it is done.
 #pragma once
 
 #include "pulsar_internal.cuh"
@@ -19,21 +22,24 @@ __device__ __forceinline__ unsigned lane_lt_mask() {
   return m;
 }
 
-// Shared-memory layout of one chunk.
+// One warp's staged spheres (at most 32, compacted).
 template <int CMAX>
-struct ChunkSmem {
-  float4 rec0[kChunk];
-  float4 rec1[kChunk];
-  float4 rec2[kChunk];
-  float feat[kChunk * CMAX];
-  int32_t id[kChunk];
-  uint8_t mask[kChunk];
-  uint8_t list[kThreads / 32][kChunk];
+struct WarpStage {
+  float4 rec0[32];
+  float4 rec1[32];
+  float4 rec2[32];
+  int32_t id[32];
+  float feat[32 * CMAX];
 };
 
-// One work item: a segment of at most `segment` entries of one tile's list.
+constexpr int kBlocksPerTile = 8;   // 8 x 4 pixel blocks (warps) per 16 x 16 tile
+
+// One work item: a segment of at most `segment` entries of one tile's list;
+// each of its eight pixel blocks is a separate one-warp CTA.
 struct ItemCtx {
-  int item;          // work-item index (also the partial-state slot)
+  int item;          // work-item index
+  int block;         // pixel block of the tile (0..7)
+  int slot;          // item * 8 + block: partial-state and partial-sum slot
   int64_t tile;      // global tile index
   int seg, nseg;     // segment index and segment count of the tile
   int first;         // first work item of the tile
@@ -42,7 +48,9 @@ struct ItemCtx {
 
 // Returns false for grid slots beyond the number of work items.
 __device__ __forceinline__ bool item_ctx(const WsView& v, ItemCtx& c) {
-  c.item = blockIdx.x;
+  c.item = blockIdx.x / kBlocksPerTile;
+  c.block = blockIdx.x % kBlocksPerTile;
+  c.slot = blockIdx.x;
   if (c.item >= v.hdr->n_items) return false;
   c.tile = v.item_tile[c.item];
   c.first = v.item_begin[c.tile];
@@ -64,11 +72,11 @@ struct PixelCtx {
   ValueRay vr;            // ray slopes for the value path
 };
 
-__device__ __forceinline__ PixelCtx pixel_ctx(const SceneDev& S, int64_t tile) {
+__device__ __forceinline__ PixelCtx pixel_ctx(const SceneDev& S, int64_t tile, int block) {
   PixelCtx c;
   const int64_t lt = tile - S.tile_begin;
   const int ty = (int)(lt / S.tiles_x), tx = (int)(lt - (int64_t)ty * S.tiles_x);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = block, lane = threadIdx.x & 31;
   c.tile_x0 = tx * kTile;
   c.tile_y0 = ty * kTile;
   c.px = c.tile_x0 + (warp & 1) * 8 + (lane & 7);
@@ -80,57 +88,81 @@ __device__ __forceinline__ PixelCtx pixel_ctx(const SceneDev& S, int64_t tile) {
   return c;
 }
 
-// Stages list[base, base + n) into shared memory and builds every warp's
-// compacted list.  Returns this warp's list length.  Ends with a CTA barrier.
+// Pixel rectangle of a warp's 8 x 4 block.
+struct WarpRect {
+  int x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ WarpRect warp_rect(const PixelCtx& pc, int block) {
+  const int warp = block;
+  WarpRect r;
+  r.x0 = pc.tile_x0 + (warp & 1) * 8;
+  r.x1 = r.x0 + 7;
+  r.y0 = pc.tile_y0 + (warp >> 1) * 4;
+  r.y1 = r.y0 + 3;
+  return r;
+}
+
+__device__ __forceinline__ bool rect_overlaps(const float4& b, const WarpRect& r) {
+  const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
+  return (int)(bx & 0xffffu) <= r.x1 && (int)(bx >> 16) >= r.x0 && (int)(by & 0xffffu) <= r.y1 &&
+         (int)(by >> 16) >= r.y0;
+}
+
+// Stages the entries of list[base, min(base + 32, end)) whose rectangles
+// overlap the warp's block into the warp's stage, in list order.  Returns
+// how many were staged.  Called by all 32 lanes; ends with a warp barrier.
 template <int CMAX>
-__device__ __forceinline__ int stage_chunk(ChunkSmem<CMAX>& sm, const WsView& v, const SceneDev& S,
-                                           const uint32_t* __restrict__ list, int base, int n,
-                                           const PixelCtx& pc, bool need_feat) {
-  const int tid = threadIdx.x;
-  __syncthreads();   // the previous chunk is no longer read
-  if (tid < n) {
-    const uint32_t id = list[base + tid];
-    const float4 a = v.rec0[id];
-    const float4 b = v.rec1[id];
-    sm.id[tid] = (int32_t)id;
-    sm.rec0[tid] = a;
-    sm.rec1[tid] = b;
-    sm.rec2[tid] = v.rec2[id];
-    const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
-    const int x0 = (int)(bx & 0xffffu), x1 = (int)(bx >> 16);
-    const int y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
-    uint32_t cm = 0u;
-    if (x0 <= pc.tile_x0 + 7 && x1 >= pc.tile_x0) cm |= 1u;
-    if (x0 <= pc.tile_x0 + 15 && x1 >= pc.tile_x0 + 8) cm |= 2u;
-    uint32_t m = 0u;
+__device__ __forceinline__ int stage_warp(WarpStage<CMAX>& st, const WsView& v, const SceneDev& S,
+                                          const uint32_t* __restrict__ list, int base, int end,
+                                          const WarpRect& wr, bool need_rec2, bool need_feat) {
+  const int lane = threadIdx.x & 31;
+  const int idx = base + lane;
+  bool ok = idx < end;
+  uint32_t id = 0;
+  float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (ok) {
+    id = __ldg(list + idx);
+    b = __ldg(v.rec1 + id);
+    ok = rect_overlaps(b, wr);
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, ok);
+  __syncwarp();   // the previous batch is no longer read
+  if (ok) {
+    const int pos = __popc(bal & lane_lt_mask());
+    st.rec1[pos] = b;
+    st.rec0[pos] = __ldg(v.rec0 + id);
+    if (need_rec2) st.rec2[pos] = __ldg(v.rec2 + id);
+    st.id[pos] = (int32_t)id;
+    if (need_feat) {
+      const int C = S.n_channels;
+      const float* __restrict__ src = S.feat + (int64_t)(id - S.sphere_begin) * C;
+      float* dst = &st.feat[pos * CMAX];
+      if ((C & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int ya = pc.tile_y0 + 4 * r;
-      if (y0 <= ya + 3 && y1 >= ya) m |= cm << (2 * r);
-    }
-    sm.mask[tid] = (uint8_t)m;
-  }
-  __syncthreads();
-  if (need_feat) {
-    const int C = S.n_channels;
-    const float* __restrict__ feat = S.feat;
-    const int64_t sb = S.sphere_begin;
-    for (int e = tid; e < n * C; e += kThreads) {
-      const int s = e / C, c = e - s * C;
-      sm.feat[s * CMAX + c] = __ldg(feat + (int64_t)(sm.id[s] - sb) * C + c);
+        for (int c = 0; c < CMAX; c += 4)
+          if (c < C) *reinterpret_cast<float4*>(dst + c) = __ldg(reinterpret_cast<const float4*>(src + c));
+      } else {
+#pragma unroll
+        for (int c = 0; c < CMAX; ++c)
+          if (c < C) dst[c] = __ldg(src + c);
+      }
     }
   }
-  const int warp = tid >> 5, lane = tid & 31;
-  int cnt = 0;
-  for (int g = 0; g < n; g += 32) {
-    const int j = g + lane;
-    const bool f = j < n && ((sm.mask[j] >> warp) & 1u);
-    const unsigned bal = __ballot_sync(0xffffffffu, f);
-    if (f) sm.list[warp][cnt + __popc(bal & lane_lt_mask())] = (uint8_t)j;
-    cnt += __popc(bal);
-  }
-  __syncthreads();
-  return cnt;
+  __syncwarp();
+  return __popc(bal);
+}
+
+// Hit predicate without the depth: the sign test of ray_hit's discriminant,
+// with the same operations, so it decides exactly as ray_hit does.
+__device__ __forceinline__ bool ray_disc_positive(float cx, float cy, float cz, float R2, float rx,
+                                                  float ry) {
+  const float ex = __fmaf_rn(cz, rx, -cx);
+  const float ey = __fmaf_rn(cz, ry, -cy);
+  const float ez = __fmaf_rn(cx, ry, -__fmul_rn(cy, rx));
+  const float cr2 = __fmaf_rn(ex, ex, __fmaf_rn(ey, ey, __fmul_rn(ez, ez)));
+  const float rr = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, 1.0f));
+  return __fmaf_rn(rr, R2, -cr2) > 0.0f;
 }
 
 __device__ __forceinline__ bool in_rect(const float4& b, int px, int py) {

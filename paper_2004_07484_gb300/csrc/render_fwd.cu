@@ -1,17 +1,28 @@
 // Forward pass: App. B, Step 1 (intersection search) and Step 2 (draw).
 //
 // Work decomposition.  A tile's depth-ordered list is cut into segments of
-// at most `segment` entries and every (tile, segment) work item gets its own
-// CTA, so a few very long lists no longer serialise the launch.  Eq. 1 is a
-// commutative sum (App. A) and the n_track closest hits of a union are the
-// closest of the per-part closest, so segments are combined afterwards: the
-// CTA that finishes a tile's segments last (a per-tile atomic counter) merges
-// the partial states the others left in the workspace and writes the pixel.
+// at most `segment` entries, and every (segment, 8 x 4 pixel block) pair is
+// one warp-sized CTA, so a few very long lists no longer serialise the launch
+// and an idle block never waits for a busy one.  Eq. 1 is a commutative sum
+// (App. A) and the n_track closest hits of a union are the closest of the
+// per-part closest, so segments are combined afterwards: the warp that
+// finishes a block's segments last (a per-block atomic counter) merges the
+// partial states the others left in the workspace and writes the pixels.
 //
-// Per pixel, hits are blended in list order with the largest exponent
-// o z / gamma divided out of numerator and denominator, and the numerator is
-// kept relative to a reference feature: the feature of the hit with the
-// largest weight so far (initially the background), i.e. the state is
+// Each batch of up to 32 staged spheres is handled in two phases: every lane
+// first runs the cheap float32 hit test of its pixel against all of them and
+// records its hits in a bit mask, then lanes walk their own hits in list
+// order.  The expensive per-hit work (hit depth, Eq. 1 update, queue) thus
+// runs once per hit of the busiest lane instead of once per sphere any lane
+// hits.  Handling a lane's hits in list order (and skipping its non-hits)
+// leaves every decision unchanged: keys rise along the list and the stop
+// bound only falls, so the first hit at or beyond the bound is where a pixel
+// would have stopped anyway.
+//
+// Per pixel, hits are blended with the largest exponent o z / gamma divided
+// out of numerator and denominator, and the numerator is kept relative to a
+// reference feature: the feature of the hit with the largest weight so far
+// (initially the background), i.e. the state is
 //   den = e^{eps/g - m} + sum_k a_k e^{-m},
 //   res = sum_k a_k e^{-m} (f_k - f_ref) + e^{eps/g - m} (bg - f_ref),
 //   F   = f_ref + res / den.
@@ -29,14 +40,14 @@
 //        at most 1e-7 of the segment's own denominator (a lower bound of the
 //        pixel's).
 // Both tests only use the segment's own state, so they stay exact when the
-// segments are merged.  A CTA stops once every pixel has stopped.
+// segments are merged.
 #include "render_common.cuh"
 
 namespace pulsar {
 
 namespace {
 
-// Fields of a partial forward state, each a plane of kThreads floats.
+// Fields of a partial forward state, each a plane of 32 floats (one per lane).
 enum : int { kPM = 0, kPDen = 1, kPAdom = 2, kPDom = 3, kPHits = 4, kPTests = 5, kPRes = 6 };
 
 template <int CMAX>
@@ -80,17 +91,17 @@ __device__ __forceinline__ const float* ref_feature(const SceneDev& S, int dom) 
 }
 
 template <int KMAX, int CMAX, bool BLEND>
-__global__ void __launch_bounds__(kThreads, 2) traverse_kernel(const WsView v,
-                                                               const uint32_t* __restrict__ list,
-                                                               int store) {
+__global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
+                                                          const uint32_t* __restrict__ list,
+                                                          int store) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ChunkSmem<CMAX>& sm = *reinterpret_cast<ChunkSmem<CMAX>*>(smem_raw);
-  __shared__ int s_last;
+  WarpStage<CMAX>& st = *reinterpret_cast<WarpStage<CMAX>*>(smem_raw);
   ItemCtx it;
   if (!item_ctx(v, it)) return;
   const int si = scene_of_tile(v.scenes, v.n_scenes, it.tile);
   const SceneDev& S = v.scenes[si];
-  const PixelCtx pc = pixel_ctx(S, it.tile);
+  const PixelCtx pc = pixel_ctx(S, it.tile, it.block);
+  const WarpRect wr = warp_rect(pc, it.block);
   const int C = S.n_channels;
   const int K = S.n_track;
   const float gamma = S.gamma, zfar = S.zfar, znear = S.znear;
@@ -98,10 +109,11 @@ __global__ void __launch_bounds__(kThreads, 2) traverse_kernel(const WsView v,
   const float range = zfar - znear, inv_range = 1.0f / range;
   const float omax = __uint_as_float(S.omax_bits);
   const bool literal = (S.flags & PULSAR_FLAG_DIST_LITERAL) != 0;
-  const int tid = threadIdx.x;
+  const int lane = threadIdx.x;
 
-  if (BLEND)
-    for (int e = tid; e < kChunk * CMAX; e += kThreads) sm.feat[e] = 0.0f;
+  if (BLEND)   // feature channels beyond C stay zero
+    for (int e = lane; e < 32 * CMAX; e += 32) st.feat[e] = 0.0f;
+  __syncwarp();
 
   // the background term e^{eps/g - m} belongs to the first segment only
   BlendState<CMAX> bs;
@@ -126,94 +138,104 @@ __global__ void __launch_bounds__(kThreads, 2) traverse_kernel(const WsView v,
   int nhit = 0, ntest = 0;
   bool done = !pc.inside;
   float kstop1 = __int_as_float(0x7f800000);   // tracked-set bound (i)
-  float kstop = kstop1;
-  const int warp = tid >> 5;
 
-  for (int base = it.b0; base < it.b1; base += kChunk) {
-    const int n = min(kChunk, it.b1 - base);
-    // remaining-mass bound (ii), from the state at the start of this chunk
+  for (int base = it.b0; base < it.b1; base += 32) {
+    if (__all_sync(0xffffffffu, done)) break;
+    // remaining-mass bound (ii), from the state at the start of this batch
     float kstop2 = -__int_as_float(0x7f800000);
     if (BLEND && !done && omax > 0.0f) {
       const float lr = bs.m + __logf(1e-7f * bs.den / ((float)(it.b1 - base) * omax));
       const float zthr = lr * gamma / omax;
       kstop2 = zthr >= 1.0f ? -__int_as_float(0x7f800000) : zfar - range * zthr;
     }
-    kstop = fmaxf(kstop1, kstop2);
-    const int cnt = stage_chunk<CMAX>(sm, v, S, list, base, n, pc, BLEND);
-    for (int k = 0; k < cnt; ++k) {
-      if (__all_sync(0xffffffffu, done)) break;
-      const int j = sm.list[warp][k];
-      const float4 a = sm.rec0[j];
-      const float4 b = sm.rec1[j];
-      if (done) continue;
-      if (b.x >= kstop) {
-        done = true;
-        continue;
+    const int cnt = stage_warp<CMAX>(st, v, S, list, base, it.b1, wr, BLEND, BLEND);
+    // phase 1: which staged spheres does this lane's ray meet?
+    uint32_t hits = 0u;
+    if (!done) {
+      for (int k = 0; k < cnt; ++k) {
+        const float4 b = st.rec1[k];
+        if (!in_rect(b, pc.px, pc.py)) continue;
+        ++ntest;
+        const float4 a = st.rec0[k];
+        if (ray_disc_positive(a.x, a.y, a.z, a.w, pc.rx, pc.ry)) hits |= 1u << k;
       }
-      if (!in_rect(b, pc.px, pc.py)) continue;
-      ++ntest;
+    }
+    // phase 2: this lane's hits, in list order
+    while (hits) {
+      const int k = __ffs(hits) - 1;
+      hits &= hits - 1u;
+      const float4 a = st.rec0[k];
+      const float4 b = st.rec1[k];
+      if (b.x >= fmaxf(kstop1, kstop2)) {
+        done = true;
+        break;
+      }
       RayHit h;
       if (!ray_hit(a.x, a.y, a.z, a.w, b.x, pc.rx, pc.ry, zfar, h)) continue;
       ++nhit;
-      const int id = sm.id[j];
+      const int id = st.id[k];
       if (BLEND) {
-        const float4 c2 = sm.rec2[j];
+        const float4 c2 = st.rec2[k];
         const ValueGeom vg = value_geom(a, c2, pc.vr);
         const float qd = fminf(vg.dist / c2.w, 1.0f);
         const float d = literal ? qd : 1.0f - qd;
         const float od = b.y * d;
         if (od != 0.0f) {   // a zero weight adds nothing and must not move the shift
           const float z = (((zfar - a.z) - c2.z) + vg.off) * inv_range;
-          blend_hit<CMAX>(bs, b.y * z * inv_gamma, od, &sm.feat[j * CMAX], id);
+          blend_hit<CMAX>(bs, b.y * z * inv_gamma, od, &st.feat[k * CMAX], id);
         }
       }
       if (hit_less(h.t, id, thr_t, thr_i)) {
         queue_insert<KMAX>(qt, qi, h.t, id);
         queue_select<KMAX>(qt, qi, K, thr_t, thr_i);
         kstop1 = next_up(thr_t);
-        kstop = fmaxf(kstop1, kstop2);
       }
     }
-    if (__syncthreads_and(done)) break;
+    // a pixel that stopped at no hit still stops once the batch's last key
+    // passes its bound (keys rise along the list)
+    if (!done && cnt > 0 && st.rec1[cnt - 1].x >= fmaxf(kstop1, kstop2)) done = true;
+    __syncwarp();
   }
 
   if (it.nseg > 1) {
-    // leave this segment's state, then let the tile's last segment merge
+    // leave this block's segment state, then let the block's last segment merge
     const int F = v.part_fields;
     const int q0 = kPRes + C;
-    float* P = v.partial + (size_t)it.item * F * kThreads + tid;
+    float* P = v.partial + (size_t)it.slot * F * 32 + lane;
     if (BLEND) {
-      P[kPM * kThreads] = bs.m;
-      P[kPDen * kThreads] = bs.den;
-      P[kPAdom * kThreads] = bs.adom;
-      P[kPDom * kThreads] = __int_as_float(bs.dom);
-      P[kPTests * kThreads] = __int_as_float(ntest);
+      P[kPM * 32] = bs.m;
+      P[kPDen * 32] = bs.den;
+      P[kPAdom * 32] = bs.adom;
+      P[kPDom * 32] = __int_as_float(bs.dom);
+      P[kPTests * 32] = __int_as_float(ntest);
 #pragma unroll
       for (int c = 0; c < CMAX; ++c)
-        if (c < C) P[(kPRes + c) * kThreads] = bs.res[c];
+        if (c < C) P[(kPRes + c) * 32] = bs.res[c];
     }
-    P[kPHits * kThreads] = __int_as_float(nhit);
+    P[kPHits * 32] = __int_as_float(nhit);
 #pragma unroll
     for (int k = 0; k < KMAX; ++k)
       if (k < K) {
-        P[(q0 + k) * kThreads] = qt[k];
-        P[(q0 + K + k) * kThreads] = __int_as_float(qi[k]);
+        P[(q0 + k) * 32] = qt[k];
+        P[(q0 + K + k) * 32] = __int_as_float(qi[k]);
       }
     __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = atomicAdd(&v.tile_done[it.tile], 1) == it.nseg - 1;
-    __syncthreads();
-    if (!s_last) return;
+    __syncwarp();
+    int last = 0;
+    if (lane == 0)
+      last = atomicAdd(&v.tile_done[it.tile * kBlocksPerTile + it.block], 1) == it.nseg - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
     __threadfence();
     for (int o = it.first; o < it.first + it.nseg; ++o) {
       if (o == it.item) continue;
-      const float* Q = v.partial + (size_t)o * F * kThreads + tid;
+      const float* Q = v.partial + ((size_t)o * kBlocksPerTile + it.block) * F * 32 + lane;
       if (BLEND) {
-        const float mB = __ldcg(Q + kPM * kThreads);
-        float denB = __ldcg(Q + kPDen * kThreads);
-        float adomB = __ldcg(Q + kPAdom * kThreads);
-        const int domB = __float_as_int(__ldcg(Q + kPDom * kThreads));
-        ntest += __float_as_int(__ldcg(Q + kPTests * kThreads));
+        const float mB = __ldcg(Q + kPM * 32);
+        float denB = __ldcg(Q + kPDen * 32);
+        float adomB = __ldcg(Q + kPAdom * 32);
+        const int domB = __float_as_int(__ldcg(Q + kPDom * 32));
+        ntest += __float_as_int(__ldcg(Q + kPTests * 32));
         const float m = fmaxf(bs.m, mB);
         const float sa = __expf(bs.m - m), sb = __expf(mB - m);
         bs.den *= sa;
@@ -227,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 2) traverse_kernel(const WsView v,
           for (int c = 0; c < CMAX; ++c)
             if (c < C) {
               const float fb = fB[c];
-              bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * kThreads),
+              bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * 32),
                                fmaf(bs.den, bs.fref[c] - fb, bs.res[c] * sa));
               bs.fref[c] = fb;
             }
@@ -237,25 +259,25 @@ __global__ void __launch_bounds__(kThreads, 2) traverse_kernel(const WsView v,
 #pragma unroll
           for (int c = 0; c < CMAX; ++c)
             if (c < C)
-              bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * kThreads),
+              bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * 32),
                                fmaf(denB, fB[c] - bs.fref[c], bs.res[c] * sa));
         }
         bs.den += denB;
         bs.m = m;
       }
-      nhit += __float_as_int(__ldcg(Q + kPHits * kThreads));
+      nhit += __float_as_int(__ldcg(Q + kPHits * 32));
 #pragma unroll
       for (int k = 0; k < KMAX; ++k)
         if (k < K) {
-          const float t = __ldcg(Q + (q0 + k) * kThreads);
-          const int id = __float_as_int(__ldcg(Q + (q0 + K + k) * kThreads));
+          const float t = __ldcg(Q + (q0 + k) * 32);
+          const int id = __float_as_int(__ldcg(Q + (q0 + K + k) * 32));
           if (hit_less(t, id, thr_t, thr_i)) {
             queue_insert<KMAX>(qt, qi, t, id);
             queue_select<KMAX>(qt, qi, K, thr_t, thr_i);
           }
         }
     }
-    if (tid == 0) v.tile_done[it.tile] = 0;   // ready for the next launch
+    if (lane == 0) v.tile_done[it.tile * kBlocksPerTile + it.block] = 0;   // ready for the next launch
   }
 
   if (!pc.inside) return;
@@ -289,11 +311,9 @@ __global__ void __launch_bounds__(kThreads, 2) traverse_kernel(const WsView v,
 
 template <int KMAX, int CMAX, bool BLEND>
 cudaError_t launch_t(const WsView& v, const uint32_t* list, bool store, cudaStream_t st) {
-  const size_t smem = sizeof(ChunkSmem<CMAX>);
+  const size_t smem = sizeof(WarpStage<CMAX>);
   auto kern = traverse_kernel<KMAX, CMAX, BLEND>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)v.max_items, kThreads, smem, st>>>(v, list, store ? 1 : 0);
+  kern<<<(unsigned)v.max_items * kBlocksPerTile, 32, smem, st>>>(v, list, store ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(1024) make_items(WsView v) {
     const uint32_t ns = len > 0 ? (uint32_t)((len + v.segment - 1) / v.segment) : 1u;
     v.item_begin[t] = (int32_t)base;
     for (uint32_t k = 0; k < ns; ++k) v.item_tile[base + k] = (int32_t)t;
-    v.tile_done[t] = 0;
+    for (int b = 0; b < 8; ++b) v.tile_done[t * 8 + b] = 0;
     base += ns;
   }
   if (threadIdx.x == 0) {
