@@ -15,8 +15,8 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t hdr, scenes, rec0, rec1, rec2, key0, key1, val0, val1, hist, block_sums, pkey0, pkey1, pval0,
-      pval1, ranges, item_begin, item_tile, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
-      gacc, fin_part, total;
+      pval1, radix_tot, ranges, item_begin, item_tile, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
+      gacc, fin_part, red_part, total;
   int64_t n_spheres, n_tiles, n_pixels, capacity, max_items;
   int32_t sort_blocks, fin_blocks, tile_bits, segment, part_fields;
 };
@@ -88,6 +88,7 @@ Layout make_layout(const pulsar_params* ps, int n) {
   L.val1 = take(4 * (size_t)M);
   L.hist = take(4 * (size_t)kRadix * L.sort_blocks);
   L.block_sums = take(4 * (size_t)L.sort_blocks);
+  L.radix_tot = take(4 * (size_t)kRadix);
   L.pkey0 = take(4 * (size_t)cap);
   L.pkey1 = take(4 * (size_t)cap);
   L.pval0 = take(4 * (size_t)cap);
@@ -104,6 +105,7 @@ Layout make_layout(const pulsar_params* ps, int n) {
   L.fres = take(4 * (size_t)P * C);
   L.gacc = take(16 * (size_t)M);
   L.fin_part = take(4 * (size_t)kCamPartials * std::max(fin, 1));
+  L.red_part = take(4 * (size_t)n * 64 * 45);
   L.total = off;
   return L;
 }
@@ -136,6 +138,7 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.val[1] = reinterpret_cast<uint32_t*>(b + L.val1);
   v.hist = reinterpret_cast<uint32_t*>(b + L.hist);
   v.block_sums = reinterpret_cast<uint32_t*>(b + L.block_sums);
+  v.radix_tot = reinterpret_cast<uint32_t*>(b + L.radix_tot);
   v.pkey[0] = reinterpret_cast<uint32_t*>(b + L.pkey0);
   v.pkey[1] = reinterpret_cast<uint32_t*>(b + L.pkey1);
   v.pval[0] = reinterpret_cast<uint32_t*>(b + L.pval0);
@@ -151,6 +154,7 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.fres = reinterpret_cast<float*>(b + L.fres);
   v.gacc = reinterpret_cast<float4*>(b + L.gacc);
   v.fin_part = reinterpret_cast<float*>(b + L.fin_part);
+  v.red_part = reinterpret_cast<float*>(b + L.red_part);
   return v;
 }
 

@@ -193,37 +193,67 @@ __device__ __forceinline__ float dot3(const float* a, const float* b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
-// One CTA per scene: deterministic sum of the per-block camera partials, the
-// per-item pitch partials and the per-tile background partials, then the
-// chain through the pixel pitch kappa = s / (W f) and the Gram-Schmidt map of
-// the 6D rotation.
-__global__ void __launch_bounds__(1024) camera_reduce_kernel(WsView v, uint32_t mask) {
-  __shared__ float sh[32];
-  __shared__ float tot[13];
+constexpr int kRedParts = 64;   // CTAs per scene in the first reduction stage
+constexpr int kRedValues = 13 + 32;
+
+// First stage of the camera and background reduction: CTA (scene, part)
+// sums its share of the per-block camera partials, the per-(item, pixel
+// block) pitch partials and the per-(tile, pixel block) background partials.
+__global__ void __launch_bounds__(256) camera_partials_kernel(WsView v, uint32_t mask) {
+  __shared__ float red[8][kRedValues];
   const SceneDev& S = v.scenes[blockIdx.x];
+  const int part = blockIdx.y;
   const int C = S.n_channels;
   const int64_t nt = (int64_t)S.tiles_x * S.tiles_y;
+  const int stride = kRedParts * blockDim.x;
+  const int start = part * blockDim.x + threadIdx.x;
+  float acc[kRedValues];
+#pragma unroll
+  for (int k = 0; k < kRedValues; ++k) acc[k] = 0.0f;
   if (mask & PULSAR_GRAD_CAM) {
-    for (int k = 0; k < 13; ++k) {
-      float x = 0.0f;
-      for (int b = threadIdx.x; b < S.fin_blocks; b += blockDim.x)
-        x += v.fin_part[(size_t)(S.fin_block_begin + b) * kCamPartials + k];
-      if (k == 12) {   // per (work item, pixel block) slots of this scene
-        const int i0 = 8 * v.item_begin[S.tile_begin], i1 = 8 * v.item_begin[S.tile_begin + nt];
-        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) x += v.item_kappa[i];
-      }
-      float r = block_sum(x, sh);
-      if (threadIdx.x == 0) tot[k] = r;
+    for (int b = start; b < S.fin_blocks; b += stride) {
+      const float* fp = v.fin_part + (size_t)(S.fin_block_begin + b) * kCamPartials;
+#pragma unroll
+      for (int k = 0; k < 13; ++k) acc[k] += fp[k];
     }
+    const int i0 = 8 * v.item_begin[S.tile_begin], i1 = 8 * v.item_begin[S.tile_begin + nt];
+    for (int i = i0 + start; i < i1; i += stride) acc[12] += v.item_kappa[i];
   }
   if (mask & PULSAR_GRAD_BG) {
-    for (int c = 0; c < C; ++c) {   // per (tile, pixel block) partials
-      const float* row = v.tile_bg + (size_t)c * v.n_tiles * 8 + S.tile_begin * 8;
-      float x = 0.0f;
-      for (int64_t t = threadIdx.x; t < 8 * nt; t += blockDim.x) x += row[t];
-      float r = block_sum(x, sh);
-      if (threadIdx.x == 0) S.g_bg[c] = r;
+    const float* rows = v.tile_bg + (size_t)S.tile_begin * 8 * C;
+    for (int64_t t = start; t < 8 * nt; t += stride) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < C) acc[13 + c] += rows[t * C + c];
     }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < kRedValues; ++k) {
+    const float x = warp_sum(acc[k]);
+    if (lane == 0) red[warp][k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < kRedValues) {
+    float x = 0.0f;
+    for (int w = 0; w < 8; ++w) x += red[w][threadIdx.x];
+    v.red_part[((size_t)blockIdx.x * kRedParts + part) * kRedValues + threadIdx.x] = x;
+  }
+}
+
+// Second stage, one CTA per scene: sums the first stage's partials in a fixed
+// order, then chains the camera sums through the pixel pitch kappa = s / (W f)
+// and the Gram-Schmidt map of the 6D rotation.
+__global__ void __launch_bounds__(64) camera_reduce_kernel(WsView v, uint32_t mask) {
+  __shared__ float tot[kRedValues];
+  const SceneDev& S = v.scenes[blockIdx.x];
+  const int C = S.n_channels;
+  if (threadIdx.x < kRedValues) {
+    float x = 0.0f;
+    for (int p = 0; p < kRedParts; ++p)
+      x += v.red_part[((size_t)blockIdx.x * kRedParts + p) * kRedValues + threadIdx.x];
+    tot[threadIdx.x] = x;
+    if ((mask & PULSAR_GRAD_BG) && threadIdx.x >= 13 && threadIdx.x < 13 + C) S.g_bg[threadIdx.x - 13] = x;
   }
   __syncthreads();
   if (threadIdx.x == 0 && (mask & PULSAR_GRAD_CAM)) {
@@ -301,8 +331,10 @@ cudaError_t launch_project(const WsView& v, cudaStream_t st) {
 cudaError_t launch_finalize(const WsView& v, uint32_t mask, cudaStream_t st) {
   if (v.fin_blocks > 0 && (mask & (PULSAR_GRAD_POS | PULSAR_GRAD_RAD | PULSAR_GRAD_CAM)))
     finalize_kernel<<<v.fin_blocks, kFinalizeThreads, 0, st>>>(v, mask);
-  if (mask & (PULSAR_GRAD_CAM | PULSAR_GRAD_BG))
-    camera_reduce_kernel<<<v.n_scenes, 1024, 0, st>>>(v, mask);
+  if (mask & (PULSAR_GRAD_CAM | PULSAR_GRAD_BG)) {
+    camera_partials_kernel<<<dim3(v.n_scenes, kRedParts), 256, 0, st>>>(v, mask);
+    camera_reduce_kernel<<<v.n_scenes, 64, 0, st>>>(v, mask);
+  }
   return cudaGetLastError();
 }
 

@@ -111,6 +111,7 @@ struct WsView {
   uint32_t* val[2];          // radix sort values (ping-pong)
   uint32_t* hist;            // radix histograms [kRadix][sort_blocks]
   uint32_t* block_sums;      // scan partials [sort_blocks]
+  uint32_t* radix_tot;       // per digit: total count of one radix pass [kRadix]
   uint32_t* pkey[2];         // pair tile ids (ping-pong)
   uint32_t* pval[2];         // pair sphere ids (ping-pong)
   int2* ranges;              // per tile [begin, end)
@@ -119,11 +120,12 @@ struct WsView {
   int32_t* tile_done;        // per tile: finished segments (last-finisher merge)
   float* partial;            // per work item: partial forward state, [field][pixel]
   float* item_kappa;         // per work item: d L / d kappa partial
-  float* tile_bg;            // channel-major: [c][tile] background-gradient partial
+  float* tile_bg;            // per (tile, pixel block) x C background-gradient partials
   float4* pix_aux;           // per pixel: (t_K, id_K bits, reference sphere bits, 0)
   float* fres;               // per pixel x C: F - f_ref, the image relative to its reference feature
   float4* gacc;              // per sphere: dL/dc (3), dL/dR
   float* fin_part;           // per finalize block: camera partials
+  float* red_part;           // per scene x 64: first-stage camera / background sums (45)
 };
 
 // ----------------------------------------------------------------------------
@@ -290,6 +292,29 @@ __device__ __forceinline__ ValueGeom value_geom(const float4& a, const float4& c
   g.sq = vsqrt(fmaf(g.rr, R * R, -g.cr2));
   g.off = vdiv(fmaf(r.rx, g.ex, fmaf(r.ry, g.ey, g.sq)), g.rr);
   g.dist = sqrtf(g.cr2 / g.rr);
+  return g;
+}
+
+// The forward pass's value path: dist / R and the depth offset only.  dist/R
+// = sqrt(|c x r|^2 / (|r|^2 R^2)) takes one correctly rounded division and
+// square root.
+struct ValueFwd {
+  float qd;    // dist / R
+  float off;   // c_z - t_h
+};
+
+__device__ __forceinline__ ValueFwd value_fwd(const float4& a, const float4& c2, const ValueRay& r) {
+  ValueFwd g;
+  const float ex = fmaf(a.z, r.rx, -a.x) + fmaf(a.z, r.rx_lo, fmaf(c2.z, r.rx, -c2.x));
+  const float ey = fmaf(a.z, r.ry, -a.y) + fmaf(a.z, r.ry_lo, fmaf(c2.z, r.ry, -c2.y));
+  const float ez = fmaf(a.x, ey, -a.y * ex) / a.z;
+  const float cr2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+  const float rr = fmaf(r.rx, r.rx, fmaf(r.ry, r.ry, 1.0f));
+  const float R = c2.w;
+  const float rR2 = rr * (R * R);
+  g.qd = sqrtf(cr2 / rR2);
+  const float sq = vsqrt(rR2 - cr2);
+  g.off = vdiv(fmaf(r.rx, ex, fmaf(r.ry, ey, sq)), rr);
   return g;
 }
 

@@ -5,11 +5,11 @@
 // mode, App. B "Preparing for the Backward Pass") or recomputed before this
 // pass by the forward traversal without blending (recompute mode).  Work is
 // split into the same one-warp (segment, pixel block) CTAs as the forward
-// pass; gradients are sums, so segments need no merge.  All lanes of a warp visit the same
-// sphere at the same time, so each sphere's per-pixel contributions are
-// summed across the warp with shuffles before one set of (vector) atomics per
-// warp and sphere.  A segment stops at the first key beyond every pixel's
-// threshold.
+// pass; gradients are sums, so segments need no merge.  As in the forward
+// pass, each batch of staged spheres is first hit-tested by every lane, then
+// each lane walks its own tracked hits and adds their gradients with (vector)
+// atomics, so lanes never wait on one another's hits.  A pixel stops at the
+// first key beyond its threshold.
 //
 // Derivatives (Eq. 1 with a = o d e^{o z / gamma}, D its denominator, G = dL/dF):
 //   dL/df_i = w_i G,   dL/da_i = G.(f_i - F) / D,
@@ -29,51 +29,26 @@ namespace pulsar {
 
 namespace {
 
+// Adds one tracked hit's gradients to its sphere (vector atomics where the
+// layout allows).
 template <int CMAX>
-__device__ __forceinline__ void warp_reduce_and_add(bool tracked, int id_global, int64_t id_local,
-                                                    float gc0, float gc1, float gc2, float gR,
-                                                    float go, const float (&gf)[CMAX], int C,
-                                                    const WsView& v, const SceneDev& S, bool geo,
-                                                    bool opa, bool feat) {
-  const unsigned bal = __ballot_sync(0xffffffffu, tracked);
-  if (bal == 0u) return;
-  const int lane = threadIdx.x & 31;
-  float r0 = gc0, r1 = gc1, r2 = gc2, r3 = gR, r4 = go;
-  float rf[CMAX];
-#pragma unroll
-  for (int c = 0; c < CMAX; ++c) rf[c] = gf[c];
-  if (__popc(bal) > 1) {
-    // several lanes hit this sphere: butterfly sums (all lanes take part)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      if (geo) {
-        r0 += __shfl_xor_sync(0xffffffffu, r0, o);
-        r1 += __shfl_xor_sync(0xffffffffu, r1, o);
-        r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-        r3 += __shfl_xor_sync(0xffffffffu, r3, o);
-      }
-      if (opa) r4 += __shfl_xor_sync(0xffffffffu, r4, o);
-      if (feat) {
-#pragma unroll
-        for (int c = 0; c < CMAX; ++c)
-          if (c < C) rf[c] += __shfl_xor_sync(0xffffffffu, rf[c], o);
-      }
-    }
-  }
-  if (lane != __ffs(bal) - 1) return;
-  if (geo) atomicAdd(&v.gacc[id_global], make_float4(r0, r1, r2, r3));
-  if (opa) atomicAdd(S.g_opa + id_local, r4);
+__device__ __forceinline__ void add_hit_grads(int id_global, int64_t id_local, float gc0, float gc1,
+                                              float gc2, float gR, float go, const float (&gf)[CMAX],
+                                              int C, const WsView& v, const SceneDev& S, bool geo,
+                                              bool opa, bool feat) {
+  if (geo) atomicAdd(&v.gacc[id_global], make_float4(gc0, gc1, gc2, gR));
+  if (opa) atomicAdd(S.g_opa + id_local, go);
   if (feat) {
     float* dst = S.g_feat + id_local * C;
     if ((C & 3) == 0) {
 #pragma unroll
       for (int c = 0; c < CMAX; c += 4)
         if (c < C)
-          atomicAdd(reinterpret_cast<float4*>(dst + c), make_float4(rf[c], rf[c + 1], rf[c + 2], rf[c + 3]));
+          atomicAdd(reinterpret_cast<float4*>(dst + c), make_float4(gf[c], gf[c + 1], gf[c + 2], gf[c + 3]));
     } else {
 #pragma unroll
       for (int c = 0; c < CMAX; ++c)
-        if (c < C) atomicAdd(dst + c, rf[c]);
+        if (c < C) atomicAdd(dst + c, gf[c]);
     }
   }
 }
@@ -134,11 +109,11 @@ __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v,
   // background gradient: sum over the block of w_B G (first segment only)
   if (bgw && it.seg == 0) {
     const float wB = pc.inside ? __expf(S.eps * inv_gamma - logD) : 0.0f;
-    const size_t nb = (size_t)v.n_tiles * kBlocksPerTile;
+    float* dst = v.tile_bg + ((size_t)it.tile * kBlocksPerTile + it.block) * C;
 #pragma unroll
     for (int c = 0; c < CMAX; ++c) {
       const float x = warp_sum(wB * G[c]);
-      if (lane == 0 && c < C) v.tile_bg[(size_t)c * nb + it.tile * kBlocksPerTile + it.block] = x;
+      if (lane == 0 && c < C) dst[c] = x;
     }
   }
   if (!(geo || opa || feat)) {
@@ -153,104 +128,111 @@ __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v,
   for (int base = it.b0; base < it.b1; base += 32) {
     if (__all_sync(0xffffffffu, done)) break;
     const int cnt = stage_warp<CMAX>(st, v, S, list, base, it.b1, wr, true, true);
-    for (int k = 0; k < cnt; ++k) {
-      if (__all_sync(0xffffffffu, done)) break;
+    // phase 1: which staged spheres does this lane's ray meet?
+    uint32_t hits = 0u;
+    if (!done) {
+      for (int k = 0; k < cnt; ++k) {
+        const float4 b = st.rec1[k];
+        if (!in_rect(b, pc.px, pc.py)) continue;
+        const float4 a = st.rec0[k];
+        if (ray_disc_positive(a.x, a.y, a.z, a.w, pc.rx, pc.ry)) hits |= 1u << k;
+      }
+    }
+    // phase 2: this lane's tracked hits, in list order
+    while (hits) {
+      const int k = __ffs(hits) - 1;
+      hits &= hits - 1u;
       const float4 a = st.rec0[k];
       const float4 b = st.rec1[k];
+      if (b.x >= kstop) {
+        done = true;
+        break;
+      }
+      RayHit h;
+      if (!ray_hit(a.x, a.y, a.z, a.w, b.x, pc.rx, pc.ry, zfar, h)) continue;
       const int id = st.id[k];
-      bool tracked = false;
+      if (hit_less(thr_t, thr_i, h.t, id)) continue;   // beyond the tracked set
       float gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, gR = 0.f, go = 0.f;
       float gf[CMAX];
+      const float4 c2 = st.rec2[k];
+      const ValueGeom g = value_geom(a, c2, pc.vr);
+      const float R = c2.w;
+      const float inv_rr = vdiv(1.0f, g.rr);
+      const float dist = g.dist;
+      const float qd = dist / R;
+      const float qdc = fminf(qd, 1.0f);
+      const float d = literal ? qdc : 1.0f - qdc;
+      const float z = (((zfar - a.z) - c2.z) + g.off) * inv_range;
+      const float t_val = (a.z - g.off) + c2.z;
+      const float o = b.y;
+      const float s = o * z * inv_gamma;
+      // e^{s} / D; the clamp only matters for zero-weight hits, whose
+      // exponent may exceed log D by any amount
+      const float E = __expf(fminf(s - logD, 80.0f));
+      const float w = o * d * E;
+      const float* f = &st.feat[k * CMAX];
+      float gdot;   // G.(f_i - F)
+      if (id == dom) {
+        gdot = -GFres;
+      } else {
+        gdot = -Gref - GFres;
 #pragma unroll
-      for (int c = 0; c < CMAX; ++c) gf[c] = 0.0f;
-      if (!done) {
-        if (b.x >= kstop) {
-          done = true;
-        } else if (in_rect(b, pc.px, pc.py)) {
-          RayHit h;
-          if (ray_hit(a.x, a.y, a.z, a.w, b.x, pc.rx, pc.ry, zfar, h) &&
-              !hit_less(thr_t, thr_i, h.t, id)) {
-            tracked = true;
-            const float4 c2 = st.rec2[k];
-            const ValueGeom g = value_geom(a, c2, pc.vr);
-            const float R = c2.w;
-            const float inv_rr = vdiv(1.0f, g.rr);
-            const float dist = g.dist;
-            const float qd = dist / R;
-            const float qdc = fminf(qd, 1.0f);
-            const float d = literal ? qdc : 1.0f - qdc;
-            const float z = (((zfar - a.z) - c2.z) + g.off) * inv_range;
-            const float t_val = (a.z - g.off) + c2.z;
-            const float o = b.y;
-            const float s = o * z * inv_gamma;
-            // e^{s} / D; the clamp only matters for zero-weight hits, whose
-            // exponent may exceed log D by any amount
-            const float E = __expf(fminf(s - logD, 80.0f));
-            const float w = o * d * E;
-            const float* f = &st.feat[k * CMAX];
-            float gdot;   // G.(f_i - F)
-            if (id == dom) {
-              gdot = -GFres;
-            } else {
-              gdot = -Gref - GFres;
-#pragma unroll
-              for (int c = 0; c < CMAX; ++c) gdot = fmaf(G[c], f[c], gdot);
-            }
-#pragma unroll
-            for (int c = 0; c < CMAX; ++c) gf[c] = w * G[c];
-            go = gdot * d * E * (1.0f + s);
-            const float gd = gdot * o * E;
-            const float gz = gdot * w * o * inv_gamma;
-            const float gt = -gz * inv_range;
-            float gdist = 0.0f;
-            if (qd < 1.0f) {
-              const float sgn = literal ? 1.0f : -1.0f;
-              gdist = sgn * vdiv(gd, R);
-              gR = -sgn * gd * vdiv(qd, R);
-            }
-            // e = (r x (c x r)) / |r|^2 with c x r = (-ey, ex, ez)
-            const float rx = pc.vr.rx, ry = pc.vr.ry;
-            const float e0 = (ry * g.ez - g.ex) * inv_rr;
-            const float e1 = (-g.ey - rx * g.ez) * inv_rr;
-            const float e2 = (rx * g.ex + ry * g.ey) * inv_rr;
-            // gt / sqrt(disc): the depth derivatives carry 1/sqrt(disc), which
-            // diverges at the rim, while gt carries d.  With d = 1 - dist/R,
-            // d / sqrt(disc) = sqrt(disc) / (|r|^2 R (R + dist)) exactly, so
-            // the product is formed without dividing by a vanishing sqrt(disc)
-            // (d itself has a float32 floor of ~1e-7 there).  With the
-            // literal d the product diverges in exact arithmetic too.
-            float gt_sq;
-            if (literal) {
-              gt_sq = g.sq > 0.0f ? vdiv(gt, g.sq) : 0.0f;
-            } else {
-              const float d_over_sq = vdiv(g.sq * inv_rr, R * (R + dist));
-              gt_sq = -gdot * o * E * o * inv_gamma * inv_range * d_over_sq;
-            }
-            const float tc = t_val + g.sq * inv_rr;   // closest-approach parameter
-            const float b_ = tc * g.rr;               // r . c
-            gc0 = gt * rx * inv_rr + gt_sq * e0;
-            gc1 = gt * ry * inv_rr + gt_sq * e1;
-            gc2 = gt * inv_rr + gt_sq * e2;
-            gR += -R * gt_sq;
-            float grx = (gt * e0 - gt_sq * b_ * e0 - gt * t_val * rx) * inv_rr;
-            float gry = (gt * e1 - gt_sq * b_ * e1 - gt * t_val * ry) * inv_rr;
-            if (dist > 0.0f) {
-              const float gi = vdiv(gdist, dist);
-              gc0 += gi * e0;
-              gc1 += gi * e1;
-              gc2 += gi * e2;
-              grx += -gi * tc * e0;
-              gry += -gi * tc * e1;
-            }
-            const float pxo = (float)(2 * pc.px + 1 - S.width) * 0.5f;
-            const float pyo = (float)(2 * pc.py + 1 - S.height) * 0.5f;
-            gk_sum += grx * pxo + gry * pyo;
-          }
-        }
+        for (int c = 0; c < CMAX; ++c) gdot = fmaf(G[c], f[c], gdot);
       }
-      warp_reduce_and_add<CMAX>(tracked, id, (int64_t)id - S.sphere_begin, gc0, gc1, gc2, gR, go,
-                                gf, C, v, S, geo, opa, feat);
+#pragma unroll
+      for (int c = 0; c < CMAX; ++c) gf[c] = w * G[c];
+      go = gdot * d * E * (1.0f + s);
+      const float gd = gdot * o * E;
+      const float gz = gdot * w * o * inv_gamma;
+      const float gt = -gz * inv_range;
+      float gdist = 0.0f;
+      if (qd < 1.0f) {
+        const float sgn = literal ? 1.0f : -1.0f;
+        gdist = sgn * vdiv(gd, R);
+        gR = -sgn * gd * vdiv(qd, R);
+      }
+      // e = (r x (c x r)) / |r|^2 with c x r = (-ey, ex, ez)
+      const float rx = pc.vr.rx, ry = pc.vr.ry;
+      const float e0 = (ry * g.ez - g.ex) * inv_rr;
+      const float e1 = (-g.ey - rx * g.ez) * inv_rr;
+      const float e2 = (rx * g.ex + ry * g.ey) * inv_rr;
+      // gt / sqrt(disc): the depth derivatives carry 1/sqrt(disc), which
+      // diverges at the rim, while gt carries d.  With d = 1 - dist/R,
+      // d / sqrt(disc) = sqrt(disc) / (|r|^2 R (R + dist)) exactly, so
+      // the product is formed without dividing by a vanishing sqrt(disc)
+      // (d itself has a float32 floor of ~1e-7 there).  With the
+      // literal d the product diverges in exact arithmetic too.
+      float gt_sq;
+      if (literal) {
+        gt_sq = g.sq > 0.0f ? vdiv(gt, g.sq) : 0.0f;
+      } else {
+        const float d_over_sq = vdiv(g.sq * inv_rr, R * (R + dist));
+        gt_sq = -gdot * o * E * o * inv_gamma * inv_range * d_over_sq;
+      }
+      const float tc = t_val + g.sq * inv_rr;   // closest-approach parameter
+      const float b_ = tc * g.rr;               // r . c
+      gc0 = gt * rx * inv_rr + gt_sq * e0;
+      gc1 = gt * ry * inv_rr + gt_sq * e1;
+      gc2 = gt * inv_rr + gt_sq * e2;
+      gR += -R * gt_sq;
+      float grx = (gt * e0 - gt_sq * b_ * e0 - gt * t_val * rx) * inv_rr;
+      float gry = (gt * e1 - gt_sq * b_ * e1 - gt * t_val * ry) * inv_rr;
+      if (dist > 0.0f) {
+        const float gi = vdiv(gdist, dist);
+        gc0 += gi * e0;
+        gc1 += gi * e1;
+        gc2 += gi * e2;
+        grx += -gi * tc * e0;
+        gry += -gi * tc * e1;
+      }
+      const float pxo = (float)(2 * pc.px + 1 - S.width) * 0.5f;
+      const float pyo = (float)(2 * pc.py + 1 - S.height) * 0.5f;
+      gk_sum += grx * pxo + gry * pyo;
+      add_hit_grads<CMAX>(id, (int64_t)id - S.sphere_begin, gc0, gc1, gc2, gR, go, gf, C, v, S, geo,
+                          opa, feat);
     }
+    if (!done && cnt > 0 && st.rec1[cnt - 1].x >= kstop) done = true;
+    __syncwarp();
   }
   if (cam) {
     const float x = warp_sum(gk_sum);

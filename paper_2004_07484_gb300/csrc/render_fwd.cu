@@ -170,14 +170,26 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
         done = true;
         break;
       }
-      RayHit h;
-      if (!ray_hit(a.x, a.y, a.z, a.w, b.x, pc.rx, pc.ry, zfar, h)) continue;
+      // The float32 hit depth orders the queue and makes the far-plane cut.
+      // Every hit depth is at least the sphere's key, so a sphere keyed
+      // beyond the n_track-th tracked depth cannot enter the queue; if its
+      // far side also lies well in front of zfar (the depth can exceed
+      // c_z + R only by rounding), the phase-1 test alone decides the hit.
+      const bool may_queue = b.x <= thr_t;
+      float4 c2 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (BLEND) c2 = st.rec2[k];
+      if (!BLEND && !may_queue) continue;   // cannot change the tracked set
+      float t = 0.0f;
+      if (may_queue || !(fmaf(1.0001f, a.z, 1.001f * c2.w) < zfar)) {
+        RayHit h;
+        if (!ray_hit(a.x, a.y, a.z, a.w, b.x, pc.rx, pc.ry, zfar, h)) continue;
+        t = h.t;
+      }
       ++nhit;
       const int id = st.id[k];
       if (BLEND) {
-        const float4 c2 = st.rec2[k];
-        const ValueGeom vg = value_geom(a, c2, pc.vr);
-        const float qd = fminf(vg.dist / c2.w, 1.0f);
+        const ValueFwd vg = value_fwd(a, c2, pc.vr);
+        const float qd = fminf(vg.qd, 1.0f);
         const float d = literal ? qd : 1.0f - qd;
         const float od = b.y * d;
         if (od != 0.0f) {   // a zero weight adds nothing and must not move the shift
@@ -185,8 +197,8 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
           blend_hit<CMAX>(bs, b.y * z * inv_gamma, od, &st.feat[k * CMAX], id);
         }
       }
-      if (hit_less(h.t, id, thr_t, thr_i)) {
-        queue_insert<KMAX>(qt, qi, h.t, id);
+      if (may_queue && hit_less(t, id, thr_t, thr_i)) {
+        queue_insert<KMAX>(qt, qi, t, id);
         queue_select<KMAX>(qt, qi, K, thr_t, thr_i);
         kstop1 = next_up(thr_t);
       }

@@ -78,46 +78,26 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
   return r;
 }
 
-// Exclusive scan, in place, of rows x cols entries stored at data[r * stride + c],
-// in row-major logical order; cols = ceil(n / kSortTile).  One CTA of 1024
-// threads: warps first total the rows (coalesced), the row totals are scanned,
-// then every warp scans its rows 32 entries at a time.
-__global__ void __launch_bounds__(1024) scan_table(uint32_t* __restrict__ data, int rows,
-                                                   const int32_t* n_dev, int n_host, int stride) {
-  __shared__ uint32_t row_base[kRadix];
+// Exclusive scan, in place, of one digit's row of per-CTA counts
+// (row r = blockIdx.x, cols = ceil(n / kSortTile) entries at data[r * stride]),
+// and the row's total into row_tot[r].  One CTA per digit.
+__global__ void __launch_bounds__(kThreads) scan_rows(uint32_t* __restrict__ data,
+                                                      uint32_t* __restrict__ row_tot,
+                                                      const int32_t* n_dev, int n_host, int stride) {
   __shared__ uint32_t warp_tot[33];
   const int n = read_count(n_dev, n_host);
   const int cols = (n + kSortTile - 1) / kSortTile;
-  if (cols == 0) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int r = warp; r < rows; r += 32) {
-    uint32_t s = 0;
-    for (int c = lane; c < cols; c += 32) s += data[(size_t)r * stride + c];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) row_base[r] = s;
+  uint32_t* row = data + (size_t)blockIdx.x * stride;
+  uint32_t carry = 0;
+  for (int c0 = 0; c0 < cols; c0 += kThreads) {
+    const int c = c0 + threadIdx.x;
+    const uint32_t x = c < cols ? row[c] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan<kThreads>(x, warp_tot, tot);
+    if (c < cols) row[c] = carry + ex;
+    carry += tot;
   }
-  __syncthreads();
-  const uint32_t mine = threadIdx.x < rows ? row_base[threadIdx.x] : 0u;
-  uint32_t tot;
-  const uint32_t ex = block_exclusive_scan<1024>(mine, warp_tot, tot);
-  if (threadIdx.x < rows) row_base[threadIdx.x] = ex;
-  __syncthreads();
-  for (int r = warp; r < rows; r += 32) {
-    uint32_t carry = row_base[r];
-    for (int c0 = 0; c0 < cols; c0 += 32) {
-      const int c = c0 + lane;
-      const uint32_t x = c < cols ? data[(size_t)r * stride + c] : 0u;
-      uint32_t inc = x;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-      }
-      if (c < cols) data[(size_t)r * stride + c] = carry + inc - x;
-      carry += __shfl_sync(0xffffffffu, inc, 31);
-    }
-  }
+  if (threadIdx.x == 0) row_tot[blockIdx.x] = carry;
 }
 
 // Stable scatter of one radix pass.  Keys are ranked within each warp with
@@ -127,7 +107,8 @@ __global__ void __launch_bounds__(1024) scan_table(uint32_t* __restrict__ data, 
 __global__ void __launch_bounds__(kThreads) radix_downsweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int32_t* n_dev,
-    int n_host, int shift, uint32_t mask, const uint32_t* __restrict__ hist, int stride) {
+    int n_host, int shift, uint32_t mask, const uint32_t* __restrict__ hist,
+    const uint32_t* __restrict__ row_tot, int stride) {
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
   __shared__ uint32_t warp_cnt[kThreads / 32][kRadix];
@@ -169,7 +150,9 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
     uint32_t all;
     uint32_t ex = block_exclusive_scan<kThreads>(tot, warp_tot, all);
     digit_local[d] = ex;
-    digit_global[d] = hist[d * stride + blockIdx.x];
+    // global start of digit d: all smaller digits, then earlier CTAs of d
+    const uint32_t base_d = block_exclusive_scan<kThreads>(row_tot[d], warp_tot, all);
+    digit_global[d] = base_d + hist[d * stride + blockIdx.x];
   }
   __syncthreads();
 #pragma unroll
@@ -298,8 +281,8 @@ __global__ void __launch_bounds__(kThreads) tile_ranges(WsView v, int buf) {
 
 // Work items of the render passes: every tile's list is cut into segments of
 // at most v.segment entries (an empty tile is one item, so its pixels are
-// still written).  Writes item_begin (n_tiles + 1), item_tile, the item count,
-// and clears the per-tile merge counters.
+// still written).  Writes item_begin (n_tiles + 1), item_tile and the item
+// count.
 __global__ void __launch_bounds__(1024) make_items(WsView v) {
   __shared__ uint32_t warp_tot[33];
   const int64_t nt = v.n_tiles;
@@ -320,7 +303,6 @@ __global__ void __launch_bounds__(1024) make_items(WsView v) {
     const uint32_t ns = len > 0 ? (uint32_t)((len + v.segment - 1) / v.segment) : 1u;
     v.item_begin[t] = (int32_t)base;
     for (uint32_t k = 0; k < ns; ++k) v.item_tile[base + k] = (int32_t)t;
-    for (int b = 0; b < 8; ++b) v.tile_done[t * 8 + b] = 0;
     base += ns;
   }
   if (threadIdx.x == 0) {
@@ -337,9 +319,10 @@ cudaError_t radix_sort(const WsView& v, uint32_t* keys[2], uint32_t* vals[2], co
     uint32_t mask = (uint32_t)((1u << min(kRadixBits, bits - shift)) - 1u);
     radix_upsweep<<<blocks, kThreads, 0, st>>>(keys[buf], n_dev, n_host, shift, mask, v.hist,
                                                v.sort_blocks);
-    scan_table<<<1, 1024, 0, st>>>(v.hist, kRadix, n_dev, n_host, v.sort_blocks);
+    scan_rows<<<kRadix, kThreads, 0, st>>>(v.hist, v.radix_tot, n_dev, n_host, v.sort_blocks);
     radix_downsweep<<<blocks, kThreads, 0, st>>>(keys[buf], vals[buf], keys[buf ^ 1], vals[buf ^ 1],
-                                                 n_dev, n_host, shift, mask, v.hist, v.sort_blocks);
+                                                 n_dev, n_host, shift, mask, v.hist, v.radix_tot,
+                                                 v.sort_blocks);
     buf ^= 1;
   }
   return cudaGetLastError();
@@ -381,8 +364,12 @@ cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st) {
     const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
     tile_ranges<<<blocks, kThreads, 0, st>>>(v, pbuf);
   }
-  // 6. work items of the render passes
-  if (v.n_tiles > 0) make_items<<<1, 1024, 0, st>>>(v);
+  // 6. work items of the render passes (and cleared merge counters)
+  if (v.n_tiles > 0) {
+    e = cudaMemsetAsync(v.tile_done, 0, sizeof(int32_t) * 8 * (size_t)v.n_tiles, st);
+    if (e != cudaSuccess) return e;
+    make_items<<<1, 1024, 0, st>>>(v);
+  }
   return cudaGetLastError();
 }
 
