@@ -345,14 +345,16 @@ def main():
 
     pk, pk_kind = peaks()
     clocks = clk.summary()
-    # ALU roofline of the dominant kernel: FP32 operations of the render passes
-    # (counts of ray-sphere tests and hits from the kernel's own counters)
-    flops_fwd = 26.0 * tests + (30.0 + 2.0 * C) * hits
+    # ALU roofline of the dominant kernel: algorithmic FP32 operations of the
+    # forward render, 14 per ray-sphere test (the hit predicate) and 21 + 2C per
+    # hit (depth, distance term, depth term, exponent, weight, C-channel update),
+    # with the test and hit counts from the kernel's own per-pixel counters
+    flops_fwd = 14.0 * tests + (21.0 + 2.0 * C) * hits
     sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     fp32_peak_max = N_SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     dominant = "render_fwd" if fwd_ms >= bwd_ms else "render_bwd"
     achieved = flops_fwd / (fwd_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "pulsar_render_fwd (render_fwd_kernel)", "achieved": achieved,
+    roofline = {"bound": "alu", "kernel": "pulsar_render_fwd (traverse_kernel<16, 16, 1>)", "achieved": achieved,
                 "peak": fp32_peak_max, "unit": "TFLOP/s", "frac": achieved / fp32_peak_max,
                 "traffic": None,
                 "peak_kind": f"FP32 FMA pipes: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x max SM clock "
@@ -364,19 +366,25 @@ def main():
         dt, frac = cpu_oracle_sample(sc, 16)
         cpu = {"value": frac / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": "16x16-pixel window of the workload, fwd + bwd, FP64 brute force over all 1M spheres"}
-    launches_per_step = 30
+    # kernels per step: project 2 (setup, project), binning 23 (four 8-bit radix
+    # passes of the 32-bit depth keys and two of the 12-bit tile keys, 3 kernels
+    # each, then count, scan, emit, ranges, items), forward 2 (setup, render),
+    # backward 5 (setup, render, finalize, camera partials, camera reduce), plus
+    # the track pass in recompute mode
+    launches_store, launches_rec = 32, 33
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-            "config": {"workload": WORKLOAD, "model": "pulsar sphere renderer", "global_batch": world,
-                       "seq_len": None, "parallelism": f"replicas x{world} (independent renders)",
+            "config": {"workload": WORKLOAD, "renders_per_step": world,
+                       "parallelism": f"replicas x{world} (independent renders)",
                        "l2": "flushed between steps (256 MB write, untimed)",
                        "hit_lists": "recompute" if args.recompute else "store"},
             "recompute_ms_per_step" if not args.recompute else "store_ms_per_step": statistics.mean(ms_rec),
             "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-            "gpu_launches": launches_per_step * (args.steps + max(3, args.steps // 2)),
+            "gpu_launches": (launches_store * args.steps + launches_rec * len(ms_rec)) if not args.recompute
+            else (launches_rec * args.steps + launches_store * len(ms_rec)),
             "wall_s_timed": t_wall}
     print(json.dumps(line))
     if world > 1:

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v,
                                                             const uint32_t* __restrict__ list,
                                                             uint32_t mask) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpStage<CMAX>& st = *reinterpret_cast<WarpStage<CMAX>*>(smem_raw);
+  StageBuf<CMAX>& sb = *reinterpret_cast<StageBuf<CMAX>*>(smem_raw);
   ItemCtx it;
   if (!item_ctx(v, it)) return;
   const int si = scene_of_tile(v.scenes, v.n_scenes, it.tile);
@@ -75,9 +75,6 @@ __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v,
   const bool cam = (mask & PULSAR_GRAD_CAM) != 0;
   const bool bgw = (mask & PULSAR_GRAD_BG) != 0;
   const int lane = threadIdx.x & 31;
-
-  for (int e = lane; e < 32 * CMAX; e += 32) st.feat[e] = 0.0f;   // channels beyond C stay zero
-  __syncwarp();
 
   // per-pixel upstream data
   const int64_t pix = pc.inside ? (int64_t)pc.py * S.width + pc.px : 0;
@@ -125,36 +122,41 @@ __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v,
   bool done = !pc.inside;
   float gk_sum = 0.0f;
   const WarpRect wr = warp_rect(pc, it.block);
-  for (int base = it.b0; base < it.b1; base += 32) {
+  WarpStream<CMAX> ws;
+  ws.start(sb, v, list, it.b0, it.b1, true);
+  for (; ws.base < it.b1; ws.advance()) {
     if (__all_sync(0xffffffffu, done)) break;
-    const int cnt = stage_warp<CMAX>(st, v, S, list, base, it.b1, wr, true, true);
+    const uint32_t live = ws.begin(sb, v, S, list, wr, true);
+    const int cur = ws.buf;
     // phase 1: which staged spheres does this lane's ray meet?
     uint32_t hits = 0u;
     if (!done) {
-      for (int k = 0; k < cnt; ++k) {
-        const float4 b = st.rec1[k];
+      for (uint32_t m = live; m; m &= m - 1u) {
+        const int j = __ffs(m) - 1;
+        const float4 b = sb.rec1[cur][j];
         if (!in_rect(b, pc.px, pc.py)) continue;
-        const float4 a = st.rec0[k];
-        if (ray_disc_positive(a.x, a.y, a.z, a.w, pc.rx, pc.ry)) hits |= 1u << k;
+        const float4 a = sb.rec0[cur][j];
+        if (ray_disc_positive(a.x, a.y, a.z, a.w, pc.rx, pc.ry)) hits |= 1u << j;
       }
     }
+    ws.wait_values();
     // phase 2: this lane's tracked hits, in list order
     while (hits) {
-      const int k = __ffs(hits) - 1;
+      const int j = __ffs(hits) - 1;
       hits &= hits - 1u;
-      const float4 a = st.rec0[k];
-      const float4 b = st.rec1[k];
+      const float4 a = sb.rec0[cur][j];
+      const float4 b = sb.rec1[cur][j];
       if (b.x >= kstop) {
         done = true;
         break;
       }
       RayHit h;
       if (!ray_hit(a.x, a.y, a.z, a.w, b.x, pc.rx, pc.ry, zfar, h)) continue;
-      const int id = st.id[k];
+      const int id = sb.id[cur][j];
       if (hit_less(thr_t, thr_i, h.t, id)) continue;   // beyond the tracked set
       float gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, gR = 0.f, go = 0.f;
       float gf[CMAX];
-      const float4 c2 = st.rec2[k];
+      const float4 c2 = sb.rec2[cur][j];
       const ValueGeom g = value_geom(a, c2, pc.vr);
       const float R = c2.w;
       const float inv_rr = vdiv(1.0f, g.rr);
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v,
       // exponent may exceed log D by any amount
       const float E = __expf(fminf(s - logD, 80.0f));
       const float w = o * d * E;
-      const float* f = &st.feat[k * CMAX];
+      const float* f = &sb.feat[cur][j * CMAX];
       float gdot;   // G.(f_i - F)
       if (id == dom) {
         gdot = -GFres;
@@ -231,9 +233,9 @@ __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v,
       add_hit_grads<CMAX>(id, (int64_t)id - S.sphere_begin, gc0, gc1, gc2, gR, go, gf, C, v, S, geo,
                           opa, feat);
     }
-    if (!done && cnt > 0 && st.rec1[cnt - 1].x >= kstop) done = true;
-    __syncwarp();
+    if (!done && sb.rec1[cur][ws.count() - 1].x >= kstop) done = true;
   }
+  ws.drain();
   if (cam) {
     const float x = warp_sum(gk_sum);
     if (lane == 0) v.item_kappa[it.slot] = x;
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v,
 
 template <int CMAX>
 cudaError_t launch_bwd_t(const WsView& v, const uint32_t* list, uint32_t mask, cudaStream_t st) {
-  const size_t smem = sizeof(WarpStage<CMAX>);
+  const size_t smem = sizeof(StageBuf<CMAX>);
   auto kern = render_bwd_kernel<CMAX>;
   kern<<<(unsigned)v.max_items * kBlocksPerTile, 32, smem, st>>>(v, list, mask);
   return cudaGetLastError();

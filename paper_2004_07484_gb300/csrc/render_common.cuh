@@ -4,10 +4,10 @@
 // each, and each thread renders one pixel, so parallelism is over pixels as
 // the paper prescribes (Sec. 3.2, App. B).  Every warp is its own CTA and
 // walks one segment of its tile's depth-ordered sphere list independently:
-// it reads 32 list entries at a time, keeps those whose pixel rectangle
-// overlaps its block (a ballot over the lanes, compacted with a popcount
-// scan) and stages their draw records and features in shared memory (App. B,
-// Step 1: block-wise intersection search with cooperative filtering).  A
+// it stages 32 list entries at a time in shared memory, marks those whose
+// pixel rectangle overlaps its block (a ballot over the lanes) and gathers
+// only their value records and features (App. B, Step 1: block-wise
+// intersection search with cooperative filtering).  A
 // warp with few candidates therefore never waits for a busy neighbour and
 // frees its slot as soon as it is done.
 #pragma once
@@ -21,16 +21,6 @@ __device__ __forceinline__ unsigned lane_lt_mask() {
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
 }
-
-// One warp's staged spheres (at most 32, compacted).
-template <int CMAX>
-struct WarpStage {
-  float4 rec0[32];
-  float4 rec1[32];
-  float4 rec2[32];
-  int32_t id[32];
-  float feat[32 * CMAX];
-};
 
 constexpr int kBlocksPerTile = 8;   // 8 x 4 pixel blocks (warps) per 16 x 16 tile
 
@@ -109,49 +99,135 @@ __device__ __forceinline__ bool rect_overlaps(const float4& b, const WarpRect& r
          (int)(by >> 16) >= r.y0;
 }
 
-// Stages the entries of list[base, min(base + 32, end)) whose rectangles
-// overlap the warp's block into the warp's stage, in list order.  Returns
-// how many were staged.  Called by all 32 lanes; ends with a warp barrier.
+// ----------------------------------------------------------------------------
+// Asynchronous staging.  A warp streams its segment of the tile list, 32
+// entries per batch, through two shared-memory buffers with cp.async: the
+// list entries of batch i + 2 and the draw records (rec0, rec1) of batch
+// i + 1 are in flight while batch i is processed, and the value records and
+// features of batch i's spheres that overlap the warp's block are gathered
+// behind its phase-1 hit tests.  Spheres are addressed by their position j in
+// the batch; the overlap ballot says which positions are live.
+// ----------------------------------------------------------------------------
+
 template <int CMAX>
-__device__ __forceinline__ int stage_warp(WarpStage<CMAX>& st, const WsView& v, const SceneDev& S,
-                                          const uint32_t* __restrict__ list, int base, int end,
-                                          const WarpRect& wr, bool need_rec2, bool need_feat) {
-  const int lane = threadIdx.x & 31;
-  const int idx = base + lane;
-  bool ok = idx < end;
-  uint32_t id = 0;
-  float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (ok) {
-    id = __ldg(list + idx);
-    b = __ldg(v.rec1 + id);
-    ok = rect_overlaps(b, wr);
+struct StageBuf {
+  float4 rec0[2][32];
+  float4 rec1[2][32];
+  float4 rec2[2][32];
+  float feat[2][32 * CMAX];
+  int32_t id[2][32];
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int CMAX>
+struct WarpStream {
+  int base;           // first list entry of the current batch
+  int end;            // end of the segment
+  int buf;            // buffer holding the current batch
+  uint32_t id_next;   // this lane's list entry of the next batch
+
+  __device__ __forceinline__ uint32_t load_id(const uint32_t* __restrict__ list, int at) const {
+    const int i = at + (int)(threadIdx.x & 31);
+    return i < end ? __ldg(list + i) : 0u;
   }
-  const unsigned bal = __ballot_sync(0xffffffffu, ok);
-  __syncwarp();   // the previous batch is no longer read
-  if (ok) {
-    const int pos = __popc(bal & lane_lt_mask());
-    st.rec1[pos] = b;
-    st.rec0[pos] = __ldg(v.rec0 + id);
-    if (need_rec2) st.rec2[pos] = __ldg(v.rec2 + id);
-    st.id[pos] = (int32_t)id;
-    if (need_feat) {
+
+  // One commit group: the draw records of the batch at `at` into buffer `to`.
+  __device__ __forceinline__ void issue_records(StageBuf<CMAX>& sb, const WsView& v, int at,
+                                                uint32_t id, int to) const {
+    const int lane = threadIdx.x & 31;
+    if (at + lane < end) {
+      cp_async16(&sb.rec0[to][lane], v.rec0 + id);
+      cp_async16(&sb.rec1[to][lane], v.rec1 + id);
+      sb.id[to][lane] = (int32_t)id;
+    }
+    cp_async_commit();
+  }
+
+  // Starts the segment [b0, b1).  Feature channels beyond C stay zero.
+  __device__ __forceinline__ void start(StageBuf<CMAX>& sb, const WsView& v,
+                                        const uint32_t* __restrict__ list, int b0, int b1,
+                                        bool need_feat) {
+    const int lane = threadIdx.x & 31;
+    if (need_feat)
+      for (int e = lane; e < 2 * 32 * CMAX; e += 32) (&sb.feat[0][0])[e] = 0.0f;
+    __syncwarp();
+    base = b0;
+    end = b1;
+    buf = 0;
+    issue_records(sb, v, b0, load_id(list, b0), 0);
+    id_next = load_id(list, b0 + 32);
+  }
+
+  // Number of entries in the current batch.
+  __device__ __forceinline__ int count() const { return min(32, end - base); }
+
+  // Waits for the current batch's draw records and returns the ballot of
+  // positions whose pixel rectangles overlap the warp's block.  Starts the
+  // gathers of those spheres' value records and features (one group) and of
+  // the next batch's draw records (another group).
+  __device__ __forceinline__ uint32_t begin(StageBuf<CMAX>& sb, const WsView& v, const SceneDev& S,
+                                            const uint32_t* __restrict__ list, const WarpRect& wr,
+                                            bool need_values) {
+    const int lane = threadIdx.x & 31;
+    cp_async_wait<0>();
+    __syncwarp();
+    const bool ok = base + lane < end && rect_overlaps(sb.rec1[buf][lane], wr);
+    const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+    if (ok && need_values) {
+      const uint32_t id = (uint32_t)sb.id[buf][lane];
+      cp_async16(&sb.rec2[buf][lane], v.rec2 + id);
       const int C = S.n_channels;
       const float* __restrict__ src = S.feat + (int64_t)(id - S.sphere_begin) * C;
-      float* dst = &st.feat[pos * CMAX];
+      float* dst = &sb.feat[buf][lane * CMAX];
       if ((C & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
 #pragma unroll
         for (int c = 0; c < CMAX; c += 4)
-          if (c < C) *reinterpret_cast<float4*>(dst + c) = __ldg(reinterpret_cast<const float4*>(src + c));
+          if (c < C) cp_async16(dst + c, src + c);
       } else {
 #pragma unroll
         for (int c = 0; c < CMAX; ++c)
-          if (c < C) dst[c] = __ldg(src + c);
+          if (c < C) cp_async4(dst + c, src + c);
       }
     }
+    cp_async_commit();
+    issue_records(sb, v, base + 32, id_next, buf ^ 1);
+    id_next = load_id(list, base + 64);
+    return bal;
   }
-  __syncwarp();
-  return __popc(bal);
-}
+
+  // Waits for the value records and features of the current batch.
+  __device__ __forceinline__ void wait_values() const {
+    cp_async_wait<1>();
+    __syncwarp();
+  }
+
+  // Moves to the next batch once every lane is done with the current one.
+  __device__ __forceinline__ void advance() {
+    __syncwarp();
+    base += 32;
+    buf ^= 1;
+  }
+
+  // Waits for every copy still in flight (before the warp leaves).
+  __device__ __forceinline__ void drain() const {
+    cp_async_wait<0>();
+    __syncwarp();
+  }
+};
 
 // Hit predicate without the depth: the sign test of ray_hit's discriminant,
 // with the same operations, so it decides exactly as ray_hit does.

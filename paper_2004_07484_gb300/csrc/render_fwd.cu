@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
                                                           const uint32_t* __restrict__ list,
                                                           int store) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpStage<CMAX>& st = *reinterpret_cast<WarpStage<CMAX>*>(smem_raw);
+  StageBuf<CMAX>& sb = *reinterpret_cast<StageBuf<CMAX>*>(smem_raw);
   ItemCtx it;
   if (!item_ctx(v, it)) return;
   const int si = scene_of_tile(v.scenes, v.n_scenes, it.tile);
@@ -110,10 +110,6 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
   const float omax = __uint_as_float(S.omax_bits);
   const bool literal = (S.flags & PULSAR_FLAG_DIST_LITERAL) != 0;
   const int lane = threadIdx.x;
-
-  if (BLEND)   // feature channels beyond C stay zero
-    for (int e = lane; e < 32 * CMAX; e += 32) st.feat[e] = 0.0f;
-  __syncwarp();
 
   // the background term e^{eps/g - m} belongs to the first segment only
   BlendState<CMAX> bs;
@@ -139,33 +135,38 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
   bool done = !pc.inside;
   float kstop1 = __int_as_float(0x7f800000);   // tracked-set bound (i)
 
-  for (int base = it.b0; base < it.b1; base += 32) {
+  WarpStream<CMAX> ws;
+  ws.start(sb, v, list, it.b0, it.b1, BLEND);
+  for (; ws.base < it.b1; ws.advance()) {
     if (__all_sync(0xffffffffu, done)) break;
     // remaining-mass bound (ii), from the state at the start of this batch
     float kstop2 = -__int_as_float(0x7f800000);
     if (BLEND && !done && omax > 0.0f) {
-      const float lr = bs.m + __logf(1e-7f * bs.den / ((float)(it.b1 - base) * omax));
+      const float lr = bs.m + __logf(1e-7f * bs.den / ((float)(it.b1 - ws.base) * omax));
       const float zthr = lr * gamma / omax;
       kstop2 = zthr >= 1.0f ? -__int_as_float(0x7f800000) : zfar - range * zthr;
     }
-    const int cnt = stage_warp<CMAX>(st, v, S, list, base, it.b1, wr, BLEND, BLEND);
+    const uint32_t live = ws.begin(sb, v, S, list, wr, BLEND);
+    const int cur = ws.buf;
     // phase 1: which staged spheres does this lane's ray meet?
     uint32_t hits = 0u;
     if (!done) {
-      for (int k = 0; k < cnt; ++k) {
-        const float4 b = st.rec1[k];
+      for (uint32_t m = live; m; m &= m - 1u) {
+        const int j = __ffs(m) - 1;
+        const float4 b = sb.rec1[cur][j];
         if (!in_rect(b, pc.px, pc.py)) continue;
         ++ntest;
-        const float4 a = st.rec0[k];
-        if (ray_disc_positive(a.x, a.y, a.z, a.w, pc.rx, pc.ry)) hits |= 1u << k;
+        const float4 a = sb.rec0[cur][j];
+        if (ray_disc_positive(a.x, a.y, a.z, a.w, pc.rx, pc.ry)) hits |= 1u << j;
       }
     }
+    if (BLEND) ws.wait_values();
     // phase 2: this lane's hits, in list order
     while (hits) {
-      const int k = __ffs(hits) - 1;
+      const int j = __ffs(hits) - 1;
       hits &= hits - 1u;
-      const float4 a = st.rec0[k];
-      const float4 b = st.rec1[k];
+      const float4 a = sb.rec0[cur][j];
+      const float4 b = sb.rec1[cur][j];
       if (b.x >= fmaxf(kstop1, kstop2)) {
         done = true;
         break;
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
       // c_z + R only by rounding), the phase-1 test alone decides the hit.
       const bool may_queue = b.x <= thr_t;
       float4 c2 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (BLEND) c2 = st.rec2[k];
+      if (BLEND) c2 = sb.rec2[cur][j];
       if (!BLEND && !may_queue) continue;   // cannot change the tracked set
       float t = 0.0f;
       if (may_queue || !(fmaf(1.0001f, a.z, 1.001f * c2.w) < zfar)) {
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
         t = h.t;
       }
       ++nhit;
-      const int id = st.id[k];
+      const int id = sb.id[cur][j];
       if (BLEND) {
         const ValueFwd vg = value_fwd(a, c2, pc.vr);
         const float qd = fminf(vg.qd, 1.0f);
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
         const float od = b.y * d;
         if (od != 0.0f) {   // a zero weight adds nothing and must not move the shift
           const float z = (((zfar - a.z) - c2.z) + vg.off) * inv_range;
-          blend_hit<CMAX>(bs, b.y * z * inv_gamma, od, &st.feat[k * CMAX], id);
+          blend_hit<CMAX>(bs, b.y * z * inv_gamma, od, &sb.feat[cur][j * CMAX], id);
         }
       }
       if (may_queue && hit_less(t, id, thr_t, thr_i)) {
@@ -205,9 +206,9 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
     }
     // a pixel that stopped at no hit still stops once the batch's last key
     // passes its bound (keys rise along the list)
-    if (!done && cnt > 0 && st.rec1[cnt - 1].x >= fmaxf(kstop1, kstop2)) done = true;
-    __syncwarp();
+    if (!done && sb.rec1[cur][ws.count() - 1].x >= fmaxf(kstop1, kstop2)) done = true;
   }
+  ws.drain();
 
   if (it.nseg > 1) {
     // leave this block's segment state, then let the block's last segment merge
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
 
 template <int KMAX, int CMAX, bool BLEND>
 cudaError_t launch_t(const WsView& v, const uint32_t* list, bool store, cudaStream_t st) {
-  const size_t smem = sizeof(WarpStage<CMAX>);
+  const size_t smem = sizeof(StageBuf<CMAX>);
   auto kern = traverse_kernel<KMAX, CMAX, BLEND>;
   kern<<<(unsigned)v.max_items * kBlocksPerTile, 32, smem, st>>>(v, list, store ? 1 : 0);
   return cudaGetLastError();
