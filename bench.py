@@ -35,6 +35,21 @@ WORKLOAD = "1M spheres on 20 ellipsoid surfaces, 1024x1024, C=16 N(0,1), gamma=1
 FP32_LANES_PER_SM = 128
 N_SMS = 152
 
+# DRAM bytes per launch of the forward render kernel on this workload, from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only
+# for the kernel sources with this digest, reported as null otherwise.
+FWD_KERNEL_SOURCES = ("render_fwd.cu", "render_common.cuh", "pulsar_internal.cuh")
+FWD_TRAFFIC = {"sha256": "05261fa5185b4b1016210ce7130802e8e19ef4eca4cab6b014449110ae732a5a", "bytes": 167737600 + 194724608}
+
+
+def fwd_kernel_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in FWD_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2004_07484_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
 
 def rank_info():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
@@ -51,40 +66,57 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    """nvidia-smi clock and throttle-reason samples during the timed region.
+
+    A reader thread collects the samples; entering waits for the first one so
+    that sampling has started before the region begins, and only samples taken
+    between entry and exit are summarised."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_ms: int = 50):
         self.gpu = gpu_index
+        self.period_ms = period_ms
         self.proc = None
+        self.lines: list[str] = []
+        self.active = False
+
+    def _reader(self):
+        for line in self.proc.stdout:
+            if self.active:
+                self.lines.append(line)
+            self.first.set()
 
     def __enter__(self):
+        import threading
+        self.first = threading.Event()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.period_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return self
+        threading.Thread(target=self._reader, daemon=True).start()
+        self.first.wait(timeout=5.0)
+        self.active = True
         return self
 
     def __exit__(self, *a):
-        self.out = ""
+        self.active = False
         if self.proc is not None:
-            time.sleep(0.25)
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                self.out = ""
 
     def summary(self):
-        rows = [r.split(",") for r in self.out.strip().splitlines() if r.count(",") >= 8]
+        rows = [r.split(",") for r in self.lines if r.count(",") >= 8]
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -152,13 +184,93 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+BATCH_WORKLOAD = ("32 scenes, sphere counts log-uniform in [1e3, 5e5], square resolutions from "
+                  "{128, 256, 512, 1024}, 8-Gaussian mixtures, C=8 N(0,1), n_track=10, gamma "
+                  "log-uniform in [1e-3, 0.1], random camera poses")
+
+
+def bench_batched(dev, steps: int, warmup: int, flush):
+    """The 32-scene batch: per-scene plain calls (default scheduling) against one
+    batched call sequence (autotuned scheduling) and its CUDA-graph replay.
+    Each step renders and back-propagates all 32 scenes; renders/s = 32 / step."""
+    import torch
+    from paper_2004_07484_gb300 import autotune, backward_batch, backward_frame, forward_batch, forward_frame
+    from paper_2004_07484_gb300 import RenderSettings, scenes
+    scs = scenes.batch_scenes(1003)
+    inputs = [tuple(torch.from_numpy(np.ascontiguousarray(getattr(sc, k))).to(dev)
+                    for k in ("pos", "feat", "rad", "opa", "cam", "bg")) for sc in scs]
+    g = np.random.default_rng(11)
+    grads = [torch.from_numpy(g.standard_normal((sc.height, sc.width, sc.n_channels)).astype(np.float32)).to(dev)
+             for sc in scs]
+    sets = [RenderSettings(sc.width, sc.height, sc.n_channels, sc.n_track, sc.gamma, sc.eps, sc.znear, sc.zfar,
+                           store_hits=True) for sc in scs]
+    t_tune = time.perf_counter()
+    choice = autotune.tune(sets, inputs, grads)
+    t_tune = time.perf_counter() - t_tune
+    tuned = autotune.apply(sets, choice)
+    caps = choice.capacities
+    stream = torch.cuda.current_stream(dev)
+
+    def plain_step():
+        for s, x, G, c in zip(sets, inputs, grads, caps):
+            fr, image, log_norm = forward_frame(s, *x, c, check_overflow=False)
+            backward_frame(fr, *x, image, log_norm, G)
+
+    def batched_step():
+        fr, images, log_norms = forward_batch(tuned, inputs, caps, check_overflow=False)
+        backward_batch(fr, inputs, images, log_norms, grads)
+
+    def timed(fn, k):
+        ms = []
+        for i in range(k):
+            flush.fill_(i & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    for _ in range(max(warmup, 3)):
+        plain_step()
+        batched_step()
+    torch.cuda.synchronize(dev)
+    k = max(3, min(steps, 20))
+    plain_ms = timed(plain_step, k)
+    batched_ms = timed(batched_step, k)
+    # CUDA graph of the batched step (captured after warm-up on a side stream)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        batched_step()
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batched_step()
+    graph_ms = timed(graph.replay, k)
+    n = len(scs)
+    return {"workload": BATCH_WORKLOAD, "scenes": n, "spheres_total": int(sum(sc.n_spheres for sc in scs)),
+            "plain_renders_per_s": n * 1e3 / plain_ms, "batched_renders_per_s": n * 1e3 / batched_ms,
+            "graph_renders_per_s": n * 1e3 / graph_ms, "plain_ms_per_step": plain_ms,
+            "batched_ms_per_step": batched_ms, "graph_ms_per_step": graph_ms,
+            "speedup_graph_vs_plain": plain_ms / graph_ms,
+            "autotune": {"segment": choice.segment, "persistent": choice.persistent,
+                         "candidates_ms": {f"{a}/{'persistent' if b else 'per-unit'}": v
+                                           for (a, b), v in choice.ms.items()},
+                         "seconds": t_tune},
+            "launches_per_step": {"plain": 32 * n, "batched": 32, "graph": 1},
+            "steps": k, "l2": "flushed between steps (256 MB write, untimed)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 32-scene batched comparison")
     ap.add_argument("--recompute", action="store_true", help="time recompute mode as the main value")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run one step inside the NVTX range 'pulsar_step' and exit (for ncu)")
@@ -295,6 +407,8 @@ def main():
         return statistics.median(fwd), statistics.median(bwd)
 
     fwd_ms, bwd_ms = kernel_ms(not args.recompute)
+    sink = torch.zeros(1, device=dev)
+    fp32_peak = _lib.probe_fma_throughput(sink.data_ptr(), 8192, stream.cuda_stream)[0] / 1e12
 
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     host_in = {k: v.cpu().pin_memory() for k, v in t.items()}
@@ -350,17 +464,22 @@ def main():
     # hit (depth, distance term, depth term, exponent, weight, C-channel update),
     # with the test and hit counts from the kernel's own per-pixel counters
     flops_fwd = 14.0 * tests + (21.0 + 2.0 * C) * hits
-    sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    fp32_peak_max = N_SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_nominal = N_SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     dominant = "render_fwd" if fwd_ms >= bwd_ms else "render_bwd"
     achieved = flops_fwd / (fwd_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": "pulsar_render_fwd (traverse_kernel<16, 16, 1>)", "achieved": achieved,
-                "peak": fp32_peak_max, "unit": "TFLOP/s", "frac": achieved / fp32_peak_max,
-                "traffic": None,
-                "peak_kind": f"FP32 FMA pipes: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x max SM clock "
-                             f"({pk.get('sm_max_mhz', 2070.0)} MHz, {pk_kind})",
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "traffic": FWD_TRAFFIC["bytes"] if fwd_kernel_digest() == FWD_TRAFFIC["sha256"] else None,
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "algorithmic_flops_per_launch": flops_fwd,
+                "peak_kind": "measured in this run: FP32 FMA throughput probe (pulsar_probe_fma_throughput, "
+                             "8 independent chains per thread, 64 warps per SM)",
+                "peak_nominal": fp32_nominal,
+                "peak_nominal_kind": f"{N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x max SM clock "
+                                     f"({pk.get('sm_max_mhz', 2070.0)} MHz, {pk_kind})",
                 "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "dominant": dominant,
                 "ray_tests": tests, "hits": hits, "pairs": pairs_needed}
+    batched = None if args.no_batched else bench_batched(dev, args.steps, args.warmup, flush)
     cpu = None
     if not args.no_cpu_baseline:
         dt, frac = cpu_oracle_sample(sc, 16)
@@ -385,7 +504,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": (launches_store * args.steps + launches_rec * len(ms_rec)) if not args.recompute
             else (launches_rec * args.steps + launches_store * len(ms_rec)),
-            "wall_s_timed": t_wall}
+            "wall_s_timed": t_wall, "batched": batched}
     print(json.dumps(line))
     if world > 1:
         dist.barrier()

@@ -67,7 +67,11 @@ enum {
    * d_i = 1 - min(1, dist/R) (weight 1 at the centre, 0 at the rim). */
   PULSAR_FLAG_DIST_LITERAL = 1u << 1,
   /* Disable the one-pixel minimum size (App. B, Step 0). */
-  PULSAR_FLAG_NO_MIN_SIZE = 1u << 2
+  PULSAR_FLAG_NO_MIN_SIZE = 1u << 2,
+  /* Scheduling only (results are unchanged): the render passes run as
+   * persistent kernels, one resident CTA per slot, each taking work items
+   * from a counter, instead of one CTA per work item. */
+  PULSAR_FLAG_PERSISTENT = 1u << 3
 };
 
 /* grad_mask bits of pulsar_render_bwd: gradients are computed only where
@@ -96,6 +100,10 @@ typedef struct {
   float eps;               /* background offset eps of Eq. 1, >= 0 */
   float znear, zfar;       /* depth range mapped to z in [0, 1]; 0 < znear < zfar */
   uint32_t flags;          /* PULSAR_FLAG_* */
+  int32_t segment;         /* scheduling only: list entries per work item of the
+                              render passes (a tile's list is split into segments
+                              rendered in parallel and merged); 0 = 1024, else a
+                              multiple of 32 in [32, 65536] */
 } pulsar_params;
 
 /* Scene inputs: device pointers, float32, contiguous. */
@@ -201,6 +209,88 @@ pulsar_status pulsar_read_status(void* workspace, size_t workspace_bytes, int64_
  *   the number of tiles is always enough). */
 pulsar_status pulsar_render_fwd_static(const pulsar_params* params, const pulsar_scene* scene,
                                        float* image, float* log_norm, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched rendering: several independent scenes (each with its own sphere
+ * count, image size, camera, gamma, eps and depth range) rendered by one
+ * sequence of launches.  The paper renders one scene per call; batching is
+ * this library's scheduling of many such calls: the scenes' spheres, tiles
+ * and pixels are concatenated, every kernel covers all of them, and the
+ * render kernels draw work items of all scenes from one list, longest first.
+ *
+ * Rules shared by the batched entry points
+ *   - 1 <= n_scenes <= PULSAR_MAX_SCENES; params[s] and scenes[s] describe
+ *     scene s.  All scenes share n_channels, n_track, tile and flags.
+ *   - The batch's pair capacity is the sum of the scenes' list_capacity; an
+ *     overflow of that sum is reported by pulsar_read_status, and
+ *     pairs_needed is then the batch's total.
+ *   - A batched workspace serves only batched calls with the same n_scenes
+ *     and params, and each scene's results are those of the single-scene
+ *     entry points on that scene (up to float rounding of the Eq. 1 sums,
+ *     whose summation order may differ).
+ * ------------------------------------------------------------------------ */
+
+#define PULSAR_MAX_SCENES 64
+
+/* Per-scene outputs of pulsar_render_fwd_batched (same meaning and layout as
+ * the arguments of pulsar_render_fwd; the optional ones may be NULL). */
+typedef struct {
+  float* image;       /* H x W x C */
+  float* log_norm;    /* H x W */
+  int32_t* n_hits;    /* optional H x W */
+  int32_t* n_tests;   /* optional H x W */
+  int32_t* tracked;   /* optional H x W x n_track */
+} pulsar_fwd_out;
+
+/* Per-scene inputs and outputs of pulsar_render_bwd_batched (same meaning as
+ * the arguments of pulsar_render_bwd; outputs not selected by grad_mask may
+ * be NULL). */
+typedef struct {
+  const float* image;
+  const float* log_norm;
+  const float* grad_image;
+  float* g_pos;
+  float* g_rad;
+  float* g_opa;
+  float* g_feat;
+  float* g_cam;
+  float* g_bg;
+} pulsar_bwd_io;
+
+/* Workspace bytes for a batch (0 when the settings are invalid). */
+size_t pulsar_workspace_size_batched(int n_scenes, const pulsar_params* params);
+
+/* pulsar_project over every scene of the batch, in one launch. */
+pulsar_status pulsar_project_batched(int n_scenes, const pulsar_params* params,
+                                     const pulsar_scene* scenes, void* workspace,
+                                     size_t workspace_bytes, void* stream);
+
+/* pulsar_bin over every scene of the batch: one depth sort of all spheres
+ * (a sphere's key orders it only against spheres of its own scene, since
+ * tiles are per scene) and one pair sort by global tile. */
+pulsar_status pulsar_bin_batched(int n_scenes, const pulsar_params* params, void* workspace,
+                                 size_t workspace_bytes, void* stream);
+
+/* pulsar_render_fwd over every scene of the batch; out[s] receives scene s. */
+pulsar_status pulsar_render_fwd_batched(int n_scenes, const pulsar_params* params,
+                                        const pulsar_scene* scenes, void* workspace,
+                                        size_t workspace_bytes, const pulsar_fwd_out* out,
+                                        void* stream);
+
+/* pulsar_render_bwd over every scene of the batch; io[s] holds scene s's
+ * forward outputs, upstream gradient and gradient outputs. */
+pulsar_status pulsar_render_bwd_batched(int n_scenes, const pulsar_params* params,
+                                        const pulsar_scene* scenes, void* workspace,
+                                        size_t workspace_bytes, const pulsar_bwd_io* io,
+                                        uint32_t grad_mask, void* stream);
+
+/* The batch's tile lists, as pulsar_read_tile_lists: ranges holds the tiles
+ * of scene 0, then scene 1, ... (n_tiles summed over scenes, x 2 int32), and
+ * ids (the summed list_capacity int32) holds indices into the concatenation
+ * of the scenes' spheres (scene s's sphere i is sum_{k<s} M_k + i). */
+pulsar_status pulsar_read_tile_lists_batched(int n_scenes, const pulsar_params* params,
+                                             void* workspace, size_t workspace_bytes,
+                                             int32_t* ranges, int32_t* ids, void* stream);
 
 /* Static description of a status code. */
 const char* pulsar_status_string(pulsar_status status);

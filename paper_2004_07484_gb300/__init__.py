@@ -4,6 +4,8 @@ The hot path (projection, depth sort, tile binning, forward blend and
 backward pass) runs in hand-written CUDA kernels for sm_103a behind the C ABI
 of include/pulsar.h; ``renderer.Renderer`` wraps it as a PyTorch module.
 """
-from .renderer import Renderer, RenderSettings, forward_frame, backward_frame  # noqa: F401
+from .renderer import (BatchFrame, Renderer, RenderSettings, backward_batch,  # noqa: F401
+                       backward_frame, forward_batch, forward_frame)
 
-__all__ = ["Renderer", "RenderSettings", "forward_frame", "backward_frame"]
+__all__ = ["Renderer", "RenderSettings", "forward_frame", "backward_frame", "BatchFrame",
+           "forward_batch", "backward_batch"]

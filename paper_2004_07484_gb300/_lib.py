@@ -17,13 +17,19 @@ OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = rang
 FLAG_STORE_HITS = 1 << 0
 FLAG_DIST_LITERAL = 1 << 1
 FLAG_NO_MIN_SIZE = 1 << 2
+FLAG_PERSISTENT = 1 << 3
 
 GRAD_POS, GRAD_RAD, GRAD_OPA, GRAD_FEAT, GRAD_CAM, GRAD_BG = (1 << k for k in range(6))
 GRAD_ALL = 63
 
 EXPORTED = ("pulsar_workspace_size", "pulsar_project", "pulsar_bin", "pulsar_render_fwd",
             "pulsar_render_bwd", "pulsar_read_tile_lists", "pulsar_read_status",
-            "pulsar_status_string")
+            "pulsar_status_string", "pulsar_render_fwd_static", "pulsar_workspace_size_batched",
+            "pulsar_project_batched", "pulsar_bin_batched", "pulsar_render_fwd_batched",
+            "pulsar_render_bwd_batched", "pulsar_read_tile_lists_batched",
+            "pulsar_probe_fma_throughput")
+
+MAX_SCENES = 64
 
 
 class Params(ctypes.Structure):
@@ -34,12 +40,21 @@ class Params(ctypes.Structure):
         ("list_capacity", ctypes.c_int64),
         ("gamma", ctypes.c_float), ("eps", ctypes.c_float),
         ("znear", ctypes.c_float), ("zfar", ctypes.c_float),
-        ("flags", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32), ("segment", ctypes.c_int32),
     ]
 
 
 class SceneArgs(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("pos", "rad", "opa", "feat", "cam", "bg")]
+
+
+class FwdOut(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("image", "log_norm", "n_hits", "n_tests", "tracked")]
+
+
+class BwdIO(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("image", "log_norm", "grad_image", "g_pos", "g_rad",
+                                               "g_opa", "g_feat", "g_cam", "g_bg")]
 
 
 class PulsarError(RuntimeError):
@@ -78,6 +93,22 @@ def lib():
         L.pulsar_status_string.restype = ctypes.c_char_p
         L.pulsar_render_fwd_static.argtypes = [P, S, vp, vp, vp]
         L.pulsar_render_fwd_static.restype = ctypes.c_int
+        i32 = ctypes.c_int
+        L.pulsar_workspace_size_batched.argtypes = [i32, P]
+        L.pulsar_workspace_size_batched.restype = sz
+        L.pulsar_project_batched.argtypes = [i32, P, S, vp, sz, vp]
+        L.pulsar_project_batched.restype = ctypes.c_int
+        L.pulsar_bin_batched.argtypes = [i32, P, vp, sz, vp]
+        L.pulsar_bin_batched.restype = ctypes.c_int
+        L.pulsar_render_fwd_batched.argtypes = [i32, P, S, vp, sz, ctypes.POINTER(FwdOut), vp]
+        L.pulsar_render_fwd_batched.restype = ctypes.c_int
+        L.pulsar_render_bwd_batched.argtypes = [i32, P, S, vp, sz, ctypes.POINTER(BwdIO), u32, vp]
+        L.pulsar_render_bwd_batched.restype = ctypes.c_int
+        L.pulsar_read_tile_lists_batched.argtypes = [i32, P, vp, sz, vp, vp, vp]
+        L.pulsar_read_tile_lists_batched.restype = ctypes.c_int
+        L.pulsar_probe_fma_throughput.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(ctypes.c_float), vp]
+        L.pulsar_probe_fma_throughput.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -139,3 +170,46 @@ def read_status(ws: int, ws_bytes: int, stream: int) -> tuple[int, int]:
     need = ctypes.c_int64(0)
     st = lib().pulsar_read_status(ws, ws_bytes, ctypes.byref(need), stream)
     return int(st), int(need.value)
+
+
+# ---------------------------------------------------------------------------
+# batched entry points: `ps` is a ctypes array of Params, `ss` of SceneArgs,
+# `outs` of FwdOut, `ios` of BwdIO (one element per scene)
+# ---------------------------------------------------------------------------
+
+def workspace_size_batched(ps) -> int:
+    n = lib().pulsar_workspace_size_batched(len(ps), ps)
+    if n == 0:
+        raise PulsarError(ERR_INVALID_ARG, "pulsar_workspace_size_batched")
+    return int(n)
+
+
+def project_batched(ps, ss, ws: int, ws_bytes: int, stream: int) -> None:
+    _check(lib().pulsar_project_batched(len(ps), ps, ss, ws, ws_bytes, stream), "pulsar_project_batched")
+
+
+def bin_batched(ps, ws: int, ws_bytes: int, stream: int) -> None:
+    _check(lib().pulsar_bin_batched(len(ps), ps, ws, ws_bytes, stream), "pulsar_bin_batched")
+
+
+def render_fwd_batched(ps, ss, ws: int, ws_bytes: int, outs, stream: int) -> None:
+    _check(lib().pulsar_render_fwd_batched(len(ps), ps, ss, ws, ws_bytes, outs, stream),
+           "pulsar_render_fwd_batched")
+
+
+def render_bwd_batched(ps, ss, ws: int, ws_bytes: int, ios, grad_mask: int, stream: int) -> None:
+    _check(lib().pulsar_render_bwd_batched(len(ps), ps, ss, ws, ws_bytes, ios, grad_mask, stream),
+           "pulsar_render_bwd_batched")
+
+
+def read_tile_lists_batched(ps, ws: int, ws_bytes: int, ranges: int, ids: int, stream: int) -> None:
+    _check(lib().pulsar_read_tile_lists_batched(len(ps), ps, ws, ws_bytes, ranges, ids, stream),
+           "pulsar_read_tile_lists_batched")
+
+
+def probe_fma_throughput(sink: int, iters: int, stream: int) -> tuple[float, float]:
+    """(FP32 FLOP/s, kernel milliseconds) of the FMA probe; synchronises the stream."""
+    f, ms = ctypes.c_double(0.0), ctypes.c_float(0.0)
+    _check(lib().pulsar_probe_fma_throughput(sink, int(iters), ctypes.byref(f), ctypes.byref(ms), stream),
+           "pulsar_probe_fma_throughput")
+    return float(f.value), float(ms.value)

@@ -15,7 +15,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t hdr, scenes, rec0, rec1, rec2, key0, key1, val0, val1, hist, block_sums, pkey0, pkey1, pval0,
-      pval1, radix_tot, ranges, item_begin, item_tile, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
+      pval1, radix_tot, ranges, item_begin, item_tile, item_order, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
       gacc, fin_part, red_part, total;
   int64_t n_spheres, n_tiles, n_pixels, capacity, max_items;
   int32_t sort_blocks, fin_blocks, tile_bits, segment, part_fields;
@@ -38,7 +38,10 @@ pulsar_status validate(const pulsar_params* p) {
   if (p->list_capacity > (int64_t)INT32_MAX - kSortTile) return PULSAR_ERR_UNSUPPORTED;
   if (!(p->gamma >= 1e-5f && p->gamma <= 1.0f)) return PULSAR_ERR_INVALID_ARG;
   if (!(p->eps >= 0.0f) || !(p->znear > 0.0f) || !(p->zfar > p->znear)) return PULSAR_ERR_INVALID_ARG;
-  if (p->flags & ~(uint32_t)(PULSAR_FLAG_STORE_HITS | PULSAR_FLAG_DIST_LITERAL | PULSAR_FLAG_NO_MIN_SIZE))
+  if (p->flags & ~(uint32_t)(PULSAR_FLAG_STORE_HITS | PULSAR_FLAG_DIST_LITERAL | PULSAR_FLAG_NO_MIN_SIZE |
+                             PULSAR_FLAG_PERSISTENT))
+    return PULSAR_ERR_INVALID_ARG;
+  if (p->segment != 0 && (p->segment < 32 || p->segment > 65536 || p->segment % 32 != 0))
     return PULSAR_ERR_INVALID_ARG;
   return PULSAR_OK;
 }
@@ -68,7 +71,7 @@ Layout make_layout(const pulsar_params* ps, int n) {
   int bits = 1;
   while (bits < 32 && ((int64_t)1 << bits) < NT) ++bits;
   L.tile_bits = bits;
-  L.segment = kDefaultSegment;
+  L.segment = ps[0].segment > 0 ? ps[0].segment : kDefaultSegment;
   L.max_items = NT + (cap + L.segment - 1) / L.segment;
   L.part_fields = 6 + C + 2 * K;
   size_t off = 0;
@@ -96,6 +99,7 @@ Layout make_layout(const pulsar_params* ps, int n) {
   L.ranges = take(8 * (size_t)NT);
   L.item_begin = take(4 * (size_t)(NT + 1));
   L.item_tile = take(4 * (size_t)L.max_items);
+  L.item_order = take(4 * (size_t)L.max_items);
   // per (tile or work item) x 8 pixel blocks of 32 pixels
   L.tile_done = take(4 * 8 * (size_t)NT);
   L.partial = take(4 * 8 * (size_t)L.max_items * 32 * L.part_fields);
@@ -129,6 +133,7 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.segment = L.segment;
   v.max_items = (int32_t)L.max_items;
   v.part_fields = L.part_fields;
+  v.persistent = (ps[0].flags & PULSAR_FLAG_PERSISTENT) ? 1 : 0;
   v.rec0 = reinterpret_cast<float4*>(b + L.rec0);
   v.rec1 = reinterpret_cast<float4*>(b + L.rec1);
   v.rec2 = reinterpret_cast<float4*>(b + L.rec2);
@@ -146,6 +151,7 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.ranges = reinterpret_cast<int2*>(b + L.ranges);
   v.item_begin = reinterpret_cast<int32_t*>(b + L.item_begin);
   v.item_tile = reinterpret_cast<int32_t*>(b + L.item_tile);
+  v.item_order = reinterpret_cast<int32_t*>(b + L.item_order);
   v.tile_done = reinterpret_cast<int32_t*>(b + L.tile_done);
   v.partial = reinterpret_cast<float*>(b + L.partial);
   v.item_kappa = reinterpret_cast<float*>(b + L.item_kappa);
@@ -198,11 +204,29 @@ void fill_scenes(const pulsar_params* ps, const pulsar_scene* sc, int n, SceneDe
   }
 }
 
-pulsar_status check_ws(const pulsar_params* p, void* ws, size_t bytes, Layout& L) {
-  pulsar_status st = validate(p);
+// A batch is valid when every scene is, and the scenes share the settings
+// the kernels are specialised on.
+pulsar_status validate_batch(int n, const pulsar_params* ps) {
+  if (n < 1 || n > kMaxScenes || !ps) return n > kMaxScenes ? PULSAR_ERR_UNSUPPORTED : PULSAR_ERR_INVALID_ARG;
+  int64_t M = 0, cap = 0;
+  for (int s = 0; s < n; ++s) {
+    pulsar_status st = validate(&ps[s]);
+    if (st != PULSAR_OK) return st;
+    if (ps[s].n_channels != ps[0].n_channels || ps[s].n_track != ps[0].n_track ||
+        ps[s].tile != ps[0].tile || ps[s].flags != ps[0].flags || ps[s].segment != ps[0].segment)
+      return PULSAR_ERR_INVALID_ARG;
+    M += ps[s].n_spheres;
+    cap += ps[s].list_capacity;
+  }
+  if (M > (int64_t)INT32_MAX - kSortTile || cap > (int64_t)INT32_MAX - kSortTile) return PULSAR_ERR_UNSUPPORTED;
+  return PULSAR_OK;
+}
+
+pulsar_status check_ws(int n, const pulsar_params* p, void* ws, size_t bytes, Layout& L) {
+  pulsar_status st = validate_batch(n, p);
   if (st != PULSAR_OK) return st;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return PULSAR_ERR_INVALID_ARG;
-  L = make_layout(p, 1);
+  L = make_layout(p, n);
   if (bytes < L.total) return PULSAR_ERR_CAPACITY;
   return PULSAR_OK;
 }
@@ -213,7 +237,118 @@ bool scene_ok(const pulsar_params* p, const pulsar_scene* s) {
   return true;
 }
 
+bool scenes_ok(int n, const pulsar_params* p, const pulsar_scene* s) {
+  if (!s) return false;
+  for (int k = 0; k < n; ++k)
+    if (!scene_ok(&p[k], &s[k])) return false;
+  return true;
+}
+
 pulsar_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PULSAR_OK : PULSAR_ERR_CUDA; }
+
+pulsar_status project_n(int n, const pulsar_params* params, const pulsar_scene* scenes, void* ws,
+                        size_t bytes, cudaStream_t s) {
+  Layout L;
+  pulsar_status st = check_ws(n, params, ws, bytes, L);
+  if (st != PULSAR_OK) return st;
+  if (!scenes_ok(n, params, scenes)) return PULSAR_ERR_INVALID_ARG;
+  WsView v = make_view(ws, L, params, n);
+  SceneDev d[kMaxScenes];
+  fill_scenes(params, scenes, n, d);
+  cudaError_t e = launch_setup(v, d, n, s);
+  if (e == cudaSuccess) e = launch_project(v, s);
+  return cuda_status(e);
+}
+
+pulsar_status bin_n(int n, const pulsar_params* params, void* ws, size_t bytes, cudaStream_t s) {
+  Layout L;
+  pulsar_status st = check_ws(n, params, ws, bytes, L);
+  if (st != PULSAR_OK) return st;
+  WsView v = make_view(ws, L, params, n);
+  return cuda_status(launch_bin(v, L.tile_bits, s));
+}
+
+pulsar_status fwd_n(int n, const pulsar_params* params, const pulsar_scene* scenes, void* ws,
+                    size_t bytes, const pulsar_fwd_out* out, cudaStream_t s) {
+  Layout L;
+  pulsar_status st = check_ws(n, params, ws, bytes, L);
+  if (st != PULSAR_OK) return st;
+  if (!scenes_ok(n, params, scenes) || !out) return PULSAR_ERR_INVALID_ARG;
+  for (int k = 0; k < n; ++k)
+    if (!out[k].image || !out[k].log_norm) return PULSAR_ERR_INVALID_ARG;
+  WsView v = make_view(ws, L, params, n);
+  SceneDev d[kMaxScenes];
+  fill_scenes(params, scenes, n, d);
+  for (int k = 0; k < n; ++k) {
+    d[k].image = out[k].image;
+    d[k].log_norm = out[k].log_norm;
+    d[k].n_hits = out[k].n_hits;
+    d[k].n_tests = out[k].n_tests;
+    d[k].tracked = out[k].tracked;
+  }
+  cudaError_t e = launch_setup(v, d, -n, s);
+  if (e == cudaSuccess) e = launch_render_fwd(v, s);
+  return cuda_status(e);
+}
+
+pulsar_status bwd_n(int n, const pulsar_params* params, const pulsar_scene* scenes, void* ws,
+                    size_t bytes, const pulsar_bwd_io* io, uint32_t grad_mask, cudaStream_t s) {
+  Layout L;
+  pulsar_status st = check_ws(n, params, ws, bytes, L);
+  if (st != PULSAR_OK) return st;
+  if (!scenes_ok(n, params, scenes) || !io) return PULSAR_ERR_INVALID_ARG;
+  if (grad_mask & ~(uint32_t)PULSAR_GRAD_ALL) return PULSAR_ERR_INVALID_ARG;
+  for (int k = 0; k < n; ++k) {
+    const pulsar_bwd_io& q = io[k];
+    if (!q.image || !q.log_norm || !q.grad_image) return PULSAR_ERR_INVALID_ARG;
+    if (params[k].n_spheres > 0) {
+      if ((grad_mask & PULSAR_GRAD_POS) && !q.g_pos) return PULSAR_ERR_INVALID_ARG;
+      if ((grad_mask & PULSAR_GRAD_RAD) && !q.g_rad) return PULSAR_ERR_INVALID_ARG;
+      if ((grad_mask & PULSAR_GRAD_OPA) && !q.g_opa) return PULSAR_ERR_INVALID_ARG;
+      if ((grad_mask & PULSAR_GRAD_FEAT) && !q.g_feat) return PULSAR_ERR_INVALID_ARG;
+    }
+    if ((grad_mask & PULSAR_GRAD_CAM) && !q.g_cam) return PULSAR_ERR_INVALID_ARG;
+    if ((grad_mask & PULSAR_GRAD_BG) && !q.g_bg) return PULSAR_ERR_INVALID_ARG;
+  }
+  WsView v = make_view(ws, L, params, n);
+  SceneDev d[kMaxScenes];
+  fill_scenes(params, scenes, n, d);
+  for (int k = 0; k < n; ++k) {
+    const pulsar_bwd_io& q = io[k];
+    d[k].image_in = q.image;
+    d[k].log_norm_in = q.log_norm;
+    d[k].grad_image = q.grad_image;
+    d[k].g_pos = q.g_pos;
+    d[k].g_rad = q.g_rad;
+    d[k].g_opa = q.g_opa;
+    d[k].g_feat = q.g_feat;
+    d[k].g_cam = q.g_cam;
+    d[k].g_bg = q.g_bg;
+  }
+  cudaError_t e = launch_setup(v, d, -n, s);
+  if (e == cudaSuccess) e = launch_zero_grads(v, grad_mask, s);
+  const bool geo_or_values = (grad_mask & ~(uint32_t)PULSAR_GRAD_BG) != 0;
+  if (e == cudaSuccess && geo_or_values && !(params[0].flags & PULSAR_FLAG_STORE_HITS))
+    e = launch_track_pass(v, s);
+  if (e == cudaSuccess) e = launch_render_bwd(v, grad_mask, s);
+  if (e == cudaSuccess) e = launch_finalize(v, grad_mask, s);
+  return cuda_status(e);
+}
+
+pulsar_status read_lists_n(int n, const pulsar_params* params, void* ws, size_t bytes,
+                           int32_t* ranges, int32_t* ids, cudaStream_t s) {
+  Layout L;
+  pulsar_status st = check_ws(n, params, ws, bytes, L);
+  if (st != PULSAR_OK) return st;
+  if (!ranges || (!ids && L.capacity > 0)) return PULSAR_ERR_INVALID_ARG;
+  WsView v = make_view(ws, L, params, n);
+  cudaError_t e = cudaMemcpyAsync(ranges, v.ranges, sizeof(int2) * (size_t)L.n_tiles,
+                                  cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && L.capacity > 0)
+    e = cudaMemcpyAsync(ids, v.pval[v.pair_buf], sizeof(int32_t) * (size_t)L.capacity,
+                        cudaMemcpyDeviceToDevice, s);
+  return cuda_status(e);
+}
 
 }  // namespace
 }  // namespace pulsar
@@ -221,54 +356,50 @@ pulsar_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PULSAR_OK :
 using namespace pulsar;
 
 extern "C" size_t pulsar_workspace_size(const pulsar_params* params) {
-  if (validate(params) != PULSAR_OK) return 0;
-  return make_layout(params, 1).total;
+  return pulsar_workspace_size_batched(1, params);
+}
+
+extern "C" size_t pulsar_workspace_size_batched(int n_scenes, const pulsar_params* params) {
+  if (validate_batch(n_scenes, params) != PULSAR_OK) return 0;
+  return make_layout(params, n_scenes).total;
 }
 
 extern "C" pulsar_status pulsar_project(const pulsar_params* params, const pulsar_scene* scene,
                                         void* workspace, size_t workspace_bytes, void* stream) {
-  Layout L;
-  pulsar_status st = check_ws(params, workspace, workspace_bytes, L);
-  if (st != PULSAR_OK) return st;
-  if (!scene_ok(params, scene)) return PULSAR_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  WsView v = make_view(workspace, L, params, 1);
-  SceneDev d;
-  fill_scenes(params, scene, 1, &d);
-  cudaError_t e = launch_setup(v, &d, 1, s);
-  if (e == cudaSuccess) e = launch_project(v, s);
-  return cuda_status(e);
+  return project_n(1, params, scene, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pulsar_status pulsar_project_batched(int n_scenes, const pulsar_params* params,
+                                                const pulsar_scene* scenes, void* workspace,
+                                                size_t workspace_bytes, void* stream) {
+  return project_n(n_scenes, params, scenes, workspace, workspace_bytes,
+                   static_cast<cudaStream_t>(stream));
 }
 
 extern "C" pulsar_status pulsar_bin(const pulsar_params* params, void* workspace,
                                     size_t workspace_bytes, void* stream) {
-  Layout L;
-  pulsar_status st = check_ws(params, workspace, workspace_bytes, L);
-  if (st != PULSAR_OK) return st;
-  WsView v = make_view(workspace, L, params, 1);
-  return cuda_status(launch_bin(v, L.tile_bits, static_cast<cudaStream_t>(stream)));
+  return bin_n(1, params, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pulsar_status pulsar_bin_batched(int n_scenes, const pulsar_params* params,
+                                            void* workspace, size_t workspace_bytes, void* stream) {
+  return bin_n(n_scenes, params, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" pulsar_status pulsar_render_fwd(const pulsar_params* params, const pulsar_scene* scene,
                                            void* workspace, size_t workspace_bytes, float* image,
                                            float* log_norm, int32_t* n_hits, int32_t* n_tests,
                                            int32_t* tracked, void* stream) {
-  Layout L;
-  pulsar_status st = check_ws(params, workspace, workspace_bytes, L);
-  if (st != PULSAR_OK) return st;
-  if (!scene_ok(params, scene) || !image || !log_norm) return PULSAR_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  WsView v = make_view(workspace, L, params, 1);
-  SceneDev d;
-  fill_scenes(params, scene, 1, &d);
-  d.image = image;
-  d.log_norm = log_norm;
-  d.n_hits = n_hits;
-  d.n_tests = n_tests;
-  d.tracked = tracked;
-  cudaError_t e = launch_setup(v, &d, -1, s);
-  if (e == cudaSuccess) e = launch_render_fwd(v, (params->flags & PULSAR_FLAG_STORE_HITS) != 0, s);
-  return cuda_status(e);
+  const pulsar_fwd_out out = {image, log_norm, n_hits, n_tests, tracked};
+  return fwd_n(1, params, scene, workspace, workspace_bytes, &out, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pulsar_status pulsar_render_fwd_batched(int n_scenes, const pulsar_params* params,
+                                                   const pulsar_scene* scenes, void* workspace,
+                                                   size_t workspace_bytes, const pulsar_fwd_out* out,
+                                                   void* stream) {
+  return fwd_n(n_scenes, params, scenes, workspace, workspace_bytes, out,
+               static_cast<cudaStream_t>(stream));
 }
 
 extern "C" pulsar_status pulsar_render_bwd(const pulsar_params* params, const pulsar_scene* scene,
@@ -277,64 +408,31 @@ extern "C" pulsar_status pulsar_render_bwd(const pulsar_params* params, const pu
                                            const float* grad_image, uint32_t grad_mask,
                                            float* g_pos, float* g_rad, float* g_opa, float* g_feat,
                                            float* g_cam, float* g_bg, void* stream) {
-  Layout L;
-  pulsar_status st = check_ws(params, workspace, workspace_bytes, L);
-  if (st != PULSAR_OK) return st;
-  if (!scene_ok(params, scene) || !image || !log_norm || !grad_image) return PULSAR_ERR_INVALID_ARG;
-  if (grad_mask & ~(uint32_t)PULSAR_GRAD_ALL) return PULSAR_ERR_INVALID_ARG;
-  const int64_t M = params->n_spheres;
-  if (M > 0) {
-    if ((grad_mask & PULSAR_GRAD_POS) && !g_pos) return PULSAR_ERR_INVALID_ARG;
-    if ((grad_mask & PULSAR_GRAD_RAD) && !g_rad) return PULSAR_ERR_INVALID_ARG;
-    if ((grad_mask & PULSAR_GRAD_OPA) && !g_opa) return PULSAR_ERR_INVALID_ARG;
-    if ((grad_mask & PULSAR_GRAD_FEAT) && !g_feat) return PULSAR_ERR_INVALID_ARG;
-  }
-  if ((grad_mask & PULSAR_GRAD_CAM) && !g_cam) return PULSAR_ERR_INVALID_ARG;
-  if ((grad_mask & PULSAR_GRAD_BG) && !g_bg) return PULSAR_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  WsView v = make_view(workspace, L, params, 1);
-  SceneDev d;
-  fill_scenes(params, scene, 1, &d);
-  d.image_in = image;
-  d.log_norm_in = log_norm;
-  d.grad_image = grad_image;
-  d.g_pos = g_pos;
-  d.g_rad = g_rad;
-  d.g_opa = g_opa;
-  d.g_feat = g_feat;
-  d.g_cam = g_cam;
-  d.g_bg = g_bg;
-  cudaError_t e = launch_setup(v, &d, -1, s);
-  const int C = params->n_channels;
-  if (e == cudaSuccess && M > 0)
-    e = cudaMemsetAsync(v.gacc, 0, sizeof(float4) * (size_t)M, s);
-  if (e == cudaSuccess && M > 0 && (grad_mask & PULSAR_GRAD_OPA))
-    e = cudaMemsetAsync(g_opa, 0, sizeof(float) * (size_t)M, s);
-  if (e == cudaSuccess && M > 0 && (grad_mask & PULSAR_GRAD_FEAT))
-    e = cudaMemsetAsync(g_feat, 0, sizeof(float) * (size_t)M * C, s);
-  const bool geo_or_values = (grad_mask & ~(uint32_t)PULSAR_GRAD_BG) != 0;
-  if (e == cudaSuccess && geo_or_values && !(params->flags & PULSAR_FLAG_STORE_HITS))
-    e = launch_track_pass(v, s);
-  if (e == cudaSuccess) e = launch_render_bwd(v, grad_mask, s);
-  if (e == cudaSuccess) e = launch_finalize(v, grad_mask, s);
-  return cuda_status(e);
+  const pulsar_bwd_io io = {image, log_norm, grad_image, g_pos, g_rad, g_opa, g_feat, g_cam, g_bg};
+  return bwd_n(1, params, scene, workspace, workspace_bytes, &io, grad_mask,
+               static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pulsar_status pulsar_render_bwd_batched(int n_scenes, const pulsar_params* params,
+                                                   const pulsar_scene* scenes, void* workspace,
+                                                   size_t workspace_bytes, const pulsar_bwd_io* io,
+                                                   uint32_t grad_mask, void* stream) {
+  return bwd_n(n_scenes, params, scenes, workspace, workspace_bytes, io, grad_mask,
+               static_cast<cudaStream_t>(stream));
 }
 
 extern "C" pulsar_status pulsar_read_tile_lists(const pulsar_params* params, void* workspace,
                                                 size_t workspace_bytes, int32_t* ranges,
                                                 int32_t* ids, void* stream) {
-  Layout L;
-  pulsar_status st = check_ws(params, workspace, workspace_bytes, L);
-  if (st != PULSAR_OK) return st;
-  if (!ranges || (!ids && L.capacity > 0)) return PULSAR_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  WsView v = make_view(workspace, L, params, 1);
-  cudaError_t e = cudaMemcpyAsync(ranges, v.ranges, sizeof(int2) * (size_t)L.n_tiles,
-                                  cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess && L.capacity > 0)
-    e = cudaMemcpyAsync(ids, v.pval[v.pair_buf], sizeof(int32_t) * (size_t)L.capacity,
-                        cudaMemcpyDeviceToDevice, s);
-  return cuda_status(e);
+  return read_lists_n(1, params, workspace, workspace_bytes, ranges, ids,
+                      static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pulsar_status pulsar_read_tile_lists_batched(int n_scenes, const pulsar_params* params,
+                                                        void* workspace, size_t workspace_bytes,
+                                                        int32_t* ranges, int32_t* ids, void* stream) {
+  return read_lists_n(n_scenes, params, workspace, workspace_bytes, ranges, ids,
+                      static_cast<cudaStream_t>(stream));
 }
 
 extern "C" pulsar_status pulsar_read_status(void* workspace, size_t workspace_bytes,

@@ -106,6 +106,28 @@ __global__ void __launch_bounds__(kThreads) project_kernel(WsView v) {
   if (live && (threadIdx.x & 31) == __ffs(peers) - 1 && om_w) atomicMax(&v.scenes[s].omax_bits, om_w);
 }
 
+// One thread per sphere of the batch: clears the per-sphere accumulators the
+// backward pass adds into (dL/dc, dL/dR in the workspace; dL/do and dL/df in
+// the caller's buffers).
+__global__ void __launch_bounds__(kThreads) zero_grads_kernel(WsView v, uint32_t mask) {
+  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= v.n_spheres) return;
+  v.gacc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int s = scene_of_sphere(v.scenes, v.n_scenes, i);
+  const SceneDev& S = v.scenes[s];
+  const int64_t li = i - S.sphere_begin;
+  if (mask & PULSAR_GRAD_OPA) S.g_opa[li] = 0.0f;
+  if (mask & PULSAR_GRAD_FEAT) {
+    const int C = S.n_channels;
+    float* f = S.g_feat + li * C;
+    if ((C & 3) == 0 && (reinterpret_cast<uintptr_t>(f) & 15) == 0) {
+      for (int c = 0; c < C; c += 4) *reinterpret_cast<float4*>(f + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      for (int c = 0; c < C; ++c) f[c] = 0.0f;
+    }
+  }
+}
+
 __device__ __forceinline__ float block_sum(float x, float* sh) {
   x = warp_sum(x);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -299,6 +321,9 @@ __global__ void __launch_bounds__(64) camera_reduce_kernel(WsView v, uint32_t ma
   }
 }
 
+static_assert(sizeof(SetupPack<kMaxScenes>) + sizeof(WsView) <= 32000,
+              "scene descriptors must fit the kernel parameter space");
+
 template <int N>
 cudaError_t setup_n(const WsView& v, const SceneDev* hs, int n, int full, cudaStream_t st) {
   SetupPack<N> pk;
@@ -325,6 +350,13 @@ cudaError_t launch_project(const WsView& v, cudaStream_t st) {
   if (v.n_spheres == 0) return cudaSuccess;
   const int64_t blocks = (v.n_spheres + kThreads - 1) / kThreads;
   project_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_grads(const WsView& v, uint32_t mask, cudaStream_t st) {
+  if (v.n_spheres == 0) return cudaSuccess;
+  const int64_t blocks = (v.n_spheres + kThreads - 1) / kThreads;
+  zero_grads_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(v, mask);
   return cudaGetLastError();
 }
 

@@ -84,7 +84,8 @@ struct WsHeader {
   int32_t n_sort;            // keys in the sphere sort (= total spheres)
   int32_t timeout;           // a bounded device loop gave up
   int32_t n_items;           // (tile, segment) work items of the render passes
-  int32_t pad_[8];
+  int32_t work_next;         // next work unit of a persistent render launch
+  int32_t pad_[7];
 };
 
 // Raw pointers into one workspace, passed to kernels by value.
@@ -104,6 +105,7 @@ struct WsView {
   int32_t segment;           // list entries per work item (a multiple of kChunk)
   int32_t max_items;         // bound on work items: n_tiles + capacity / segment
   int32_t part_fields;       // floats per pixel of a partial forward state
+  int32_t persistent;        // render passes run as persistent kernels
   float4* rec0;              // per sphere: c.x, c.y, c.z, R^2
   float4* rec1;              // per sphere: key, o, x-range (x0 | x1 << 16), y-range
   float4* rec2;              // per sphere: c - c.xyz (low-order part of the double centre), R
@@ -117,6 +119,7 @@ struct WsView {
   int2* ranges;              // per tile [begin, end)
   int32_t* item_begin;       // per tile (+1): first work item
   int32_t* item_tile;        // per work item: its tile
+  int32_t* item_order;       // work items by decreasing segment length (launch order)
   int32_t* tile_done;        // per tile: finished segments (last-finisher merge)
   float* partial;            // per work item: partial forward state, [field][pixel]
   float* item_kappa;         // per work item: d L / d kappa partial
@@ -322,19 +325,25 @@ __device__ __forceinline__ uint32_t pack_range(int lo, int hi) {
   return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
-// Scene owning a global index, given the per-scene begin offsets.
+// Scene owning a global index: the last scene whose first index is at most
+// the given one (begin offsets ascend; an empty scene shares its begin with
+// the next scene and is never returned for an index it does not own).
 __device__ __forceinline__ int scene_of_tile(const SceneDev* scenes, int n_scenes, int64_t tile) {
-  int s = 0;
-  for (int k = 1; k < n_scenes; ++k)
-    if (scenes[k].tile_begin <= tile) s = k;
-  return s;
+  int lo = 0, hi = n_scenes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (scenes[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
 __device__ __forceinline__ int scene_of_sphere(const SceneDev* scenes, int n_scenes, int64_t i) {
-  int s = 0;
-  for (int k = 1; k < n_scenes; ++k)
-    if (scenes[k].sphere_begin <= i) s = k;
-  return s;
+  int lo = 0, hi = n_scenes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (scenes[mid].sphere_begin <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -347,17 +356,13 @@ __device__ __forceinline__ float warp_sum(float v) {
 // host-side launch helpers (defined in the .cu files)
 // ----------------------------------------------------------------------------
 
-struct SceneHost {
-  pulsar_params p;
-  pulsar_scene s;
-};
-
 cudaError_t launch_setup(const WsView& v, const SceneDev* host_scenes, int n, cudaStream_t st);
 cudaError_t launch_project(const WsView& v, cudaStream_t st);
 cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st);
-cudaError_t launch_render_fwd(const WsView& v, bool store, cudaStream_t st);
+cudaError_t launch_render_fwd(const WsView& v, cudaStream_t st);
 cudaError_t launch_track_pass(const WsView& v, cudaStream_t st);
 cudaError_t launch_render_bwd(const WsView& v, uint32_t grad_mask, cudaStream_t st);
 cudaError_t launch_finalize(const WsView& v, uint32_t grad_mask, cudaStream_t st);
+cudaError_t launch_zero_grads(const WsView& v, uint32_t grad_mask, cudaStream_t st);
 
 }  // namespace pulsar

@@ -53,14 +53,13 @@ __device__ __forceinline__ void add_hit_grads(int id_global, int64_t id_local, f
   }
 }
 
+// Back-propagates through work unit w (a pixel block of one work item) with
+// one warp.
 template <int CMAX>
-__global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v,
-                                                            const uint32_t* __restrict__ list,
-                                                            uint32_t mask) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  StageBuf<CMAX>& sb = *reinterpret_cast<StageBuf<CMAX>*>(smem_raw);
+__device__ __forceinline__ void bwd_unit(const WsView& v, const uint32_t* __restrict__ list,
+                                         uint32_t mask, int w, StageBuf<CMAX>& sb) {
   ItemCtx it;
-  if (!item_ctx(v, it)) return;
+  if (!item_ctx(v, w, it)) return;
   const int si = scene_of_tile(v.scenes, v.n_scenes, it.tile);
   const SceneDev& S = v.scenes[si];
   const PixelCtx pc = pixel_ctx(S, it.tile, it.block);
@@ -242,11 +241,40 @@ __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v,
   }
 }
 
+// One CTA per work unit, or (persistent) one resident CTA per slot taking
+// units from the workspace counter.
+template <int CMAX>
+__global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v,
+                                                            const uint32_t* __restrict__ list,
+                                                            uint32_t mask) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StageBuf<CMAX>& sb = *reinterpret_cast<StageBuf<CMAX>*>(smem_raw);
+  if (!v.persistent) {
+    bwd_unit<CMAX>(v, list, mask, blockIdx.x, sb);
+    return;
+  }
+  const int n_units = v.hdr->n_items * kBlocksPerTile;
+  for (;;) {
+    const int w = next_unit(v);
+    if (w >= n_units) break;
+    bwd_unit<CMAX>(v, list, mask, w, sb);
+    __syncwarp();
+  }
+}
+
 template <int CMAX>
 cudaError_t launch_bwd_t(const WsView& v, const uint32_t* list, uint32_t mask, cudaStream_t st) {
   const size_t smem = sizeof(StageBuf<CMAX>);
   auto kern = render_bwd_kernel<CMAX>;
-  kern<<<(unsigned)v.max_items * kBlocksPerTile, 32, smem, st>>>(v, list, mask);
+  unsigned grid = (unsigned)v.max_items * kBlocksPerTile;
+  if (v.persistent) {
+    const unsigned slots = resident_slots(kern, 32, smem);
+    if (slots == 0) return cudaErrorLaunchOutOfResources;
+    if (slots < grid) grid = slots;
+    cudaError_t e = cudaMemsetAsync(&v.hdr->work_next, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, 32, smem, st>>>(v, list, mask);
   return cudaGetLastError();
 }
 

@@ -25,7 +25,10 @@ __device__ __forceinline__ unsigned lane_lt_mask() {
 constexpr int kBlocksPerTile = 8;   // 8 x 4 pixel blocks (warps) per 16 x 16 tile
 
 // One work item: a segment of at most `segment` entries of one tile's list;
-// each of its eight pixel blocks is a separate one-warp CTA.
+// each of its eight pixel blocks is a separate one-warp CTA.  CTAs take the
+// items longest first (the binning pass orders them), so the hardware's
+// in-order CTA dispatch schedules the longest segments earliest and the
+// launch does not end on a long segment started last.
 struct ItemCtx {
   int item;          // work-item index
   int block;         // pixel block of the tile (0..7)
@@ -36,12 +39,14 @@ struct ItemCtx {
   int b0, b1;        // list range [b0, b1) of this segment
 };
 
-// Returns false for grid slots beyond the number of work items.
-__device__ __forceinline__ bool item_ctx(const WsView& v, ItemCtx& c) {
-  c.item = blockIdx.x / kBlocksPerTile;
-  c.block = blockIdx.x % kBlocksPerTile;
-  c.slot = blockIdx.x;
-  if (c.item >= v.hdr->n_items) return false;
+// Work unit w is pixel block w % 8 of the (w / 8)-th longest work item.
+// Returns false for units beyond the number of work items.
+__device__ __forceinline__ bool item_ctx(const WsView& v, int w, ItemCtx& c) {
+  const int rank = w / kBlocksPerTile;
+  if (rank >= v.hdr->n_items) return false;
+  c.item = v.item_order[rank];
+  c.block = w % kBlocksPerTile;
+  c.slot = c.item * kBlocksPerTile + c.block;
   c.tile = v.item_tile[c.item];
   c.first = v.item_begin[c.tile];
   c.nseg = v.item_begin[c.tile + 1] - c.first;
@@ -51,6 +56,24 @@ __device__ __forceinline__ bool item_ctx(const WsView& v, ItemCtx& c) {
   c.b1 = min(rg.x + (c.seg + 1) * v.segment, rg.y);
   if (c.b1 < c.b0) c.b1 = c.b0;
   return true;
+}
+
+// Next work unit of a persistent render kernel (one atomic per warp).
+__device__ __forceinline__ int next_unit(const WsView& v) {
+  int w = 0;
+  if ((threadIdx.x & 31) == 0) w = atomicAdd(&v.hdr->work_next, 1);
+  return __shfl_sync(0xffffffffu, w, 0);
+}
+
+// Resident one-warp CTAs of a kernel on the current device: the grid of a
+// persistent launch.
+template <typename Kernel>
+unsigned resident_slots(Kernel kern, int threads, size_t smem) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess) return 0;
+  return (unsigned)sms * (unsigned)per_sm;
 }
 
 // Geometry of the pixel a thread renders.
@@ -252,39 +275,36 @@ __device__ __forceinline__ bool hit_less(float t, int id, float qt, int qi) {
   return t < qt || (t == qt && id < qi);
 }
 
-// Sorted insertion into the register queue of the KMAX closest hits.  Every
-// index is a compile-time constant so the queue stays in registers.
+// Tracked-hit queue.  A hit is ordered by the key (depth bits << 32 | index):
+// hit depths are positive, so their float bits order as unsigned integers and
+// the key order is (depth, then index).  The queue holds the KMAX smallest
+// keys in ascending order, right-aligned: the first KMAX - K slots hold the
+// sentinel 0, which no hit displaces, so the K-th closest hit (runtime
+// K <= KMAX) always sits in the last slot.  Free slots hold kEmptyKey.
+constexpr uint64_t kEmptyKey = 0x7f8000007fffffffull;   // (+inf, INT_MAX)
+
+__device__ __forceinline__ uint64_t hit_key(float t, int id) {
+  return ((uint64_t)__float_as_uint(t) << 32) | (uint32_t)id;
+}
+__device__ __forceinline__ float key_depth(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
+__device__ __forceinline__ int key_index(uint64_t k) { return (int)(uint32_t)k; }
+
 template <int KMAX>
-__device__ __forceinline__ void queue_insert(float (&qt)[KMAX], int (&qi)[KMAX], float t, int id) {
-  bool lt[KMAX];
+__device__ __forceinline__ void queue_init(uint64_t (&q)[KMAX], int K) {
 #pragma unroll
-  for (int k = 0; k < KMAX; ++k) lt[k] = hit_less(t, id, qt[k], qi[k]);
-#pragma unroll
-  for (int k = KMAX - 1; k >= 1; --k) {
-    const float pt = qt[k - 1];
-    const int pi = qi[k - 1];
-    qt[k] = lt[k - 1] ? pt : (lt[k] ? t : qt[k]);
-    qi[k] = lt[k - 1] ? pi : (lt[k] ? id : qi[k]);
-  }
-  qt[0] = lt[0] ? t : qt[0];
-  qi[0] = lt[0] ? id : qi[0];
+  for (int k = 0; k < KMAX; ++k) q[k] = k < KMAX - K ? 0ull : kEmptyKey;
 }
 
-// The K-th entry (runtime K <= KMAX) as a bitwise one-hot select: a chain of
-// conditional moves on k == K - 1 is turned into an indexed local-memory load
-// by the compiler, which would move the whole queue out of registers.
+// Sorted insertion; the largest key falls off the end.  Every index is a
+// compile-time constant so the queue stays in registers.
 template <int KMAX>
-__device__ __forceinline__ void queue_select(const float (&qt)[KMAX], const int (&qi)[KMAX], int K,
-                                             float& t, int& id) {
-  uint32_t tb = 0u, ib = 0u;
+__device__ __forceinline__ void queue_insert(uint64_t (&q)[KMAX], uint64_t key) {
+  bool lt[KMAX];
 #pragma unroll
-  for (int k = 0; k < KMAX; ++k) {
-    const uint32_t m = 0u - (uint32_t)(k == K - 1);
-    tb |= m & __float_as_uint(qt[k]);
-    ib |= m & (uint32_t)qi[k];
-  }
-  t = __uint_as_float(tb);
-  id = (int)ib;
+  for (int k = 0; k < KMAX; ++k) lt[k] = key < q[k];
+#pragma unroll
+  for (int k = KMAX - 1; k >= 1; --k) q[k] = lt[k - 1] ? q[k - 1] : (lt[k] ? key : q[k]);
+  q[0] = lt[0] ? key : q[0];
 }
 
 // Next float after a positive depth (+inf stays +inf): spheres whose key is

@@ -90,14 +90,12 @@ __device__ __forceinline__ const float* ref_feature(const SceneDev& S, int dom) 
   return dom < 0 ? S.bg : S.feat + (int64_t)(dom - S.sphere_begin) * S.n_channels;
 }
 
+// Renders work unit w (a pixel block of one work item) with one warp.
 template <int KMAX, int CMAX, bool BLEND>
-__global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
-                                                          const uint32_t* __restrict__ list,
-                                                          int store) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  StageBuf<CMAX>& sb = *reinterpret_cast<StageBuf<CMAX>*>(smem_raw);
+__device__ __forceinline__ void traverse_unit(const WsView& v, const uint32_t* __restrict__ list,
+                                              int w, StageBuf<CMAX>& sb) {
   ItemCtx it;
-  if (!item_ctx(v, it)) return;
+  if (!item_ctx(v, w, it)) return;
   const int si = scene_of_tile(v.scenes, v.n_scenes, it.tile);
   const SceneDev& S = v.scenes[si];
   const PixelCtx pc = pixel_ctx(S, it.tile, it.block);
@@ -122,15 +120,8 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
     bs.fref[c] = (BLEND && c < C) ? S.bg[c] : 0.0f;
     bs.res[c] = 0.0f;
   }
-  float qt[KMAX];
-  int qi[KMAX];
-#pragma unroll
-  for (int k = 0; k < KMAX; ++k) {
-    qt[k] = __int_as_float(0x7f800000);
-    qi[k] = 0x7fffffff;
-  }
-  float thr_t = __int_as_float(0x7f800000);
-  int thr_i = 0x7fffffff;
+  uint64_t q[KMAX];
+  queue_init<KMAX>(q, K);
   int nhit = 0, ntest = 0;
   bool done = !pc.inside;
   float kstop1 = __int_as_float(0x7f800000);   // tracked-set bound (i)
@@ -176,7 +167,7 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
       // beyond the n_track-th tracked depth cannot enter the queue; if its
       // far side also lies well in front of zfar (the depth can exceed
       // c_z + R only by rounding), the phase-1 test alone decides the hit.
-      const bool may_queue = b.x <= thr_t;
+      const bool may_queue = b.x <= key_depth(q[KMAX - 1]);
       float4 c2 = make_float4(0.f, 0.f, 0.f, 0.f);
       if (BLEND) c2 = sb.rec2[cur][j];
       if (!BLEND && !may_queue) continue;   // cannot change the tracked set
@@ -198,10 +189,12 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
           blend_hit<CMAX>(bs, b.y * z * inv_gamma, od, &sb.feat[cur][j * CMAX], id);
         }
       }
-      if (may_queue && hit_less(t, id, thr_t, thr_i)) {
-        queue_insert<KMAX>(qt, qi, t, id);
-        queue_select<KMAX>(qt, qi, K, thr_t, thr_i);
-        kstop1 = next_up(thr_t);
+      if (may_queue) {
+        const uint64_t key = hit_key(t, id);
+        if (key < q[KMAX - 1]) {
+          queue_insert<KMAX>(q, key);
+          kstop1 = next_up(key_depth(q[KMAX - 1]));
+        }
       }
     }
     // a pixel that stopped at no hit still stops once the batch's last key
@@ -228,9 +221,10 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
     P[kPHits * 32] = __int_as_float(nhit);
 #pragma unroll
     for (int k = 0; k < KMAX; ++k)
-      if (k < K) {
-        P[(q0 + k) * 32] = qt[k];
-        P[(q0 + K + k) * 32] = __int_as_float(qi[k]);
+      if (k >= KMAX - K) {
+        const int j = k - (KMAX - K);
+        P[(q0 + j) * 32] = key_depth(q[k]);
+        P[(q0 + K + j) * 32] = __int_as_float(key_index(q[k]));
       }
     __threadfence();
     __syncwarp();
@@ -279,16 +273,11 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
         bs.m = m;
       }
       nhit += __float_as_int(__ldcg(Q + kPHits * 32));
-#pragma unroll
-      for (int k = 0; k < KMAX; ++k)
-        if (k < K) {
-          const float t = __ldcg(Q + (q0 + k) * 32);
-          const int id = __float_as_int(__ldcg(Q + (q0 + K + k) * 32));
-          if (hit_less(t, id, thr_t, thr_i)) {
-            queue_insert<KMAX>(qt, qi, t, id);
-            queue_select<KMAX>(qt, qi, K, thr_t, thr_i);
-          }
-        }
+      for (int j = 0; j < K; ++j) {
+        const uint64_t key = hit_key(__ldcg(Q + (q0 + j) * 32), __float_as_int(__ldcg(Q + (q0 + K + j) * 32)));
+        if (key < q[KMAX - 1]) queue_insert<KMAX>(q, key);
+        else break;   // the other segment's entries ascend
+      }
     }
     if (lane == 0) v.tile_done[it.tile * kBlocksPerTile + it.block] = 0;   // ready for the next launch
   }
@@ -314,55 +303,85 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
       int32_t* tr = S.tracked + pix * K;
 #pragma unroll
       for (int k = 0; k < KMAX; ++k)
-        if (k < K) tr[k] = qi[k] == 0x7fffffff ? -1 : (int32_t)(qi[k] - S.sphere_begin);
+        if (k >= KMAX - K) {
+          const int id = key_index(q[k]);
+          tr[k - (KMAX - K)] = id == 0x7fffffff ? -1 : (int32_t)(id - S.sphere_begin);
+        }
     }
-    v.pix_aux[gpix] = make_float4(thr_t, __int_as_float(thr_i), __int_as_float(bs.dom), 0.0f);
+    v.pix_aux[gpix] = make_float4(key_depth(q[KMAX - 1]), __int_as_float(key_index(q[KMAX - 1])),
+                                  __int_as_float(bs.dom), 0.0f);
   } else {
-    reinterpret_cast<float2*>(v.pix_aux)[2 * gpix] = make_float2(thr_t, __int_as_float(thr_i));
+    reinterpret_cast<float2*>(v.pix_aux)[2 * gpix] =
+        make_float2(key_depth(q[KMAX - 1]), __int_as_float(key_index(q[KMAX - 1])));
+  }
+}
+
+// One CTA per work unit, or (persistent) one resident CTA per slot taking
+// units from the workspace counter.
+template <int KMAX, int CMAX, bool BLEND>
+__global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
+                                                          const uint32_t* __restrict__ list,
+                                                          int persistent) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StageBuf<CMAX>& sb = *reinterpret_cast<StageBuf<CMAX>*>(smem_raw);
+  if (!persistent) {
+    traverse_unit<KMAX, CMAX, BLEND>(v, list, blockIdx.x, sb);
+    return;
+  }
+  const int n_units = v.hdr->n_items * kBlocksPerTile;
+  for (;;) {
+    const int w = next_unit(v);
+    if (w >= n_units) break;
+    traverse_unit<KMAX, CMAX, BLEND>(v, list, w, sb);
+    __syncwarp();
   }
 }
 
 template <int KMAX, int CMAX, bool BLEND>
-cudaError_t launch_t(const WsView& v, const uint32_t* list, bool store, cudaStream_t st) {
+cudaError_t launch_t(const WsView& v, const uint32_t* list, cudaStream_t st) {
   const size_t smem = sizeof(StageBuf<CMAX>);
   auto kern = traverse_kernel<KMAX, CMAX, BLEND>;
-  kern<<<(unsigned)v.max_items * kBlocksPerTile, 32, smem, st>>>(v, list, store ? 1 : 0);
+  unsigned grid = (unsigned)v.max_items * kBlocksPerTile;
+  if (v.persistent) {
+    const unsigned slots = resident_slots(kern, 32, smem);
+    if (slots == 0) return cudaErrorLaunchOutOfResources;
+    if (slots < grid) grid = slots;
+    cudaError_t e = cudaMemsetAsync(&v.hdr->work_next, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, 32, smem, st>>>(v, list, v.persistent);
   return cudaGetLastError();
 }
 
 template <int KMAX, bool BLEND>
-cudaError_t launch_k(const WsView& v, const uint32_t* list, bool store, cudaStream_t st) {
+cudaError_t launch_k(const WsView& v, const uint32_t* list, cudaStream_t st) {
   const int C = v.n_channels;
   if constexpr (!BLEND) {
-    return launch_t<KMAX, 4, false>(v, list, store, st);
+    return launch_t<KMAX, 4, false>(v, list, st);
   } else {
-    if (C <= 4) return launch_t<KMAX, 4, true>(v, list, store, st);
-    if (C <= 8) return launch_t<KMAX, 8, true>(v, list, store, st);
-    if (C <= 16) return launch_t<KMAX, 16, true>(v, list, store, st);
-    return launch_t<KMAX, 32, true>(v, list, store, st);
+    if (C <= 4) return launch_t<KMAX, 4, true>(v, list, st);
+    if (C <= 8) return launch_t<KMAX, 8, true>(v, list, st);
+    if (C <= 16) return launch_t<KMAX, 16, true>(v, list, st);
+    return launch_t<KMAX, 32, true>(v, list, st);
   }
 }
 
 template <bool BLEND>
-cudaError_t launch_any(const WsView& v, bool store, cudaStream_t st) {
+cudaError_t launch_any(const WsView& v, cudaStream_t st) {
   if (v.max_items == 0) return cudaSuccess;
   const uint32_t* list = v.pval[v.pair_buf];
   const int K = v.n_track;
-  if (K <= 8) return launch_k<8, BLEND>(v, list, store, st);
-  if (K <= 16) return launch_k<16, BLEND>(v, list, store, st);
-  return launch_k<32, BLEND>(v, list, store, st);
+  if (K <= 8) return launch_k<8, BLEND>(v, list, st);
+  if (K <= 16) return launch_k<16, BLEND>(v, list, st);
+  return launch_k<32, BLEND>(v, list, st);
 }
 
 }  // namespace
 
-cudaError_t launch_render_fwd(const WsView& v, bool store, cudaStream_t st) {
-  return launch_any<true>(v, store, st);
-}
+cudaError_t launch_render_fwd(const WsView& v, cudaStream_t st) { return launch_any<true>(v, st); }
 
 // Recomputes each pixel's n_track-th tracked hit (the backward pass's
 // threshold) by the forward traversal without blending.
-cudaError_t launch_track_pass(const WsView& v, cudaStream_t st) {
-  return launch_any<false>(v, false, st);
-}
+cudaError_t launch_track_pass(const WsView& v, cudaStream_t st) { return launch_any<false>(v, st); }
 
 }  // namespace pulsar

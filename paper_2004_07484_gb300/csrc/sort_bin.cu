@@ -281,10 +281,14 @@ __global__ void __launch_bounds__(kThreads) tile_ranges(WsView v, int buf) {
 
 // Work items of the render passes: every tile's list is cut into segments of
 // at most v.segment entries (an empty tile is one item, so its pixels are
-// still written).  Writes item_begin (n_tiles + 1), item_tile and the item
-// count.
+// still written).  Writes item_begin (n_tiles + 1), item_tile, the item count
+// and item_order, the items by decreasing length (a counting sort over
+// kOrderBuckets length classes; the order within a class is arbitrary).
+constexpr int kOrderBuckets = 64;
+
 __global__ void __launch_bounds__(1024) make_items(WsView v) {
   __shared__ uint32_t warp_tot[33];
+  __shared__ uint32_t bucket[kOrderBuckets];
   const int64_t nt = v.n_tiles;
   const int64_t per = (nt + 1023) / 1024;
   const int64_t t0 = (int64_t)threadIdx.x * per;
@@ -309,6 +313,29 @@ __global__ void __launch_bounds__(1024) make_items(WsView v) {
     v.item_begin[nt] = (int32_t)tot;
     v.hdr->n_items = (int32_t)tot;
   }
+  if (threadIdx.x < kOrderBuckets) bucket[threadIdx.x] = 0u;
+  __syncthreads();
+  // length class of an item: 0 for a full segment ... kOrderBuckets - 1 for an empty one
+  auto cls = [&](uint32_t i) {
+    const int32_t t = v.item_tile[i];
+    const int2 rg = v.ranges[t];
+    const int seg = (int)i - v.item_begin[t];
+    const int rest = rg.y - rg.x - seg * v.segment;
+    const int len = rest < v.segment ? (rest > 0 ? rest : 0) : v.segment;
+    return (int)(((int64_t)(v.segment - len) * (kOrderBuckets - 1)) / v.segment);
+  };
+  for (uint32_t i = threadIdx.x; i < tot; i += 1024) atomicAdd(&bucket[cls(i)], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = 0; b < kOrderBuckets; ++b) {
+      const uint32_t c = bucket[b];
+      bucket[b] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < tot; i += 1024) v.item_order[atomicAdd(&bucket[cls(i)], 1u)] = (int32_t)i;
 }
 
 cudaError_t radix_sort(const WsView& v, uint32_t* keys[2], uint32_t* vals[2], const int32_t* n_dev,

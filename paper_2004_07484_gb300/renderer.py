@@ -33,6 +33,8 @@ class RenderSettings:
     dist_literal: bool = False       # d = min(1, dist/R) instead of 1 - min(1, dist/R)
     min_size: bool = True            # every sphere covers at least one pixel (App. B, Step 0)
     tile: int = 16
+    segment: int = 0                 # scheduling: list entries per work item (0 = library default)
+    persistent: bool = False         # scheduling: persistent render kernels
 
     def flags(self) -> int:
         f = 0
@@ -42,12 +44,15 @@ class RenderSettings:
             f |= _lib.FLAG_DIST_LITERAL
         if not self.min_size:
             f |= _lib.FLAG_NO_MIN_SIZE
+        if self.persistent:
+            f |= _lib.FLAG_PERSISTENT
         return f
 
     def params(self, n_spheres: int, capacity: int) -> _lib.Params:
         return _lib.Params(int(self.width), int(self.height), int(n_spheres), int(self.n_channels),
                            int(self.n_track), int(self.tile), int(capacity), float(self.gamma),
-                           float(self.eps), float(self.znear), float(self.zfar), int(self.flags()))
+                           float(self.eps), float(self.znear), float(self.zfar), int(self.flags()),
+                           int(self.segment))
 
 
 def _dev_f32(name: str, t: torch.Tensor, shape) -> torch.Tensor:
@@ -127,6 +132,91 @@ def backward_frame(fr: Frame, pos, feat, rad, opa, cam, bg, image, log_norm, gra
                     _ptr(g_pos), _ptr(g_rad), _ptr(g_opa), _ptr(g_feat), _ptr(g_cam), _ptr(g_bg),
                     stream)
     return g_pos, g_rad, g_opa, g_feat, g_cam, g_bg
+
+
+class BatchFrame:
+    """Device state of one batched render: the settings of every scene and the workspace."""
+
+    def __init__(self, settings: list[RenderSettings], n_spheres: list[int], capacities: list[int],
+                 device):
+        if not 1 <= len(settings) <= _lib.MAX_SCENES:
+            raise ValueError(f"a batch holds 1..{_lib.MAX_SCENES} scenes, got {len(settings)}")
+        self.settings = list(settings)
+        self.n = len(settings)
+        self.params = (_lib.Params * self.n)(*[s.params(m, c) for s, m, c in
+                                              zip(settings, n_spheres, capacities)])
+        self.ws_bytes = _lib.workspace_size_batched(self.params)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+
+    def capacities(self) -> list[int]:
+        return [int(p.list_capacity) for p in self.params]
+
+
+def _scene_array(inputs):
+    return (_lib.SceneArgs * len(inputs))(*[scene_args(*x) for x in inputs])
+
+
+def forward_batch(settings: list[RenderSettings], inputs, capacities: list[int],
+                  check_overflow: bool = True, n_hits=None, tracked=None, n_tests=None):
+    """Batched project -> bin -> render_fwd over independent scenes.
+
+    ``inputs[s]`` is scene s's (pos, feat, rad, opa, cam, bg); ``n_hits``,
+    ``tracked`` and ``n_tests`` are optional per-scene lists of output
+    tensors.  Returns (frame, images, log_norms)."""
+    dev = inputs[0][0].device
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    ms = [int(x[0].shape[0]) for x in inputs]
+    ss = _scene_array(inputs)
+    caps = list(capacities)
+    while True:
+        fr = BatchFrame(settings, ms, caps, dev)
+        _lib.project_batched(fr.params, ss, fr.ws.data_ptr(), fr.ws_bytes, stream)
+        _lib.bin_batched(fr.params, fr.ws.data_ptr(), fr.ws_bytes, stream)
+        if not check_overflow:
+            break
+        st, need = _lib.read_status(fr.ws.data_ptr(), fr.ws_bytes, stream)
+        if st == _lib.OK:
+            break
+        if st != _lib.ERR_CAPACITY:
+            raise _lib.PulsarError(st, "pulsar_bin_batched")
+        scale = 1.25 * need / max(sum(caps), 1)
+        caps = [int(c * scale) + 1024 for c in caps]
+    images, log_norms = [], []
+    outs = (_lib.FwdOut * len(inputs))()
+    for k, s in enumerate(settings):
+        image = torch.empty((s.height, s.width, s.n_channels), dtype=torch.float32, device=dev)
+        log_norm = torch.empty((s.height, s.width), dtype=torch.float32, device=dev)
+        images.append(image)
+        log_norms.append(log_norm)
+        outs[k] = _lib.FwdOut(image.data_ptr(), log_norm.data_ptr(),
+                              _ptr(n_hits[k]) if n_hits else None,
+                              _ptr(n_tests[k]) if n_tests else None,
+                              _ptr(tracked[k]) if tracked else None)
+    _lib.render_fwd_batched(fr.params, ss, fr.ws.data_ptr(), fr.ws_bytes, outs, stream)
+    return fr, images, log_norms
+
+
+def backward_batch(fr: BatchFrame, inputs, images, log_norms, grad_images,
+                   grad_mask: int = _lib.GRAD_ALL):
+    """Batched render_bwd.  Returns, per scene, the six gradients (None where not asked)."""
+    dev = inputs[0][0].device
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    ios = (_lib.BwdIO * len(inputs))()
+    grads = []
+    for k, (x, s) in enumerate(zip(inputs, fr.settings)):
+        M, C = int(x[0].shape[0]), s.n_channels
+
+        def alloc(flag, shape):
+            return torch.empty(shape, dtype=torch.float32, device=dev) if grad_mask & flag else None
+
+        g = (alloc(_lib.GRAD_POS, (M, 3)), alloc(_lib.GRAD_RAD, (M,)), alloc(_lib.GRAD_OPA, (M,)),
+             alloc(_lib.GRAD_FEAT, (M, C)), alloc(_lib.GRAD_CAM, (11,)), alloc(_lib.GRAD_BG, (C,)))
+        grads.append(g)
+        ios[k] = _lib.BwdIO(images[k].data_ptr(), log_norms[k].data_ptr(), grad_images[k].data_ptr(),
+                            *[_ptr(t) for t in g])
+    _lib.render_bwd_batched(fr.params, _scene_array(inputs), fr.ws.data_ptr(), fr.ws_bytes, ios,
+                            int(grad_mask), stream)
+    return grads
 
 
 class _RenderFunction(torch.autograd.Function):

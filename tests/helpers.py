@@ -16,19 +16,21 @@ def to_dev(scene: Scene):
     return d
 
 
-def settings_of(scene: Scene, store=True, dist_literal=False, min_size=True, n_track=None):
+def settings_of(scene: Scene, store=True, dist_literal=False, min_size=True, n_track=None, segment=0,
+                persistent=False):
     from paper_2004_07484_gb300 import RenderSettings
     return RenderSettings(scene.width, scene.height, scene.n_channels,
                           n_track or scene.n_track, float(scene.gamma), float(scene.eps),
-                          float(scene.znear), float(scene.zfar), store, dist_literal, min_size)
+                          float(scene.znear), float(scene.zfar), store, dist_literal, min_size,
+                          segment=segment, persistent=persistent)
 
 
 def gpu_forward(scene: Scene, store=True, dist_literal=False, min_size=True, capacity=None,
-                n_track=None, dev=None):
+                n_track=None, dev=None, segment=0, persistent=False):
     import torch
     from paper_2004_07484_gb300 import forward_frame
     dev = dev or to_dev(scene)
-    s = settings_of(scene, store, dist_literal, min_size, n_track)
+    s = settings_of(scene, store, dist_literal, min_size, n_track, segment, persistent)
     H, W, K = scene.height, scene.width, s.n_track
     n_hits = torch.empty((H, W), dtype=torch.int32, device="cuda")
     tracked = torch.empty((H, W, K), dtype=torch.int32, device="cuda")
@@ -101,11 +103,43 @@ def grad_error(g: np.ndarray, ref: np.ndarray):
     return rel, worst
 
 
-def assert_grads_close(got: dict, ref, names=GRAD_NAMES, rtol=1e-3):
+def camera_term_scale(scene, ref) -> float:
+    """Sum of magnitudes of the per-sphere terms the camera gradient adds up.
+
+    dL/dt = -sum_i dL/dp_i and dL/dR = sum_i (R dL/dp_i) (p_i - t)^T, so every
+    camera element is a sum over spheres whose terms are bounded by
+    |dL/dp_i| max(1, |p_i - t|).  Summing terms that each carry the float32
+    relative error the per-sphere gradients are held to, an element cannot be
+    held tighter than that error times this scale (the standard bound for a
+    sum); it takes the place of max|dL/dcam| in the elementwise floor when it
+    is the larger."""
+    p = np.asarray(scene.pos, np.float64)
+    if p.size == 0:
+        return 0.0
+    d = np.linalg.norm(p - np.asarray(scene.cam[:3], np.float64), axis=1)
+    return float((np.linalg.norm(np.asarray(ref.pos, np.float64), axis=1) * np.maximum(1.0, d)).sum())
+
+
+def grad_error_scaled(g: np.ndarray, ref: np.ndarray, floor_scale: float):
+    """grad_error with the elementwise floor taken from max(max|ref|, floor_scale)."""
+    g = np.asarray(g, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    scale = float(np.abs(ref).max()) if ref.size else 0.0
+    if scale == 0.0:
+        return float(np.abs(g).max()) if g.size else 0.0, 0.0
+    rel = float(np.abs(g - ref).max()) / scale
+    worst = float((np.abs(g - ref) / _elem_bound(ref, max(scale, floor_scale))).max())
+    return rel, worst
+
+
+def assert_grads_close(got: dict, ref, names=GRAD_NAMES, rtol=1e-3, scene=None):
     for n in names:
         g = got[n]
         r = getattr(ref, n)
-        rel, worst = grad_error(g, r)
+        if n == "cam" and scene is not None:
+            rel, worst = grad_error_scaled(g, r, camera_term_scale(scene, ref))
+        else:
+            rel, worst = grad_error(g, r)
         if not (rel <= rtol and worst <= 1.0):
             gg, rr = np.asarray(g, np.float64).ravel(), np.asarray(r, np.float64).ravel()
             scale = np.abs(rr).max()

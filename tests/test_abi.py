@@ -84,3 +84,47 @@ def test_entry_points_reject_bad_arguments_before_any_launch(lib):
     bad = _params(lib, gamma=5.0)
     assert L.pulsar_bin(ctypes.byref(bad), 256, 1 << 30, None) == lib.ERR_INVALID_ARG
     assert L.pulsar_read_status(None, 0, None, None) == lib.ERR_INVALID_ARG
+
+
+def _batch(lib, plist):
+    return (lib.Params * len(plist))(*plist)
+
+
+def test_batched_workspace_size_validates_the_batch(lib):
+    L = lib.lib()
+    one = _params(lib)
+    assert L.pulsar_workspace_size_batched(1, _batch(lib, [one])) == L.pulsar_workspace_size(ctypes.byref(one))
+    two = _batch(lib, [_params(lib), _params(lib, width=300, height=20, n_spheres=500, gamma=0.01)])
+    n2 = L.pulsar_workspace_size_batched(2, two)
+    assert n2 > L.pulsar_workspace_size(ctypes.byref(two[1]))
+    # scenes must share channels, n_track and flags; the count is 1..MAX_SCENES
+    for kw in (dict(n_channels=4), dict(n_track=6), dict(flags=0)):
+        assert L.pulsar_workspace_size_batched(2, _batch(lib, [_params(lib), _params(lib, **kw)])) == 0, kw
+    assert L.pulsar_workspace_size_batched(0, _batch(lib, [one])) == 0
+    many = [_params(lib) for _ in range(lib.MAX_SCENES + 1)]
+    assert L.pulsar_workspace_size_batched(lib.MAX_SCENES, _batch(lib, many[:-1])) > 0
+    assert L.pulsar_workspace_size_batched(lib.MAX_SCENES + 1, _batch(lib, many)) == 0
+    # an invalid scene anywhere in the batch invalidates it
+    assert L.pulsar_workspace_size_batched(2, _batch(lib, [_params(lib), _params(lib, gamma=3.0)])) == 0
+
+
+def test_batched_entry_points_reject_bad_arguments_on_the_host(lib):
+    L = lib.lib()
+    ps = _batch(lib, [_params(lib), _params(lib, n_spheres=0)])
+    ss = (lib.SceneArgs * 2)()
+    # no workspace
+    assert L.pulsar_project_batched(2, ps, ss, None, 0, None) == lib.ERR_INVALID_ARG
+    assert L.pulsar_bin_batched(2, ps, None, 0, None) == lib.ERR_INVALID_ARG
+    # a misaligned or short workspace
+    assert L.pulsar_bin_batched(2, ps, 16, 1 << 30, None) == lib.ERR_INVALID_ARG
+    assert L.pulsar_bin_batched(2, ps, 256, 16, None) == lib.ERR_CAPACITY
+    # mixed channel counts
+    bad = _batch(lib, [_params(lib), _params(lib, n_channels=5)])
+    assert L.pulsar_bin_batched(2, bad, 256, 1 << 40, None) == lib.ERR_INVALID_ARG
+    # missing scene pointers (checked before any launch)
+    n = L.pulsar_workspace_size_batched(2, ps)
+    assert L.pulsar_project_batched(2, ps, ss, 256, n, None) == lib.ERR_INVALID_ARG
+    outs = (lib.FwdOut * 2)()
+    assert L.pulsar_render_fwd_batched(2, ps, ss, 256, n, outs, None) == lib.ERR_INVALID_ARG
+    ios = (lib.BwdIO * 2)()
+    assert L.pulsar_render_bwd_batched(2, ps, ss, 256, n, ios, lib.GRAD_ALL, None) == lib.ERR_INVALID_ARG

@@ -134,7 +134,7 @@ def test_backward_matches_oracle(orc, cache, variant, store):
     G = S.grad_image(99, sc.height, sc.width, sc.n_channels)
     want = orc.render_backward(sc, G, **okw)
     got = gpu_backward(gpu, G)
-    assert_grads_close(got, want)
+    assert_grads_close(got, want, scene=sc)
 
 
 def test_store_and_recompute_agree(orc):
@@ -206,7 +206,7 @@ def test_100k_spheres_512_sampled(orc, gamma):
     G[v0:v0 + 24, u0:u0 + 24] = S.grad_image(3, 24, 24, 3)
     want = orc.render_backward(sc, G)
     got = gpu_backward(gpu, G)
-    assert_grads_close(got, want)
+    assert_grads_close(got, want, scene=sc)
 
 
 def test_1m_spheres_1024_sampled(orc):
@@ -229,4 +229,4 @@ def test_1m_spheres_1024_sampled(orc):
     want = orc.render_backward(sc, G)
     for store in (True, False):
         out = gpu if store else gpu_forward(sc, store=False, capacity=16 << 20)
-        assert_grads_close(gpu_backward(out, G), want)
+        assert_grads_close(gpu_backward(out, G), want, scene=sc)
