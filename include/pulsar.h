@@ -187,14 +187,14 @@ pulsar_status pulsar_read_status(void* workspace, size_t workspace_bytes, int64_
                                  void* stream);
 
 /* Size of the device array pulsar_render_fwd_static uses as its workspace. */
-#define PULSAR_STATIC_WORKSPACE_BYTES (16u << 20)
+#define PULSAR_STATIC_WORKSPACE_BYTES (64u << 20)
 
 /* Forward render without a caller-provided workspace and without allocating
  * (the paper has no counterpart; this exists for callers that cannot
  * allocate device memory when they render, e.g. code running where another
  * component owns the device memory, or code that must avoid the device-wide
  * synchronisation cudaFree can cause).
- *   Runs pulsar_project, pulsar_bin and pulsar_render_fwd with a 16 MiB
+ *   Runs pulsar_project, pulsar_bin and pulsar_render_fwd with a 64 MiB
  *   device array inside the library as the workspace.  Inputs and outputs
  *   are the caller's, as for pulsar_render_fwd.
  *   Returns PULSAR_ERR_CAPACITY, before enqueuing anything, when

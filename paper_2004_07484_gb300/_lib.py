@@ -113,7 +113,7 @@ def lib():
     return _lib
 
 
-STATIC_WORKSPACE_BYTES = 16 << 20
+STATIC_WORKSPACE_BYTES = 64 << 20
 
 
 def render_fwd_static(p: Params, s: SceneArgs, image: int, log_norm: int, stream: int) -> None:

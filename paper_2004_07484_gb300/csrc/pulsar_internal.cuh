@@ -120,6 +120,9 @@ struct WsView {
   int32_t* item_begin;       // per tile (+1): first work item
   int32_t* item_tile;        // per work item: its tile
   int32_t* item_order;       // work items by decreasing segment length (launch order)
+  uint2* unit_list;          // block lists: [pixel block][capacity] (sphere, hit mask)
+  int32_t* unit_count;       // per work unit (item x 8 + block): block-list length
+  int32_t* unit_tests;       // per work unit x 32 pixels: rectangle tests made
   int32_t* tile_done;        // per tile: finished segments (last-finisher merge)
   float* partial;            // per work item: partial forward state, [field][pixel]
   float* item_kappa;         // per work item: d L / d kappa partial
@@ -359,6 +362,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 cudaError_t launch_setup(const WsView& v, const SceneDev* host_scenes, int n, cudaStream_t st);
 cudaError_t launch_project(const WsView& v, cudaStream_t st);
 cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st);
+cudaError_t launch_block_lists(const WsView& v, cudaStream_t st);
 cudaError_t launch_render_fwd(const WsView& v, cudaStream_t st);
 cudaError_t launch_track_pass(const WsView& v, cudaStream_t st);
 cudaError_t launch_render_bwd(const WsView& v, uint32_t grad_mask, cudaStream_t st);

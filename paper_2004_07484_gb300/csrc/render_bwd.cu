@@ -56,8 +56,7 @@ __device__ __forceinline__ void add_hit_grads(int id_global, int64_t id_local, f
 // Back-propagates through work unit w (a pixel block of one work item) with
 // one warp.
 template <int CMAX>
-__device__ __forceinline__ void bwd_unit(const WsView& v, const uint32_t* __restrict__ list,
-                                         uint32_t mask, int w, StageBuf<CMAX>& sb) {
+__device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, StageBuf<CMAX>& sb) {
   ItemCtx it;
   if (!item_ctx(v, w, it)) return;
   const int si = scene_of_tile(v.scenes, v.n_scenes, it.tile);
@@ -120,25 +119,13 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, const uint32_t* __rest
   const float kstop = next_up(thr_t);
   bool done = !pc.inside;
   float gk_sum = 0.0f;
-  const WarpRect wr = warp_rect(pc, it.block);
-  WarpStream<CMAX> ws;
-  ws.start(sb, v, list, it.b0, it.b1, true);
-  for (; ws.base < it.b1; ws.advance()) {
+  UnitStream<CMAX> ws;
+  ws.start(sb, v, S, it, true);
+  for (; ws.base < ws.n; ws.advance()) {
     if (__all_sync(0xffffffffu, done)) break;
-    const uint32_t live = ws.begin(sb, v, S, list, wr, true);
+    uint32_t hits = ws.begin(sb, v, S, true);
     const int cur = ws.buf;
-    // phase 1: which staged spheres does this lane's ray meet?
-    uint32_t hits = 0u;
-    if (!done) {
-      for (uint32_t m = live; m; m &= m - 1u) {
-        const int j = __ffs(m) - 1;
-        const float4 b = sb.rec1[cur][j];
-        if (!in_rect(b, pc.px, pc.py)) continue;
-        const float4 a = sb.rec0[cur][j];
-        if (ray_disc_positive(a.x, a.y, a.z, a.w, pc.rx, pc.ry)) hits |= 1u << j;
-      }
-    }
-    ws.wait_values();
+    if (done) hits = 0u;
     // phase 2: this lane's tracked hits, in list order
     while (hits) {
       const int j = __ffs(hits) - 1;
@@ -244,26 +231,24 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, const uint32_t* __rest
 // One CTA per work unit, or (persistent) one resident CTA per slot taking
 // units from the workspace counter.
 template <int CMAX>
-__global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v,
-                                                            const uint32_t* __restrict__ list,
-                                                            uint32_t mask) {
+__global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v, uint32_t mask) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageBuf<CMAX>& sb = *reinterpret_cast<StageBuf<CMAX>*>(smem_raw);
   if (!v.persistent) {
-    bwd_unit<CMAX>(v, list, mask, blockIdx.x, sb);
+    bwd_unit<CMAX>(v, mask, blockIdx.x, sb);
     return;
   }
   const int n_units = v.hdr->n_items * kBlocksPerTile;
   for (;;) {
     const int w = next_unit(v);
     if (w >= n_units) break;
-    bwd_unit<CMAX>(v, list, mask, w, sb);
+    bwd_unit<CMAX>(v, mask, w, sb);
     __syncwarp();
   }
 }
 
 template <int CMAX>
-cudaError_t launch_bwd_t(const WsView& v, const uint32_t* list, uint32_t mask, cudaStream_t st) {
+cudaError_t launch_bwd_t(const WsView& v, uint32_t mask, cudaStream_t st) {
   const size_t smem = sizeof(StageBuf<CMAX>);
   auto kern = render_bwd_kernel<CMAX>;
   unsigned grid = (unsigned)v.max_items * kBlocksPerTile;
@@ -274,7 +259,7 @@ cudaError_t launch_bwd_t(const WsView& v, const uint32_t* list, uint32_t mask, c
     cudaError_t e = cudaMemsetAsync(&v.hdr->work_next, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
   }
-  kern<<<grid, 32, smem, st>>>(v, list, mask);
+  kern<<<grid, 32, smem, st>>>(v, mask);
   return cudaGetLastError();
 }
 
@@ -282,12 +267,11 @@ cudaError_t launch_bwd_t(const WsView& v, const uint32_t* list, uint32_t mask, c
 
 cudaError_t launch_render_bwd(const WsView& v, uint32_t mask, cudaStream_t st) {
   if (v.max_items == 0) return cudaSuccess;
-  const uint32_t* list = v.pval[v.pair_buf];
   const int C = v.n_channels;
-  if (C <= 4) return launch_bwd_t<4>(v, list, mask, st);
-  if (C <= 8) return launch_bwd_t<8>(v, list, mask, st);
-  if (C <= 16) return launch_bwd_t<16>(v, list, mask, st);
-  return launch_bwd_t<32>(v, list, mask, st);
+  if (C <= 4) return launch_bwd_t<4>(v, mask, st);
+  if (C <= 8) return launch_bwd_t<8>(v, mask, st);
+  if (C <= 16) return launch_bwd_t<16>(v, mask, st);
+  return launch_bwd_t<32>(v, mask, st);
 }
 
 }  // namespace pulsar

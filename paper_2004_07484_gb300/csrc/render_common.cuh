@@ -39,23 +39,30 @@ struct ItemCtx {
   int b0, b1;        // list range [b0, b1) of this segment
 };
 
-// Work unit w is pixel block w % 8 of the (w / 8)-th longest work item.
-// Returns false for units beyond the number of work items.
-__device__ __forceinline__ bool item_ctx(const WsView& v, int w, ItemCtx& c) {
-  const int rank = w / kBlocksPerTile;
-  if (rank >= v.hdr->n_items) return false;
-  c.item = v.item_order[rank];
-  c.block = w % kBlocksPerTile;
-  c.slot = c.item * kBlocksPerTile + c.block;
-  c.tile = v.item_tile[c.item];
+// Work item `item` itself and its pixel block `block` (0..7).  Returns false
+// for items beyond the number of work items.
+__device__ __forceinline__ bool item_ctx_direct(const WsView& v, int item, int block, ItemCtx& c) {
+  if (item >= v.hdr->n_items) return false;
+  c.item = item;
+  c.block = block;
+  c.slot = item * kBlocksPerTile + block;
+  c.tile = v.item_tile[item];
   c.first = v.item_begin[c.tile];
   c.nseg = v.item_begin[c.tile + 1] - c.first;
-  c.seg = c.item - c.first;
+  c.seg = item - c.first;
   const int2 rg = v.ranges[c.tile];
   c.b0 = rg.x + c.seg * v.segment;
   c.b1 = min(rg.x + (c.seg + 1) * v.segment, rg.y);
   if (c.b1 < c.b0) c.b1 = c.b0;
   return true;
+}
+
+// Work unit w of a render pass: pixel block w % 8 of the (w / 8)-th longest
+// work item.
+__device__ __forceinline__ bool item_ctx(const WsView& v, int w, ItemCtx& c) {
+  const int rank = w / kBlocksPerTile;
+  if (rank >= v.hdr->n_items) return false;
+  return item_ctx_direct(v, v.item_order[rank], w % kBlocksPerTile, c);
 }
 
 // Next work unit of a persistent render kernel (one atomic per warp).
@@ -123,13 +130,32 @@ __device__ __forceinline__ bool rect_overlaps(const float4& b, const WarpRect& r
 }
 
 // ----------------------------------------------------------------------------
-// Asynchronous staging.  A warp streams its segment of the tile list, 32
-// entries per batch, through two shared-memory buffers with cp.async: the
-// list entries of batch i + 2 and the draw records (rec0, rec1) of batch
-// i + 1 are in flight while batch i is processed, and the value records and
-// features of batch i's spheres that overlap the warp's block are gathered
-// behind its phase-1 hit tests.  Spheres are addressed by their position j in
-// the batch; the overlap ballot says which positions are live.
+// 32 x 32 bit-matrix transpose across a warp: lane i passes row i (bit j =
+// element (i, j)) and receives column i (bit j = element (j, i)).  Five
+// butterfly stages, each swapping the off-diagonal blocks of the next finer
+// block size.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t transpose32(uint32_t x) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t masks[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int s = 16 >> k;
+    const uint32_t m = masks[k];
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
+    x = (lane & s) ? ((x & ~m) | ((y >> s) & m)) : ((x & m) | ((y << s) & ~m));
+  }
+  return x;
+}
+
+// ----------------------------------------------------------------------------
+// Asynchronous staging of a work unit's block list.  A warp streams the list
+// (entries: sphere index, hit mask over the block's 32 pixels), 32 entries
+// per batch, through two shared-memory buffers with cp.async: while batch i
+// is processed, the draw records, value records and features of batch i + 1
+// are in flight and the list entries of batch i + 2 are being loaded.  The
+// batch's hit masks, transposed across the warp, give every lane the bit set
+// of the batch entries that hit its pixel.
 // ----------------------------------------------------------------------------
 
 template <int CMAX>
@@ -139,6 +165,7 @@ struct StageBuf {
   float4 rec2[2][32];
   float feat[2][32 * CMAX];
   int32_t id[2][32];
+  uint32_t hm[2][32];
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -157,85 +184,76 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 template <int CMAX>
-struct WarpStream {
-  int base;           // first list entry of the current batch
-  int end;            // end of the segment
-  int buf;            // buffer holding the current batch
-  uint32_t id_next;   // this lane's list entry of the next batch
+struct UnitStream {
+  const uint2* __restrict__ src;   // the unit's block list
+  int n;                           // its length
+  int base;                        // first entry of the current batch
+  int buf;                         // buffer holding the current batch
+  uint2 e_next;                    // this lane's entry of the next batch
 
-  __device__ __forceinline__ uint32_t load_id(const uint32_t* __restrict__ list, int at) const {
+  __device__ __forceinline__ uint2 load(int at) const {
     const int i = at + (int)(threadIdx.x & 31);
-    return i < end ? __ldg(list + i) : 0u;
+    return i < n ? src[i] : make_uint2(0u, 0u);
   }
 
-  // One commit group: the draw records of the batch at `at` into buffer `to`.
-  __device__ __forceinline__ void issue_records(StageBuf<CMAX>& sb, const WsView& v, int at,
-                                                uint32_t id, int to) const {
+  // One commit group: records (and, with need_values, value records and
+  // features) of the batch at `at`, whose lane entries are e, into buffer `to`.
+  __device__ __forceinline__ void issue(StageBuf<CMAX>& sb, const WsView& v, const SceneDev& S, uint2 e,
+                                        int at, int to, bool need_values) const {
     const int lane = threadIdx.x & 31;
-    if (at + lane < end) {
+    if (at + lane < n) {
+      const uint32_t id = e.x;
       cp_async16(&sb.rec0[to][lane], v.rec0 + id);
       cp_async16(&sb.rec1[to][lane], v.rec1 + id);
       sb.id[to][lane] = (int32_t)id;
-    }
-    cp_async_commit();
-  }
-
-  // Starts the segment [b0, b1).  Feature channels beyond C stay zero.
-  __device__ __forceinline__ void start(StageBuf<CMAX>& sb, const WsView& v,
-                                        const uint32_t* __restrict__ list, int b0, int b1,
-                                        bool need_feat) {
-    const int lane = threadIdx.x & 31;
-    if (need_feat)
-      for (int e = lane; e < 2 * 32 * CMAX; e += 32) (&sb.feat[0][0])[e] = 0.0f;
-    __syncwarp();
-    base = b0;
-    end = b1;
-    buf = 0;
-    issue_records(sb, v, b0, load_id(list, b0), 0);
-    id_next = load_id(list, b0 + 32);
-  }
-
-  // Number of entries in the current batch.
-  __device__ __forceinline__ int count() const { return min(32, end - base); }
-
-  // Waits for the current batch's draw records and returns the ballot of
-  // positions whose pixel rectangles overlap the warp's block.  Starts the
-  // gathers of those spheres' value records and features (one group) and of
-  // the next batch's draw records (another group).
-  __device__ __forceinline__ uint32_t begin(StageBuf<CMAX>& sb, const WsView& v, const SceneDev& S,
-                                            const uint32_t* __restrict__ list, const WarpRect& wr,
-                                            bool need_values) {
-    const int lane = threadIdx.x & 31;
-    cp_async_wait<0>();
-    __syncwarp();
-    const bool ok = base + lane < end && rect_overlaps(sb.rec1[buf][lane], wr);
-    const uint32_t bal = __ballot_sync(0xffffffffu, ok);
-    if (ok && need_values) {
-      const uint32_t id = (uint32_t)sb.id[buf][lane];
-      cp_async16(&sb.rec2[buf][lane], v.rec2 + id);
-      const int C = S.n_channels;
-      const float* __restrict__ src = S.feat + (int64_t)(id - S.sphere_begin) * C;
-      float* dst = &sb.feat[buf][lane * CMAX];
-      if ((C & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+      sb.hm[to][lane] = e.y;
+      if (need_values) {
+        cp_async16(&sb.rec2[to][lane], v.rec2 + id);
+        const int C = S.n_channels;
+        const float* __restrict__ f = S.feat + (int64_t)(id - S.sphere_begin) * C;
+        float* dst = &sb.feat[to][lane * CMAX];
+        if ((C & 3) == 0 && (reinterpret_cast<uintptr_t>(f) & 15) == 0) {
 #pragma unroll
-        for (int c = 0; c < CMAX; c += 4)
-          if (c < C) cp_async16(dst + c, src + c);
-      } else {
+          for (int c = 0; c < CMAX; c += 4)
+            if (c < C) cp_async16(dst + c, f + c);
+        } else {
 #pragma unroll
-        for (int c = 0; c < CMAX; ++c)
-          if (c < C) cp_async4(dst + c, src + c);
+          for (int c = 0; c < CMAX; ++c)
+            if (c < C) cp_async4(dst + c, f + c);
+        }
       }
     }
     cp_async_commit();
-    issue_records(sb, v, base + 32, id_next, buf ^ 1);
-    id_next = load_id(list, base + 64);
-    return bal;
   }
 
-  // Waits for the value records and features of the current batch.
-  __device__ __forceinline__ void wait_values() const {
-    cp_async_wait<1>();
+  // Starts the block list of `unit`.  Feature channels beyond C stay zero.
+  __device__ __forceinline__ void start(StageBuf<CMAX>& sb, const WsView& v, const SceneDev& S,
+                                        const ItemCtx& it, bool need_values) {
+    const int lane = threadIdx.x & 31;
+    if (need_values)
+      for (int e = lane; e < 2 * 32 * CMAX; e += 32) (&sb.feat[0][0])[e] = 0.0f;
     __syncwarp();
+    src = v.unit_list + (size_t)it.block * v.capacity + it.b0;
+    n = v.unit_count[it.slot];
+    base = 0;
+    buf = 0;
+    issue(sb, v, S, load(0), 0, 0, need_values);
+    e_next = load(32);
+  }
+
+  __device__ __forceinline__ int count() const { return min(32, n - base); }
+
+  // Waits for the current batch's staging, starts the next batch's, and
+  // returns the entries of the current batch that hit this lane's pixel.
+  __device__ __forceinline__ uint32_t begin(StageBuf<CMAX>& sb, const WsView& v, const SceneDev& S,
+                                            bool need_values) {
+    cp_async_wait<0>();
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    const uint32_t hits = transpose32(base + lane < n ? sb.hm[buf][lane] : 0u);
+    issue(sb, v, S, e_next, base + 32, buf ^ 1, need_values);
+    e_next = load(base + 64);
+    return hits;
   }
 
   // Moves to the next batch once every lane is done with the current one.

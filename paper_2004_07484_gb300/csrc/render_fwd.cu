@@ -54,7 +54,7 @@ template <int CMAX>
 struct BlendState {
   float m, den, adom;
   int dom;            // global index of the reference sphere, -1 = background
-  float fref[CMAX];
+  float* fref;   // this lane's reference feature, in shared memory (channel stride 32)
   float res[CMAX];
 };
 
@@ -73,14 +73,14 @@ __device__ __forceinline__ void blend_hit(BlendState<CMAX>& b, float s, float od
     // the new hit becomes the reference: re-express the numerator
 #pragma unroll
     for (int c = 0; c < CMAX; ++c) {
-      b.res[c] = fmaf(b.den, b.fref[c] - f[c], b.res[c]);
-      b.fref[c] = f[c];
+      b.res[c] = fmaf(b.den, b.fref[32 * c] - f[c], b.res[c]);
+      b.fref[32 * c] = f[c];
     }
     b.adom = ap;
     b.dom = id;
   } else {
 #pragma unroll
-    for (int c = 0; c < CMAX; ++c) b.res[c] = fmaf(ap, f[c] - b.fref[c], b.res[c]);
+    for (int c = 0; c < CMAX; ++c) b.res[c] = fmaf(ap, f[c] - b.fref[32 * c], b.res[c]);
   }
   b.den += ap;
 }
@@ -92,8 +92,7 @@ __device__ __forceinline__ const float* ref_feature(const SceneDev& S, int dom) 
 
 // Renders work unit w (a pixel block of one work item) with one warp.
 template <int KMAX, int CMAX, bool BLEND>
-__device__ __forceinline__ void traverse_unit(const WsView& v, const uint32_t* __restrict__ list,
-                                              int w, StageBuf<CMAX>& sb) {
+__device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<CMAX>& sb) {
   ItemCtx it;
   if (!item_ctx(v, w, it)) return;
   const int si = scene_of_tile(v.scenes, v.n_scenes, it.tile);
@@ -111,13 +110,14 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, const uint32_t* _
 
   // the background term e^{eps/g - m} belongs to the first segment only
   BlendState<CMAX> bs;
+  bs.fref = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(&sb) + sizeof(StageBuf<CMAX>)) + lane;
   bs.m = S.eps * inv_gamma;
   bs.den = it.seg == 0 ? 1.0f : 0.0f;
   bs.adom = bs.den;
   bs.dom = -1;
 #pragma unroll
   for (int c = 0; c < CMAX; ++c) {
-    bs.fref[c] = (BLEND && c < C) ? S.bg[c] : 0.0f;
+    if (BLEND) bs.fref[32 * c] = c < C ? S.bg[c] : 0.0f;
     bs.res[c] = 0.0f;
   }
   uint64_t q[KMAX];
@@ -126,32 +126,23 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, const uint32_t* _
   bool done = !pc.inside;
   float kstop1 = __int_as_float(0x7f800000);   // tracked-set bound (i)
 
-  WarpStream<CMAX> ws;
-  ws.start(sb, v, list, it.b0, it.b1, BLEND);
-  for (; ws.base < it.b1; ws.advance()) {
+  UnitStream<CMAX> ws;
+  ws.start(sb, v, S, it, BLEND);
+  if (S.n_tests) ntest = v.unit_tests[(size_t)it.slot * 32 + lane];
+  for (; ws.base < ws.n; ws.advance()) {
     if (__all_sync(0xffffffffu, done)) break;
-    // remaining-mass bound (ii), from the state at the start of this batch
+    // remaining-mass bound (ii), from the state at the start of this batch;
+    // the unit's remaining entries are every sphere that can still reach
+    // this block's pixels
     float kstop2 = -__int_as_float(0x7f800000);
     if (BLEND && !done && omax > 0.0f) {
-      const float lr = bs.m + __logf(1e-7f * bs.den / ((float)(it.b1 - ws.base) * omax));
+      const float lr = bs.m + __logf(1e-7f * bs.den / ((float)(ws.n - ws.base) * omax));
       const float zthr = lr * gamma / omax;
       kstop2 = zthr >= 1.0f ? -__int_as_float(0x7f800000) : zfar - range * zthr;
     }
-    const uint32_t live = ws.begin(sb, v, S, list, wr, BLEND);
+    uint32_t hits = ws.begin(sb, v, S, BLEND);
     const int cur = ws.buf;
-    // phase 1: which staged spheres does this lane's ray meet?
-    uint32_t hits = 0u;
-    if (!done) {
-      for (uint32_t m = live; m; m &= m - 1u) {
-        const int j = __ffs(m) - 1;
-        const float4 b = sb.rec1[cur][j];
-        if (!in_rect(b, pc.px, pc.py)) continue;
-        ++ntest;
-        const float4 a = sb.rec0[cur][j];
-        if (ray_disc_positive(a.x, a.y, a.z, a.w, pc.rx, pc.ry)) hits |= 1u << j;
-      }
-    }
-    if (BLEND) ws.wait_values();
+    if (done) hits = 0u;
     // phase 2: this lane's hits, in list order
     while (hits) {
       const int j = __ffs(hits) - 1;
@@ -166,7 +157,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, const uint32_t* _
       // Every hit depth is at least the sphere's key, so a sphere keyed
       // beyond the n_track-th tracked depth cannot enter the queue; if its
       // far side also lies well in front of zfar (the depth can exceed
-      // c_z + R only by rounding), the phase-1 test alone decides the hit.
+      // c_z + R only by rounding), the hit mask alone decides the hit.
       const bool may_queue = b.x <= key_depth(q[KMAX - 1]);
       float4 c2 = make_float4(0.f, 0.f, 0.f, 0.f);
       if (BLEND) c2 = sb.rec2[cur][j];
@@ -257,8 +248,8 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, const uint32_t* _
             if (c < C) {
               const float fb = fB[c];
               bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * 32),
-                               fmaf(bs.den, bs.fref[c] - fb, bs.res[c] * sa));
-              bs.fref[c] = fb;
+                               fmaf(bs.den, bs.fref[32 * c] - fb, bs.res[c] * sa));
+              bs.fref[32 * c] = fb;
             }
           bs.adom = adomB;
           bs.dom = domB;
@@ -267,7 +258,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, const uint32_t* _
           for (int c = 0; c < CMAX; ++c)
             if (c < C)
               bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * 32),
-                               fmaf(denB, fB[c] - bs.fref[c], bs.res[c] * sa));
+                               fmaf(denB, fB[c] - bs.fref[32 * c], bs.res[c] * sa));
         }
         bs.den += denB;
         bs.m = m;
@@ -293,7 +284,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, const uint32_t* _
     for (int c = 0; c < CMAX; ++c)
       if (c < C) {
         const float r = bs.res[c] * inv;
-        out[c] = bs.fref[c] + r;
+        out[c] = bs.fref[32 * c] + r;
         fr[c] = r;
       }
     S.log_norm[pix] = bs.m + __logf(bs.den);
@@ -319,27 +310,26 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, const uint32_t* _
 // One CTA per work unit, or (persistent) one resident CTA per slot taking
 // units from the workspace counter.
 template <int KMAX, int CMAX, bool BLEND>
-__global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v,
-                                                          const uint32_t* __restrict__ list,
-                                                          int persistent) {
+__global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v, int persistent) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageBuf<CMAX>& sb = *reinterpret_cast<StageBuf<CMAX>*>(smem_raw);
   if (!persistent) {
-    traverse_unit<KMAX, CMAX, BLEND>(v, list, blockIdx.x, sb);
+    traverse_unit<KMAX, CMAX, BLEND>(v, blockIdx.x, sb);
     return;
   }
   const int n_units = v.hdr->n_items * kBlocksPerTile;
   for (;;) {
     const int w = next_unit(v);
     if (w >= n_units) break;
-    traverse_unit<KMAX, CMAX, BLEND>(v, list, w, sb);
+    traverse_unit<KMAX, CMAX, BLEND>(v, w, sb);
     __syncwarp();
   }
 }
 
 template <int KMAX, int CMAX, bool BLEND>
-cudaError_t launch_t(const WsView& v, const uint32_t* list, cudaStream_t st) {
-  const size_t smem = sizeof(StageBuf<CMAX>);
+cudaError_t launch_t(const WsView& v, cudaStream_t st) {
+  // staging buffers, then (blending) every lane's reference feature
+  const size_t smem = sizeof(StageBuf<CMAX>) + (BLEND ? sizeof(float) * 32 * CMAX : 0);
   auto kern = traverse_kernel<KMAX, CMAX, BLEND>;
   unsigned grid = (unsigned)v.max_items * kBlocksPerTile;
   if (v.persistent) {
@@ -349,31 +339,30 @@ cudaError_t launch_t(const WsView& v, const uint32_t* list, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(&v.hdr->work_next, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
   }
-  kern<<<grid, 32, smem, st>>>(v, list, v.persistent);
+  kern<<<grid, 32, smem, st>>>(v, v.persistent);
   return cudaGetLastError();
 }
 
 template <int KMAX, bool BLEND>
-cudaError_t launch_k(const WsView& v, const uint32_t* list, cudaStream_t st) {
+cudaError_t launch_k(const WsView& v, cudaStream_t st) {
   const int C = v.n_channels;
   if constexpr (!BLEND) {
-    return launch_t<KMAX, 4, false>(v, list, st);
+    return launch_t<KMAX, 4, false>(v, st);
   } else {
-    if (C <= 4) return launch_t<KMAX, 4, true>(v, list, st);
-    if (C <= 8) return launch_t<KMAX, 8, true>(v, list, st);
-    if (C <= 16) return launch_t<KMAX, 16, true>(v, list, st);
-    return launch_t<KMAX, 32, true>(v, list, st);
+    if (C <= 4) return launch_t<KMAX, 4, true>(v, st);
+    if (C <= 8) return launch_t<KMAX, 8, true>(v, st);
+    if (C <= 16) return launch_t<KMAX, 16, true>(v, st);
+    return launch_t<KMAX, 32, true>(v, st);
   }
 }
 
 template <bool BLEND>
 cudaError_t launch_any(const WsView& v, cudaStream_t st) {
   if (v.max_items == 0) return cudaSuccess;
-  const uint32_t* list = v.pval[v.pair_buf];
   const int K = v.n_track;
-  if (K <= 8) return launch_k<8, BLEND>(v, list, st);
-  if (K <= 16) return launch_k<16, BLEND>(v, list, st);
-  return launch_k<32, BLEND>(v, list, st);
+  if (K <= 8) return launch_k<8, BLEND>(v, st);
+  if (K <= 16) return launch_k<16, BLEND>(v, st);
+  return launch_k<32, BLEND>(v, st);
 }
 
 }  // namespace

@@ -3,7 +3,10 @@
 //   2. exclusive scan of each sorted sphere's tile count,
 //   3. emission of one (tile, sphere) pair per overlapped tile, in depth order,
 //   4. stable LSD radix sort of the pairs by tile,
-//   5. per-tile [begin, end) ranges.
+//   5. per-tile [begin, end) ranges,
+//   6. work items (list segments) in decreasing length,
+//   7. block lists: per segment and 8 x 4 pixel block, the hitting spheres
+//      with their per-pixel hit masks (block_lists.cu).
 // A stable sort of pairs that arrive in depth order keeps every tile's list in
 // (earliest depth, index) order, the order the paper's intersection search
 // relies on for early termination (Sec. 3.2, App. B Step 0).
@@ -396,8 +399,11 @@ cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st) {
     e = cudaMemsetAsync(v.tile_done, 0, sizeof(int32_t) * 8 * (size_t)v.n_tiles, st);
     if (e != cudaSuccess) return e;
     make_items<<<1, 1024, 0, st>>>(v);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
-  return cudaGetLastError();
+  // 7. per pixel block: the spheres hitting it, with their hit masks
+  return launch_block_lists(v, st);
 }
 
 }  // namespace pulsar
