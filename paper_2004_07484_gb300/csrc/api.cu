@@ -293,7 +293,10 @@ pulsar_status fwd_n(int n, const pulsar_params* params, const pulsar_scene* scen
     d[k].n_tests = out[k].n_tests;
     d[k].tracked = out[k].tracked;
   }
+  bool tests = false;
+  for (int k = 0; k < n; ++k) tests = tests || out[k].n_tests != nullptr;
   cudaError_t e = launch_setup(v, d, -n, s);
+  if (e == cudaSuccess && tests) e = launch_count_tests(v, s);
   if (e == cudaSuccess) e = launch_render_fwd(v, s);
   return cuda_status(e);
 }

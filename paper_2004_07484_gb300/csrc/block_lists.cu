@@ -6,11 +6,11 @@
 // order, the spheres the float32 hit predicate reports for at least one
 // pixel of the block, each with its 32-bit hit mask (bit 8 y + x for block
 // pixel (x, y)).  Each lane takes one list entry: it intersects the sphere's
-// pixel rectangle with the block and tests only the pixels of that overlap.
-// The forward pass, the track pass and the backward pass then stream only
-// these entries and read each pixel's hits from the masks, so none of them
-// repeats the rectangle or ray-disc tests.  Per unit and pixel the warp also
-// counts the rectangle tests made (the n_tests diagnostic of the forward).
+// pixel rectangle with the block and tests only the pixels of that overlap;
+// the next chunk's entries and rectangles load while the current chunk is
+// tested.  The forward pass, the track pass and the backward pass then
+// stream only these entries and read each pixel's hits from the masks, so
+// none of them repeats the rectangle or ray-disc tests.
 #include "render_common.cuh"
 
 namespace pulsar {
@@ -28,36 +28,72 @@ __global__ void __launch_bounds__(256) block_lists_kernel(const WsView v, const 
   const WarpRect wr = warp_rect(pc, it.block);
   uint2* out = v.unit_list + (size_t)it.block * v.capacity + it.b0;
   int n = 0;
-  int tests = 0;   // rectangle tests of this lane's pixel
+  // the current chunk's entry and rectangle; the next chunk's are loaded
+  // while this one is tested
+  uint32_t id = 0u;
+  float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (it.b0 + lane < it.b1) {
+    id = __ldg(list + it.b0 + lane);
+    b = __ldg(v.rec1 + id);
+  }
   for (int base = it.b0; base < it.b1; base += 32) {
     const int i = base + lane;
-    uint32_t id = 0u, hm = 0u, rm = 0u;
-    if (i < it.b1) {
-      id = __ldg(list + i);
-      const float4 b = __ldg(v.rec1 + id);
-      if (rect_overlaps(b, wr)) {
-        const float4 a = __ldg(v.rec0 + id);
-        const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
-        const int x0 = max((int)(bx & 0xffffu), wr.x0), x1 = min((int)(bx >> 16), wr.x1);
-        const int y0 = max((int)(by & 0xffffu), wr.y0), y1 = min((int)(by >> 16), wr.y1);
-        for (int y = y0; y <= y1; ++y) {
-          const float ry = ray_coord(y, S.height, S.kappa);
-          for (int x = x0; x <= x1; ++x) {
-            const uint32_t bit = 1u << ((y - wr.y0) * 8 + (x - wr.x0));
-            rm |= bit;
-            if (ray_disc_positive(a.x, a.y, a.z, a.w, ray_coord(x, S.width, S.kappa), ry)) hm |= bit;
-          }
-        }
+    uint32_t id_n = 0u;
+    float4 b_n = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i + 32 < it.b1) {
+      id_n = __ldg(list + i + 32);
+      b_n = __ldg(v.rec1 + id_n);
+    }
+    uint32_t hm = 0u;
+    if (i < it.b1 && rect_overlaps(b, wr)) {
+      const float4 a = __ldg(v.rec0 + id);
+      const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
+      const int x0 = max((int)(bx & 0xffffu), wr.x0), x1 = min((int)(bx >> 16), wr.x1);
+      const int y0 = max((int)(by & 0xffffu), wr.y0), y1 = min((int)(by >> 16), wr.y1);
+      for (int y = y0; y <= y1; ++y) {
+        const float ry = ray_coord(y, S.height, S.kappa);
+        for (int x = x0; x <= x1; ++x)
+          if (ray_disc_positive(a.x, a.y, a.z, a.w, ray_coord(x, S.width, S.kappa), ry))
+            hm |= 1u << ((y - wr.y0) * 8 + (x - wr.x0));
       }
     }
-    tests += __popc(transpose32(rm));
     const uint32_t bal = __ballot_sync(0xffffffffu, hm != 0u);
     if (hm) out[n + __popc(bal & lane_lt_mask())] = make_uint2(id, hm);
     n += __popc(bal);
+    id = id_n;
+    b = b_n;
   }
-  const int unit = item * kBlocksPerTile + it.block;
-  if (lane == 0) v.unit_count[unit] = n;
-  v.unit_tests[(size_t)unit * 32 + lane] = tests;
+  if (lane == 0) v.unit_count[item * kBlocksPerTile + it.block] = n;
+}
+
+// The n_tests diagnostic: per work unit and pixel, the spheres of the
+// segment whose rectangle contains the pixel (the tests the block lists
+// made), counted through a warp bit-matrix transpose.  Run only when a
+// forward pass asks for n_tests.
+__global__ void __launch_bounds__(256) count_tests_kernel(const WsView v, const uint32_t* __restrict__ list) {
+  const int item = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  ItemCtx it;
+  if (!item_ctx_direct(v, item, threadIdx.x >> 5, it)) return;
+  const SceneDev& S = v.scenes[scene_of_tile(v.scenes, v.n_scenes, it.tile)];
+  const WarpRect wr = warp_rect(pixel_ctx(S, it.tile, it.block), it.block);
+  int tests = 0;
+  for (int base = it.b0; base < it.b1; base += 32) {
+    const int i = base + lane;
+    uint32_t rm = 0u;
+    if (i < it.b1) {
+      const float4 b = __ldg(v.rec1 + __ldg(list + i));
+      if (rect_overlaps(b, wr)) {
+        const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
+        const int x0 = max((int)(bx & 0xffffu), wr.x0), x1 = min((int)(bx >> 16), wr.x1);
+        const int y0 = max((int)(by & 0xffffu), wr.y0), y1 = min((int)(by >> 16), wr.y1);
+        const uint32_t row = ((2u << (x1 - wr.x0)) - (1u << (x0 - wr.x0)));
+        for (int y = y0; y <= y1; ++y) rm |= row << ((y - wr.y0) * 8);
+      }
+    }
+    tests += __popc(transpose32(rm));
+  }
+  v.unit_tests[((size_t)item * kBlocksPerTile + it.block) * 32 + lane] = tests;
 }
 
 }  // namespace
@@ -65,6 +101,12 @@ __global__ void __launch_bounds__(256) block_lists_kernel(const WsView v, const 
 cudaError_t launch_block_lists(const WsView& v, cudaStream_t st) {
   if (v.max_items == 0) return cudaSuccess;
   block_lists_kernel<<<(unsigned)v.max_items, 256, 0, st>>>(v, v.pval[v.pair_buf]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_tests(const WsView& v, cudaStream_t st) {
+  if (v.max_items == 0) return cudaSuccess;
+  count_tests_kernel<<<(unsigned)v.max_items, 256, 0, st>>>(v, v.pval[v.pair_buf]);
   return cudaGetLastError();
 }
 

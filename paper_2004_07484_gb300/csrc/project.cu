@@ -40,6 +40,10 @@ __global__ void setup_kernel(WsView v, const SetupPack<N> pk) {
       rows_from_rot6(d.cam + 3, d.rows);
       d.kappa = pixel_pitch(d.cam, d.width);
       rows_from_rot6_f64(d.cam + 3, d.rows64);
+      for (int k = 0; k < 9; ++k) {
+        d.rows_hi[k] = (float)d.rows64[k];
+        d.rows_lo[k] = (float)(d.rows64[k] - (double)d.rows_hi[k]);
+      }
       d.kappa64 = (double)d.cam[10] / ((double)d.width * (double)d.cam[9]);
       d.kappa_hi = (float)d.kappa64;
       d.kappa_lo = (float)(d.kappa64 - (double)d.kappa_hi);
@@ -49,6 +53,8 @@ __global__ void setup_kernel(WsView v, const SetupPack<N> pk) {
       for (int k = 0; k < 9; ++k) {
         d.rows[k] = o.rows[k];
         d.rows64[k] = o.rows64[k];
+        d.rows_hi[k] = o.rows_hi[k];
+        d.rows_lo[k] = o.rows_lo[k];
       }
       d.kappa = o.kappa;
       d.kappa64 = o.kappa64;
@@ -86,18 +92,39 @@ __global__ void __launch_bounds__(kThreads) project_kernel(WsView v) {
                             __uint_as_float(pack_range(pr.y0, pr.y1)));
     v.key[0][i] = __float_as_uint(pr.key);
     v.val[0][i] = (uint32_t)i;
-    // value path: the centre in double, kept as the float32 decision centre
-    // plus a float correction; the radius as used by the value path
-    const double* B = S.rows64;
-    const double dx = (double)p[0] - (double)S.cam[0];
-    const double dy = (double)p[1] - (double)S.cam[1];
-    const double dz = (double)p[2] - (double)S.cam[2];
-    const double cx = B[0] * dx + B[1] * dy + B[2] * dz;
-    const double cy = B[3] * dx + B[4] * dy + B[5] * dz;
-    const double cz = B[6] * dx + B[7] * dy + B[8] * dz;
-    const float Rv = pr.R != r ? (float)(0.75 * sqrt(cx * cx + cy * cy + cz * cz) * S.kappa64) : r;
-    v.rec2[i] = make_float4((float)(cx - (double)pr.cx), (float)(cy - (double)pr.cy),
-                            (float)(cz - (double)pr.cz), Rv);
+    // value path: the centre to about 2^-46 relative (float-float), kept as
+    // the float32 decision centre plus a float correction; the radius as
+    // used by the value path
+    FF c[3];
+    {
+      const FF d0 = two_sum(p[0], -S.cam[0]), d1 = two_sum(p[1], -S.cam[1]), d2 = two_sum(p[2], -S.cam[2]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const FF b0 = {S.rows_hi[3 * k], S.rows_lo[3 * k]};
+        const FF b1 = {S.rows_hi[3 * k + 1], S.rows_lo[3 * k + 1]};
+        const FF b2 = {S.rows_hi[3 * k + 2], S.rows_lo[3 * k + 2]};
+        c[k] = ff_add(ff_add(ff_mul(b0, d0), ff_mul(b1, d1)), ff_mul(b2, d2));
+      }
+    }
+    float Rv = r;
+    if (pr.R != r) {   // R = 0.75 |c| kappa
+      FF n2 = two_prod(c[0].hi, c[0].hi);
+      n2.lo = __fmaf_rn(2.0f * c[0].hi, c[0].lo, n2.lo);
+#pragma unroll
+      for (int k = 1; k < 3; ++k) {
+        FF t = two_prod(c[k].hi, c[k].hi);
+        t.lo = __fmaf_rn(2.0f * c[k].hi, c[k].lo, t.lo);
+        n2 = ff_add(n2, t);
+      }
+      const float sh = __fsqrt_rn(n2.hi);
+      const float sl = __fdiv_rn(__fadd_rn(__fmaf_rn(-sh, sh, n2.hi), n2.lo), __fmul_rn(2.0f, sh));
+      const FF rk = ff_mul(FF{sh, sl}, FF{S.kappa_hi, S.kappa_lo});
+      const FF q = two_prod(rk.hi, 0.75f);
+      Rv = __fadd_rn(q.hi, __fmaf_rn(0.75f, rk.lo, q.lo));
+    }
+    v.rec2[i] = make_float4(__fadd_rn(__fsub_rn(c[0].hi, pr.cx), c[0].lo),
+                            __fadd_rn(__fsub_rn(c[1].hi, pr.cy), c[1].lo),
+                            __fadd_rn(__fsub_rn(c[2].hi, pr.cz), c[2].lo), Rv);
     if (pr.visible) om = __float_as_uint(fabsf(o));
   }
   // warp-aggregated maxima per scene (non-negative floats order as integers)

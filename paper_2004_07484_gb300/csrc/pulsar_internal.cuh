@@ -67,6 +67,8 @@ struct SceneDev {
   float gamma, eps, znear, zfar;
   // derived on the device by the setup kernel
   double rows64[9];          // camera axes in double (value path)
+  float rows_hi[9];          // rows64 as float pairs hi + lo (per-sphere value path)
+  float rows_lo[9];
   double kappa64;            // pixel pitch in double (value path)
   float rows[9];             // camera axes b1, b2, b3 (world -> camera rows), float32 decisions
   float kappa;               // pixel pitch on the unit image plane, s / (W f), float32 decisions
@@ -324,6 +326,38 @@ __device__ __forceinline__ ValueFwd value_fwd(const float4& a, const float4& c2,
   return g;
 }
 
+// Float-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2) from the
+// error-free transformations TwoSum (Knuth) and TwoProd (one FMA).  The
+// per-sphere value path uses it instead of double: FP64 throughput is a small
+// fraction of FP32 on this GPU.
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ FF two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+// (ah + al) * (bh + bl), dropping al * bl.
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  FF p = two_prod(a.hi, b.hi);
+  p.lo = __fadd_rn(p.lo, __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi)));
+  return p;
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  FF s = two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return s;
+}
+
 __device__ __forceinline__ uint32_t pack_range(int lo, int hi) {
   return (uint32_t)lo | ((uint32_t)hi << 16);
 }
@@ -363,6 +397,7 @@ cudaError_t launch_setup(const WsView& v, const SceneDev* host_scenes, int n, cu
 cudaError_t launch_project(const WsView& v, cudaStream_t st);
 cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st);
 cudaError_t launch_block_lists(const WsView& v, cudaStream_t st);
+cudaError_t launch_count_tests(const WsView& v, cudaStream_t st);
 cudaError_t launch_render_fwd(const WsView& v, cudaStream_t st);
 cudaError_t launch_track_pass(const WsView& v, cudaStream_t st);
 cudaError_t launch_render_bwd(const WsView& v, uint32_t grad_mask, cudaStream_t st);
