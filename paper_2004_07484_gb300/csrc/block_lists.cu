@@ -5,10 +5,12 @@
 // 8 x 4 pixel blocks) a warp walks the segment once and keeps, in list
 // order, the spheres the float32 hit predicate reports for at least one
 // pixel of the block, each with its 32-bit hit mask (bit 8 y + x for block
-// pixel (x, y)).  Each lane takes one list entry: it intersects the sphere's
-// pixel rectangle with the block and tests only the pixels of that overlap;
-// the next chunk's entries and rectangles load while the current chunk is
-// tested.  The forward pass, the track pass and the backward pass then
+// pixel (x, y)).  Per chunk of 32 list entries, each lane intersects one
+// sphere's pixel rectangle with the block; the pixel tests of all overlaps
+// (a few per sphere, very unevenly) are then numbered across the warp and
+// spread evenly over the lanes, which OR their results into the entries'
+// masks in shared memory.  The next chunk's entries and rectangles load
+// while the current chunk is tested.  The forward pass, the track pass and the backward pass then
 // stream only these entries and read each pixel's hits from the masks, so
 // none of them repeats the rectangle or ray-disc tests.
 #include "render_common.cuh"
@@ -17,10 +19,22 @@ namespace pulsar {
 
 namespace {
 
+// Per warp: the current chunk's overlapping entries, for the lanes that test
+// their pixels.
+struct ChunkTests {
+  float4 rec0[32];     // draw record (decision centre, R^2)
+  int first[32];       // first test number of each entry
+  uint32_t geom[32];   // overlap with the block: x0 | y0 << 8 | width << 16
+  uint32_t wdiv[32];   // ceil(2^16 / width): test index / width = (index * wdiv) >> 16
+  uint32_t hm[32];     // hit masks being built
+};
+
 __global__ void __launch_bounds__(256) block_lists_kernel(const WsView v, const uint32_t* __restrict__ list) {
+  __shared__ ChunkTests tests_all[8];
   const int item = blockIdx.x;
   const int block = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  ChunkTests& ct = tests_all[block];
   ItemCtx it;
   if (!item_ctx_direct(v, item, block, it)) return;
   const SceneDev& S = v.scenes[scene_of_tile(v.scenes, v.n_scenes, it.tile)];
@@ -44,24 +58,43 @@ __global__ void __launch_bounds__(256) block_lists_kernel(const WsView v, const 
       id_n = __ldg(list + i + 32);
       b_n = __ldg(v.rec1 + id_n);
     }
-    uint32_t hm = 0u;
+    // this entry's overlap with the block: its pixel tests
+    int ntest = 0;
     if (i < it.b1 && rect_overlaps(b, wr)) {
-      const float4 a = __ldg(v.rec0 + id);
       const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
       const int x0 = max((int)(bx & 0xffffu), wr.x0), x1 = min((int)(bx >> 16), wr.x1);
       const int y0 = max((int)(by & 0xffffu), wr.y0), y1 = min((int)(by >> 16), wr.y1);
-      for (int y = y0; y <= y1; ++y) {
-        const float ry = ray_coord(y, S.height, S.kappa);
-        for (int x = x0; x <= x1; ++x)
-          if (ray_disc_positive(a.x, a.y, a.z, a.w, ray_coord(x, S.width, S.kappa), ry))
-            hm |= 1u << ((y - wr.y0) * 8 + (x - wr.x0));
-      }
+      const int w = x1 - x0 + 1;
+      ntest = w * (y1 - y0 + 1);
+      ct.rec0[lane] = __ldg(v.rec0 + id);
+      ct.geom[lane] = (uint32_t)(x0 - wr.x0) | ((uint32_t)(y0 - wr.y0) << 8) | ((uint32_t)w << 16);
+      ct.wdiv[lane] = (65536u + (uint32_t)w - 1u) / (uint32_t)w;
     }
+    int total;
+    ct.first[lane] = warp_exclusive_scan(ntest, total);
+    ct.hm[lane] = 0u;
+    __syncwarp();
+    // the chunk's pixel tests, spread evenly over the lanes
+    for (int k = lane; k < total; k += 32) {
+      const int e = item_owner(ct.first, k);
+      const uint32_t r = (uint32_t)(k - ct.first[e]);
+      const uint32_t g = ct.geom[e];
+      const uint32_t dy = (r * ct.wdiv[e]) >> 16;
+      const uint32_t dx = r - dy * (g >> 16);
+      const int bx = (int)(g & 0xffu) + (int)dx, by = (int)((g >> 8) & 0xffu) + (int)dy;
+      const float4 a = ct.rec0[e];
+      if (ray_disc_positive(a.x, a.y, a.z, a.w, ray_coord(wr.x0 + bx, S.width, S.kappa),
+                            ray_coord(wr.y0 + by, S.height, S.kappa)))
+        atomicOr(&ct.hm[e], 1u << (by * 8 + bx));
+    }
+    __syncwarp();
+    const uint32_t hm = ct.hm[lane];
     const uint32_t bal = __ballot_sync(0xffffffffu, hm != 0u);
     if (hm) out[n + __popc(bal & lane_lt_mask())] = make_uint2(id, hm);
     n += __popc(bal);
     id = id_n;
     b = b_n;
+    __syncwarp();   // the chunk's shared data is rewritten next
   }
   if (lane == 0) v.unit_count[item * kBlocksPerTile + it.block] = n;
 }

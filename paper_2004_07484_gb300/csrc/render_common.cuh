@@ -148,6 +148,32 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x) {
   return x;
 }
 
+// Exclusive prefix sum over the warp's lanes; total receives the sum.
+__device__ __forceinline__ int warp_exclusive_scan(int x, int& total) {
+  const int lane = threadIdx.x & 31;
+  int inc = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += y;
+  }
+  total = __shfl_sync(0xffffffffu, inc, 31);
+  return inc - x;
+}
+
+// The lane owning item k of a warp-wide enumeration, given every lane's
+// first item number (ascending): the last lane whose items start at or
+// before k.  A lane without items shares its first number with the next
+// lane, so the last one is the owner.
+__device__ __forceinline__ int item_owner(const int* first, int k) {
+  int l = 0, r = 31;
+  while (l < r) {
+    const int mid = (l + r + 1) >> 1;
+    if (first[mid] <= k) l = mid; else r = mid - 1;
+  }
+  return l;
+}
+
 // ----------------------------------------------------------------------------
 // Asynchronous staging of a work unit's block list.  A warp streams the list
 // (entries: sphere index, hit mask over the block's 32 pixels), 32 entries
