@@ -304,16 +304,20 @@ def main():
         np.random.default_rng(7 + rank).standard_normal((sc.height, sc.width, sc.n_channels)).astype(np.float32))).to(dev)
     stream = torch.cuda.current_stream(dev)
 
+    # scheduling (segment length, kernel form) and pair capacity chosen by the
+    # library's autotuner on this workload, as a batch of one
+    from paper_2004_07484_gb300 import autotune
+    base = RenderSettings(sc.width, sc.height, sc.n_channels, sc.n_track, sc.gamma, sc.eps, sc.znear, sc.zfar,
+                          store_hits=True)
+    inputs = [(t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"])]
+    tuned = autotune.tune([base], inputs, [G])
+    pairs_needed = autotune.pairs_per_scene([base], inputs)[0]
+    capacity = tuned.capacities[0]
+
     def settings(store: bool):
         return RenderSettings(sc.width, sc.height, sc.n_channels, sc.n_track, sc.gamma, sc.eps,
-                              sc.znear, sc.zfar, store_hits=store)
-
-    # size the pair list once (synchronising check), then run without checks
-    fr, _, _ = forward_frame(settings(True), t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"],
-                             4 * sc.n_spheres, check_overflow=True)
-    pairs_needed = _lib.read_status(fr.ws.data_ptr(), fr.ws_bytes, stream.cuda_stream)[1]
-    capacity = int(pairs_needed * 1.25) + 4096   # the Renderer's growth policy after an overflow
-    del fr
+                              sc.znear, sc.zfar, store_hits=store, segment=tuned.segment,
+                              persistent=tuned.persistent)
 
     # counters for the algorithmic work of the render kernels
     H, W, C = sc.height, sc.width, sc.n_channels
@@ -504,7 +508,10 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": (launches_store * args.steps + launches_rec * len(ms_rec)) if not args.recompute
             else (launches_rec * args.steps + launches_store * len(ms_rec)),
-            "wall_s_timed": t_wall, "batched": batched}
+            "wall_s_timed": t_wall, "batched": batched,
+            "autotune": {"segment": tuned.segment, "persistent": tuned.persistent,
+                         "candidates_ms": {f"{a}/{'persistent' if b else 'per-unit'}": v
+                                           for (a, b), v in tuned.ms.items()}}}
     print(json.dumps(line))
     if world > 1:
         dist.barrier()

@@ -15,7 +15,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t hdr, scenes, rec0, rec1, rec2, key0, key1, val0, val1, hist, block_sums, pkey0, pkey1, pval0,
-      pval1, radix_tot, ranges, item_begin, item_tile, item_order, unit_list, unit_count, unit_tests, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
+      pval1, radix_tot, ranges, item_begin, item_desc, item_order, unit_list, unit_count, unit_tests, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
       gacc, fin_part, red_part, total;
   int64_t n_spheres, n_tiles, n_pixels, capacity, max_items;
   int32_t sort_blocks, fin_blocks, tile_bits, segment, part_fields;
@@ -98,7 +98,7 @@ Layout make_layout(const pulsar_params* ps, int n) {
   L.pval1 = take(4 * (size_t)cap);
   L.ranges = take(8 * (size_t)NT);
   L.item_begin = take(4 * (size_t)(NT + 1));
-  L.item_tile = take(4 * (size_t)L.max_items);
+  L.item_desc = take(sizeof(ItemDesc) * (size_t)L.max_items);
   L.item_order = take(4 * (size_t)L.max_items);
   // block lists: per pixel block, one slot per pair of capacity; per work unit a count
   L.unit_list = take(8 * 8 * (size_t)cap);
@@ -154,7 +154,7 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.pval[1] = reinterpret_cast<uint32_t*>(b + L.pval1);
   v.ranges = reinterpret_cast<int2*>(b + L.ranges);
   v.item_begin = reinterpret_cast<int32_t*>(b + L.item_begin);
-  v.item_tile = reinterpret_cast<int32_t*>(b + L.item_tile);
+  v.item_desc = reinterpret_cast<ItemDesc*>(b + L.item_desc);
   v.item_order = reinterpret_cast<int32_t*>(b + L.item_order);
   v.unit_list = reinterpret_cast<uint2*>(b + L.unit_list);
   v.unit_count = reinterpret_cast<int32_t*>(b + L.unit_count);
@@ -298,6 +298,7 @@ pulsar_status fwd_n(int n, const pulsar_params* params, const pulsar_scene* scen
   cudaError_t e = launch_setup(v, d, -n, s);
   if (e == cudaSuccess && tests) e = launch_count_tests(v, s);
   if (e == cudaSuccess) e = launch_render_fwd(v, s);
+  if (e == cudaSuccess) e = launch_background(v, false, 0u, s);
   return cuda_status(e);
 }
 
@@ -341,6 +342,7 @@ pulsar_status bwd_n(int n, const pulsar_params* params, const pulsar_scene* scen
   if (e == cudaSuccess && geo_or_values && !(params[0].flags & PULSAR_FLAG_STORE_HITS))
     e = launch_track_pass(v, s);
   if (e == cudaSuccess) e = launch_render_bwd(v, grad_mask, s);
+  if (e == cudaSuccess && (grad_mask & PULSAR_GRAD_BG)) e = launch_background(v, true, grad_mask, s);
   if (e == cudaSuccess) e = launch_finalize(v, grad_mask, s);
   return cuda_status(e);
 }

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) block_lists_kernel(const WsView v, const 
   ChunkTests& ct = tests_all[block];
   ItemCtx it;
   if (!item_ctx_direct(v, item, block, it)) return;
-  const SceneDev& S = v.scenes[scene_of_tile(v.scenes, v.n_scenes, it.tile)];
+  const SceneDev& S = v.scenes[it.scene];
   const PixelCtx pc = pixel_ctx(S, it.tile, it.block);
   const WarpRect wr = warp_rect(pc, it.block);
   uint2* out = v.unit_list + (size_t)it.block * v.capacity + it.b0;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) count_tests_kernel(const WsView v, const 
   const int lane = threadIdx.x & 31;
   ItemCtx it;
   if (!item_ctx_direct(v, item, threadIdx.x >> 5, it)) return;
-  const SceneDev& S = v.scenes[scene_of_tile(v.scenes, v.n_scenes, it.tile)];
+  const SceneDev& S = v.scenes[it.scene];
   const WarpRect wr = warp_rect(pixel_ctx(S, it.tile, it.block), it.block);
   int tests = 0;
   for (int base = it.b0; base < it.b1; base += 32) {

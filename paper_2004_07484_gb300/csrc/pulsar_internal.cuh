@@ -90,6 +90,17 @@ struct WsHeader {
   int32_t pad_[7];
 };
 
+// One work item of the render passes: a segment [b0, b1) of a tile's list.
+struct __align__(16) ItemDesc {
+  int32_t tile;    // global tile index
+  int32_t b0, b1;  // list range
+  int32_t seg;     // segment index within the tile
+  int32_t nseg;    // segments of the tile
+  int32_t first;   // first work item of the tile
+  int32_t scene;   // scene owning the tile
+  int32_t pad_;
+};
+
 // Raw pointers into one workspace, passed to kernels by value.
 struct WsView {
   WsHeader* hdr;
@@ -120,7 +131,7 @@ struct WsView {
   uint32_t* pval[2];         // pair sphere ids (ping-pong)
   int2* ranges;              // per tile [begin, end)
   int32_t* item_begin;       // per tile (+1): first work item
-  int32_t* item_tile;        // per work item: its tile
+  ItemDesc* item_desc;       // per work item
   int32_t* item_order;       // work items by decreasing segment length (launch order)
   uint2* unit_list;          // block lists: [pixel block][capacity] (sphere, hit mask)
   int32_t* unit_count;       // per work unit (item x 8 + block): block-list length
@@ -398,6 +409,7 @@ cudaError_t launch_project(const WsView& v, cudaStream_t st);
 cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st);
 cudaError_t launch_block_lists(const WsView& v, cudaStream_t st);
 cudaError_t launch_count_tests(const WsView& v, cudaStream_t st);
+cudaError_t launch_background(const WsView& v, bool backward, uint32_t grad_mask, cudaStream_t st);
 cudaError_t launch_render_fwd(const WsView& v, cudaStream_t st);
 cudaError_t launch_track_pass(const WsView& v, cudaStream_t st);
 cudaError_t launch_render_bwd(const WsView& v, uint32_t grad_mask, cudaStream_t st);

@@ -59,8 +59,7 @@ template <int CMAX>
 __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, StageBuf<CMAX>& sb) {
   ItemCtx it;
   if (!item_ctx(v, w, it)) return;
-  const int si = scene_of_tile(v.scenes, v.n_scenes, it.tile);
-  const SceneDev& S = v.scenes[si];
+  const SceneDev& S = v.scenes[it.scene];
   const PixelCtx pc = pixel_ctx(S, it.tile, it.block);
   const int C = S.n_channels;
   const float gamma = S.gamma, zfar = S.zfar, znear = S.znear;
@@ -84,21 +83,36 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
 #pragma unroll
   for (int c = 0; c < CMAX; ++c) G[c] = 0.0f;
   if (pc.inside) {
+    const float4 aux = v.pix_aux[gpix];
+    logD = S.log_norm_in[pix];
     const float* g = S.grad_image + pix * C;
     const float* fr = v.fres + gpix * C;
-    const float4 aux = v.pix_aux[gpix];
+    // 16-byte loads where the layout allows
+    const bool vec = (C & 3) == 0 && ((reinterpret_cast<uintptr_t>(g) | reinterpret_cast<uintptr_t>(fr)) & 15) == 0;
+    if (vec) {
+#pragma unroll
+      for (int c = 0; c < CMAX; c += 4)
+        if (c < C) {
+          const float4 x = __ldg(reinterpret_cast<const float4*>(g + c));
+          const float4 y = __ldg(reinterpret_cast<const float4*>(fr + c));
+          G[c] = x.x; G[c + 1] = x.y; G[c + 2] = x.z; G[c + 3] = x.w;
+          GFres = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, GFres))));
+        }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CMAX; ++c)
+        if (c < C) {
+          G[c] = __ldg(g + c);
+          GFres = fmaf(G[c], __ldg(fr + c), GFres);
+        }
+    }
     thr_t = aux.x;
     thr_i = __float_as_int(aux.y);
     dom = __float_as_int(aux.z);
     const float* fref = dom < 0 ? S.bg : S.feat + (int64_t)(dom - S.sphere_begin) * C;
 #pragma unroll
     for (int c = 0; c < CMAX; ++c)
-      if (c < C) {
-        G[c] = g[c];
-        GFres = fmaf(G[c], fr[c], GFres);
-        Gref = fmaf(G[c], fref[c], Gref);
-      }
-    logD = S.log_norm_in[pix];
+      if (c < C) Gref = fmaf(G[c], __ldg(fref + c), Gref);
   }
 
   // background gradient: sum over the block of w_B G (first segment only)

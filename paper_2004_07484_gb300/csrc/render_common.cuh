@@ -37,23 +37,24 @@ struct ItemCtx {
   int seg, nseg;     // segment index and segment count of the tile
   int first;         // first work item of the tile
   int b0, b1;        // list range [b0, b1) of this segment
+  int scene;         // scene owning the tile
 };
 
 // Work item `item` itself and its pixel block `block` (0..7).  Returns false
 // for items beyond the number of work items.
 __device__ __forceinline__ bool item_ctx_direct(const WsView& v, int item, int block, ItemCtx& c) {
   if (item >= v.hdr->n_items) return false;
+  const ItemDesc d = v.item_desc[item];
   c.item = item;
   c.block = block;
   c.slot = item * kBlocksPerTile + block;
-  c.tile = v.item_tile[item];
-  c.first = v.item_begin[c.tile];
-  c.nseg = v.item_begin[c.tile + 1] - c.first;
-  c.seg = item - c.first;
-  const int2 rg = v.ranges[c.tile];
-  c.b0 = rg.x + c.seg * v.segment;
-  c.b1 = min(rg.x + (c.seg + 1) * v.segment, rg.y);
-  if (c.b1 < c.b0) c.b1 = c.b0;
+  c.tile = d.tile;
+  c.first = d.first;
+  c.nseg = d.nseg;
+  c.seg = d.seg;
+  c.b0 = d.b0;
+  c.b1 = d.b1;
+  c.scene = d.scene;
   return true;
 }
 
@@ -256,7 +257,7 @@ struct UnitStream {
   __device__ __forceinline__ void start(StageBuf<CMAX>& sb, const WsView& v, const SceneDev& S,
                                         const ItemCtx& it, bool need_values) {
     const int lane = threadIdx.x & 31;
-    if (need_values)
+    if (need_values && S.n_channels < CMAX)
       for (int e = lane; e < 2 * 32 * CMAX; e += 32) (&sb.feat[0][0])[e] = 0.0f;
     __syncwarp();
     src = v.unit_list + (size_t)it.block * v.capacity + it.b0;

@@ -282,11 +282,12 @@ __global__ void __launch_bounds__(kThreads) tile_ranges(WsView v, int buf) {
   }
 }
 
-// Work items of the render passes: every tile's list is cut into segments of
-// at most v.segment entries (an empty tile is one item, so its pixels are
-// still written).  Writes item_begin (n_tiles + 1), item_tile, the item count
-// and item_order, the items by decreasing length (a counting sort over
-// kOrderBuckets length classes; the order within a class is arbitrary).
+// Work items of the render passes: every non-empty tile's list is cut into
+// segments of at most v.segment entries (the pixels of empty tiles are
+// written by the background pass).  Writes item_begin (n_tiles + 1), one
+// descriptor per item, the item count and item_order, the items by
+// decreasing length (a counting sort over kOrderBuckets length classes; the
+// order within a class is arbitrary).
 constexpr int kOrderBuckets = 64;
 
 __global__ void __launch_bounds__(1024) make_items(WsView v) {
@@ -296,21 +297,32 @@ __global__ void __launch_bounds__(1024) make_items(WsView v) {
   const int64_t per = (nt + 1023) / 1024;
   const int64_t t0 = (int64_t)threadIdx.x * per;
   const int64_t t1 = t0 + per < nt ? t0 + per : nt;
+  const int seg_len = v.segment;
   uint32_t s = 0;
   for (int64_t t = t0; t < t1; ++t) {
     const int2 rg = v.ranges[t];
-    const int len = rg.y - rg.x;
-    s += len > 0 ? (uint32_t)((len + v.segment - 1) / v.segment) : 1u;
+    s += (uint32_t)((rg.y - rg.x + seg_len - 1) / seg_len);
   }
   uint32_t tot;
   uint32_t base = block_exclusive_scan<1024>(s, warp_tot, tot);
   for (int64_t t = t0; t < t1; ++t) {
     const int2 rg = v.ranges[t];
-    const int len = rg.y - rg.x;
-    const uint32_t ns = len > 0 ? (uint32_t)((len + v.segment - 1) / v.segment) : 1u;
+    const int ns = (rg.y - rg.x + seg_len - 1) / seg_len;
     v.item_begin[t] = (int32_t)base;
-    for (uint32_t k = 0; k < ns; ++k) v.item_tile[base + k] = (int32_t)t;
-    base += ns;
+    const int scene = ns > 0 ? scene_of_tile(v.scenes, v.n_scenes, t) : 0;
+    for (int k = 0; k < ns; ++k) {
+      ItemDesc d;
+      d.tile = (int32_t)t;
+      d.b0 = rg.x + k * seg_len;
+      d.b1 = min(rg.x + (k + 1) * seg_len, rg.y);
+      d.seg = k;
+      d.nseg = ns;
+      d.first = (int32_t)base;
+      d.scene = scene;
+      d.pad_ = 0;
+      v.item_desc[base + k] = d;
+    }
+    base += (uint32_t)ns;
   }
   if (threadIdx.x == 0) {
     v.item_begin[nt] = (int32_t)tot;
@@ -318,14 +330,11 @@ __global__ void __launch_bounds__(1024) make_items(WsView v) {
   }
   if (threadIdx.x < kOrderBuckets) bucket[threadIdx.x] = 0u;
   __syncthreads();
-  // length class of an item: 0 for a full segment ... kOrderBuckets - 1 for an empty one
+  // length class of an item: 0 for a full segment ... kOrderBuckets - 1 for one entry
   auto cls = [&](uint32_t i) {
-    const int32_t t = v.item_tile[i];
-    const int2 rg = v.ranges[t];
-    const int seg = (int)i - v.item_begin[t];
-    const int rest = rg.y - rg.x - seg * v.segment;
-    const int len = rest < v.segment ? (rest > 0 ? rest : 0) : v.segment;
-    return (int)(((int64_t)(v.segment - len) * (kOrderBuckets - 1)) / v.segment);
+    const ItemDesc& d = v.item_desc[i];
+    const int len = d.b1 - d.b0;
+    return (int)(((int64_t)(seg_len - len) * (kOrderBuckets - 1)) / seg_len);
   };
   for (uint32_t i = threadIdx.x; i < tot; i += 1024) atomicAdd(&bucket[cls(i)], 1u);
   __syncthreads();
