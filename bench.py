@@ -51,6 +51,23 @@ def fwd_kernel_digest() -> str:
     return h.hexdigest()
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, renders_per_rank: int, max_ms: float) -> float:
+    """Whole-job renders/s: every rank renders renders_per_rank scenes, and the
+    job takes as long as its slowest rank (max_ms)."""
+    return world * renders_per_rank / (max_ms / 1e3)
+
+
 def rank_info():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -176,8 +193,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)",
-            "config": {"workload": WORKLOAD, "model": "pulsar sphere renderer", "global_batch": 1,
-                       "seq_len": None, "parallelism": "none (host cores)"},
+            "config": {"workload": WORKLOAD, "renders_per_step": 1,
+                       "parallelism": "replicas x1 (independent renders)", "hit_lists": "store"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                              "sample": f"{n_side}x{n_side}-pixel window per step, fwd + bwd, FP64 brute force"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -376,13 +393,9 @@ def main():
     assert st == _lib.OK, f"pair list overflow during timing (status {st})"
     if world > 1:
         dist.barrier()
-    total_ms = sum(ms_store)
-    if world > 1:
-        x = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        total_ms = float(x.item())
+    total_ms = max_over_ranks(sum(ms_store), world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
+    value = job_throughput(world, args.steps, total_ms)
 
     # per-kernel timing of the dominant kernels (events on the launch stream)
     def kernel_ms(store: bool, reps: int = 5):
@@ -449,11 +462,7 @@ def main():
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / k_e2e
-    if world > 1:
-        x = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        e2e_ms = float(x.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / k_e2e, world, dev)
 
     if rank != 0:
         if world > 1:
@@ -503,7 +512,7 @@ def main():
                        "l2": "flushed between steps (256 MB write, untimed)",
                        "hit_lists": "recompute" if args.recompute else "store"},
             "recompute_ms_per_step" if not args.recompute else "store_ms_per_step": statistics.mean(ms_rec),
-            "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_throughput(world, 1, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": (launches_store * args.steps + launches_rec * len(ms_rec)) if not args.recompute

@@ -95,8 +95,7 @@ template <int KMAX, int CMAX, bool BLEND>
 __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<CMAX>& sb) {
   ItemCtx it;
   if (!item_ctx(v, w, it)) return;
-  const int si = scene_of_tile(v.scenes, v.n_scenes, it.tile);
-  const SceneDev& S = v.scenes[si];
+  const SceneDev& S = v.scenes[it.scene];
   const PixelCtx pc = pixel_ctx(S, it.tile, it.block);
   const WarpRect wr = warp_rect(pc, it.block);
   const int C = S.n_channels;
@@ -273,20 +272,37 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
     if (lane == 0) v.tile_done[it.tile * kBlocksPerTile + it.block] = 0;   // ready for the next launch
   }
 
-  if (!pc.inside) return;
   const int64_t pix = (int64_t)pc.py * S.width + pc.px;
   const int64_t gpix = S.pixel_begin + pix;
   if (BLEND) {
+    // F and F - f_ref of the block's pixels, staged in shared memory (the
+    // staging buffers are free now), then written row by row: each pixel row
+    // of the block is one contiguous run of the row-major outputs
+    float* st_img = &sb.feat[0][0];
+    float* st_res = &sb.feat[1][0];
     const float inv = 1.0f / bs.den;
-    float* out = S.image + pix * C;
-    float* fr = v.fres + gpix * C;
 #pragma unroll
     for (int c = 0; c < CMAX; ++c)
       if (c < C) {
         const float r = bs.res[c] * inv;
-        out[c] = bs.fref[32 * c] + r;
-        fr[c] = r;
+        st_img[lane * CMAX + c] = bs.fref[32 * c] + r;
+        st_res[lane * CMAX + c] = r;
       }
+    __syncwarp();
+    const int bx0 = pc.tile_x0 + (it.block & 1) * 8, by0 = pc.tile_y0 + (it.block >> 1) * 4;
+    const int nx = min(8, S.width - bx0);
+    for (int r = 0; r < 4 && by0 + r < S.height; ++r) {
+      const int64_t p0 = (int64_t)(by0 + r) * S.width + bx0;
+      float* img = S.image + p0 * C;
+      float* fr = v.fres + (S.pixel_begin + p0) * C;
+      for (int f = lane; f < nx * C; f += 32) {
+        const int pxl = f / C;
+        const int src = (r * 8 + pxl) * CMAX + (f - pxl * C);
+        img[f] = st_img[src];
+        fr[f] = st_res[src];
+      }
+    }
+    if (!pc.inside) return;
     S.log_norm[pix] = bs.m + __logf(bs.den);
     if (S.n_hits) S.n_hits[pix] = nhit;
     if (S.n_tests) S.n_tests[pix] = ntest;
@@ -302,6 +318,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
     v.pix_aux[gpix] = make_float4(key_depth(q[KMAX - 1]), __int_as_float(key_index(q[KMAX - 1])),
                                   __int_as_float(bs.dom), 0.0f);
   } else {
+    if (!pc.inside) return;
     reinterpret_cast<float2*>(v.pix_aux)[2 * gpix] =
         make_float2(key_depth(q[KMAX - 1]), __int_as_float(key_index(q[KMAX - 1])));
   }
