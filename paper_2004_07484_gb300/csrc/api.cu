@@ -226,6 +226,13 @@ pulsar_status validate_batch(int n, const pulsar_params* ps) {
     cap += ps[s].list_capacity;
   }
   if (M > (int64_t)INT32_MAX - kSortTile || cap > (int64_t)INT32_MAX - kSortTile) return PULSAR_ERR_UNSUPPORTED;
+  int64_t nt = 0;
+  for (int s = 0; s < n; ++s) {
+    int tx, ty;
+    tiles_of(ps[s], tx, ty);
+    nt += (int64_t)tx * ty;
+  }
+  if (nt > ((int64_t)1 << kTileKeyBits)) return PULSAR_ERR_UNSUPPORTED;   // tile index bits of a pair key
   return PULSAR_OK;
 }
 

@@ -5,12 +5,13 @@
 // 8 x 4 pixel blocks) a warp walks the segment once and keeps, in list
 // order, the spheres the float32 hit predicate reports for at least one
 // pixel of the block, each with its 32-bit hit mask (bit 8 y + x for block
-// pixel (x, y)).  Per chunk of 32 list entries, each lane intersects one
-// sphere's pixel rectangle with the block; the pixel tests of all overlaps
-// (a few per sphere, very unevenly) are then numbered across the warp and
-// spread evenly over the lanes, which OR their results into the entries'
-// masks in shared memory.  The next chunk's entries and rectangles load
-// while the current chunk is tested.  The forward pass, the track pass and the backward pass then
+// pixel (x, y)).  The warp reads the segment's pair keys, whose high bits
+// say which of the tile's blocks each sphere's rectangle meets, and gathers
+// the entries meeting its block into batches of 32; per batch each lane
+// intersects one sphere's rectangle with the block, and the pixel tests of
+// all overlaps (a few per sphere, very unevenly) are numbered across the warp
+// and spread evenly over the lanes, which OR their results into the entries'
+// masks in shared memory.  The forward pass, the track pass and the backward pass then
 // stream only these entries and read each pixel's hits from the masks, so
 // none of them repeats the rectangle or ray-disc tests.
 #include "render_common.cuh"
@@ -19,9 +20,10 @@ namespace pulsar {
 
 namespace {
 
-// Per warp: the current chunk's overlapping entries, for the lanes that test
-// their pixels.
-struct ChunkTests {
+// Per warp: list positions of entries whose rectangle meets the warp's block,
+// gathered into full batches, and the current batch's test bookkeeping.
+struct BlockListWarp {
+  int32_t pos[64];     // gathered list positions, in list order
   float4 rec0[32];     // draw record (decision centre, R^2)
   int first[32];       // first test number of each entry
   uint32_t geom[32];   // overlap with the block: x0 | y0 << 8 | width << 16
@@ -29,72 +31,87 @@ struct ChunkTests {
   uint32_t hm[32];     // hit masks being built
 };
 
-__global__ void __launch_bounds__(256) block_lists_kernel(const WsView v, const uint32_t* __restrict__ list) {
-  __shared__ ChunkTests tests_all[8];
+// Tests the pixels of the first cnt gathered entries against the block and
+// appends the entries with hits, in order, to out (n entries so far).
+__device__ __forceinline__ void block_batch(BlockListWarp& W, int cnt, const WsView& v, const SceneDev& S,
+                                            const WarpRect& wr, const uint32_t* __restrict__ list,
+                                            uint2* out, int& n) {
+  const int lane = threadIdx.x & 31;
+  uint32_t id = 0u;
+  int ntest = 0;
+  if (lane < cnt) {
+    id = __ldg(list + W.pos[lane]);
+    const float4 b = __ldg(v.rec1 + id);
+    const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
+    const int x0 = max((int)(bx & 0xffffu), wr.x0), x1 = min((int)(bx >> 16), wr.x1);
+    const int y0 = max((int)(by & 0xffffu), wr.y0), y1 = min((int)(by >> 16), wr.y1);
+    const int w = max(x1 - x0 + 1, 1);
+    ntest = (x1 >= x0 && y1 >= y0) ? w * (y1 - y0 + 1) : 0;   // the pair key says they meet
+    W.rec0[lane] = __ldg(v.rec0 + id);
+    W.geom[lane] = (uint32_t)(x0 - wr.x0) | ((uint32_t)(y0 - wr.y0) << 8) | ((uint32_t)w << 16);
+    W.wdiv[lane] = (65536u + (uint32_t)w - 1u) / (uint32_t)w;
+  }
+  int total;
+  W.first[lane] = warp_exclusive_scan(ntest, total);
+  W.hm[lane] = 0u;
+  __syncwarp();
+  // the batch's pixel tests, spread evenly over the lanes
+  for (int k = lane; k < total; k += 32) {
+    const int e = item_owner(W.first, k);
+    const uint32_t r = (uint32_t)(k - W.first[e]);
+    const uint32_t g = W.geom[e];
+    const uint32_t dy = (r * W.wdiv[e]) >> 16;
+    const uint32_t dx = r - dy * (g >> 16);
+    const int px = (int)(g & 0xffu) + (int)dx, py = (int)((g >> 8) & 0xffu) + (int)dy;
+    const float4 a = W.rec0[e];
+    if (ray_disc_positive(a.x, a.y, a.z, a.w, ray_coord(wr.x0 + px, S.width, S.kappa),
+                          ray_coord(wr.y0 + py, S.height, S.kappa)))
+      atomicOr(&W.hm[e], 1u << (py * 8 + px));
+  }
+  __syncwarp();
+  const uint32_t hm = W.hm[lane];
+  const uint32_t bal = __ballot_sync(0xffffffffu, hm != 0u);
+  if (hm) out[n + __popc(bal & lane_lt_mask())] = make_uint2(id, hm);
+  n += __popc(bal);
+  __syncwarp();   // the batch's shared data is rewritten next
+}
+
+__global__ void __launch_bounds__(256) block_lists_kernel(const WsView v, const uint32_t* __restrict__ keys,
+                                                          const uint32_t* __restrict__ list) {
+  __shared__ BlockListWarp warps[8];
   const int item = blockIdx.x;
   const int block = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  ChunkTests& ct = tests_all[block];
+  BlockListWarp& W = warps[block];
   ItemCtx it;
   if (!item_ctx_direct(v, item, block, it)) return;
   const SceneDev& S = v.scenes[it.scene];
   const PixelCtx pc = pixel_ctx(S, it.tile, it.block);
   const WarpRect wr = warp_rect(pc, it.block);
   uint2* out = v.unit_list + (size_t)it.block * v.capacity + it.b0;
-  int n = 0;
-  // the current chunk's entry and rectangle; the next chunk's are loaded
-  // while this one is tested
-  uint32_t id = 0u;
-  float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (it.b0 + lane < it.b1) {
-    id = __ldg(list + it.b0 + lane);
-    b = __ldg(v.rec1 + id);
-  }
+  const uint32_t mine = 1u << (kTileKeyBits + block);
+  int n = 0, pending = 0;
+  uint32_t key_next = it.b0 + lane < it.b1 ? __ldg(keys + it.b0 + lane) : 0u;
   for (int base = it.b0; base < it.b1; base += 32) {
-    const int i = base + lane;
-    uint32_t id_n = 0u;
-    float4 b_n = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i + 32 < it.b1) {
-      id_n = __ldg(list + i + 32);
-      b_n = __ldg(v.rec1 + id_n);
+    const uint32_t key = key_next;
+    key_next = base + 32 + lane < it.b1 ? __ldg(keys + base + 32 + lane) : 0u;
+    // gather the entries whose rectangle meets this block (from the pair key)
+    const bool ok = base + lane < it.b1 && (key & mine) != 0u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+    if (ok) W.pos[pending + __popc(bal & lane_lt_mask())] = base + lane;
+    pending += __popc(bal);
+    if (pending >= 32) {
+      __syncwarp();
+      block_batch(W, 32, v, S, wr, list, out, n);
+      const int rest = pending - 32;
+      if (lane < rest) W.pos[lane] = W.pos[32 + lane];
+      pending = rest;
+      __syncwarp();
     }
-    // this entry's overlap with the block: its pixel tests
-    int ntest = 0;
-    if (i < it.b1 && rect_overlaps(b, wr)) {
-      const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
-      const int x0 = max((int)(bx & 0xffffu), wr.x0), x1 = min((int)(bx >> 16), wr.x1);
-      const int y0 = max((int)(by & 0xffffu), wr.y0), y1 = min((int)(by >> 16), wr.y1);
-      const int w = x1 - x0 + 1;
-      ntest = w * (y1 - y0 + 1);
-      ct.rec0[lane] = __ldg(v.rec0 + id);
-      ct.geom[lane] = (uint32_t)(x0 - wr.x0) | ((uint32_t)(y0 - wr.y0) << 8) | ((uint32_t)w << 16);
-      ct.wdiv[lane] = (65536u + (uint32_t)w - 1u) / (uint32_t)w;
-    }
-    int total;
-    ct.first[lane] = warp_exclusive_scan(ntest, total);
-    ct.hm[lane] = 0u;
+  }
+  if (pending > 0) {
     __syncwarp();
-    // the chunk's pixel tests, spread evenly over the lanes
-    for (int k = lane; k < total; k += 32) {
-      const int e = item_owner(ct.first, k);
-      const uint32_t r = (uint32_t)(k - ct.first[e]);
-      const uint32_t g = ct.geom[e];
-      const uint32_t dy = (r * ct.wdiv[e]) >> 16;
-      const uint32_t dx = r - dy * (g >> 16);
-      const int bx = (int)(g & 0xffu) + (int)dx, by = (int)((g >> 8) & 0xffu) + (int)dy;
-      const float4 a = ct.rec0[e];
-      if (ray_disc_positive(a.x, a.y, a.z, a.w, ray_coord(wr.x0 + bx, S.width, S.kappa),
-                            ray_coord(wr.y0 + by, S.height, S.kappa)))
-        atomicOr(&ct.hm[e], 1u << (by * 8 + bx));
-    }
-    __syncwarp();
-    const uint32_t hm = ct.hm[lane];
-    const uint32_t bal = __ballot_sync(0xffffffffu, hm != 0u);
-    if (hm) out[n + __popc(bal & lane_lt_mask())] = make_uint2(id, hm);
-    n += __popc(bal);
-    id = id_n;
-    b = b_n;
-    __syncwarp();   // the chunk's shared data is rewritten next
+    block_batch(W, pending, v, S, wr, list, out, n);
   }
   if (lane == 0) v.unit_count[item * kBlocksPerTile + it.block] = n;
 }
@@ -133,7 +150,7 @@ __global__ void __launch_bounds__(256) count_tests_kernel(const WsView v, const 
 
 cudaError_t launch_block_lists(const WsView& v, cudaStream_t st) {
   if (v.max_items == 0) return cudaSuccess;
-  block_lists_kernel<<<(unsigned)v.max_items, 256, 0, st>>>(v, v.pval[v.pair_buf]);
+  block_lists_kernel<<<(unsigned)v.max_items, 256, 0, st>>>(v, v.pkey[v.pair_buf], v.pval[v.pair_buf]);
   return cudaGetLastError();
 }
 

@@ -28,6 +28,8 @@ constexpr int kMaxScenes = 64;
 constexpr int kFinalizeThreads = 256;
 constexpr int kCamPartials = 16;     // floats per finalize-block camera partial (13 used)
 constexpr int kDefaultSegment = 1024;  // list entries one CTA processes per work item
+constexpr int kTileKeyBits = 24;        // pair keys: tile index bits (the block set above them)
+constexpr uint32_t kTileKeyMask = (1u << kTileKeyBits) - 1u;
 
 // Per-scene description in the workspace.  The host fills the inputs; the
 // setup kernel derives the camera rows and pixel pitch.

@@ -29,6 +29,10 @@ namespace pulsar {
 
 namespace {
 
+// Staging depth of the backward pass (batches staged ahead + 1); staging two
+// batches ahead measured slower than one.
+constexpr int kBwdBuffers = 2;
+
 // Adds one tracked hit's gradients to its sphere (vector atomics where the
 // layout allows).
 template <int CMAX>
@@ -56,7 +60,7 @@ __device__ __forceinline__ void add_hit_grads(int id_global, int64_t id_local, f
 // Back-propagates through work unit w (a pixel block of one work item) with
 // one warp.
 template <int CMAX>
-__device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, StageBuf<CMAX>& sb) {
+__device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, StageBuf<CMAX, kBwdBuffers>& sb) {
   ItemCtx it;
   if (!item_ctx(v, w, it)) return;
   const SceneDev& S = v.scenes[it.scene];
@@ -133,7 +137,7 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
   const float kstop = next_up(thr_t);
   bool done = !pc.inside;
   float gk_sum = 0.0f;
-  UnitStream<CMAX> ws;
+  UnitStream<CMAX, kBwdBuffers> ws;
   ws.start(sb, v, S, it, true);
   for (; ws.base < ws.n; ws.advance()) {
     if (__all_sync(0xffffffffu, done)) break;
@@ -247,7 +251,7 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
 template <int CMAX>
 __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v, uint32_t mask) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StageBuf<CMAX>& sb = *reinterpret_cast<StageBuf<CMAX>*>(smem_raw);
+  StageBuf<CMAX, kBwdBuffers>& sb = *reinterpret_cast<StageBuf<CMAX, kBwdBuffers>*>(smem_raw);
   if (!v.persistent) {
     bwd_unit<CMAX>(v, mask, blockIdx.x, sb);
     return;
@@ -263,7 +267,7 @@ __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v, uint
 
 template <int CMAX>
 cudaError_t launch_bwd_t(const WsView& v, uint32_t mask, cudaStream_t st) {
-  const size_t smem = sizeof(StageBuf<CMAX>);
+  const size_t smem = sizeof(StageBuf<CMAX, kBwdBuffers>);
   auto kern = render_bwd_kernel<CMAX>;
   unsigned grid = (unsigned)v.max_items * kBlocksPerTile;
   if (v.persistent) {

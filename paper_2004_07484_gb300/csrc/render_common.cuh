@@ -185,14 +185,14 @@ __device__ __forceinline__ int item_owner(const int* first, int k) {
 // of the batch entries that hit its pixel.
 // ----------------------------------------------------------------------------
 
-template <int CMAX>
+template <int CMAX, int NB = 2>
 struct StageBuf {
-  float4 rec0[2][32];
-  float4 rec1[2][32];
-  float4 rec2[2][32];
-  float feat[2][32 * CMAX];
-  int32_t id[2][32];
-  uint32_t hm[2][32];
+  float4 rec0[NB][32];
+  float4 rec1[NB][32];
+  float4 rec2[NB][32];
+  float feat[NB][32 * CMAX];
+  int32_t id[NB][32];
+  uint32_t hm[NB][32];
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -210,13 +210,14 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <int CMAX>
+template <int CMAX, int NB = 2>
 struct UnitStream {
+  static_assert(NB >= 2, "at least double buffering");
   const uint2* __restrict__ src;   // the unit's block list
   int n;                           // its length
   int base;                        // first entry of the current batch
   int buf;                         // buffer holding the current batch
-  uint2 e_next;                    // this lane's entry of the next batch
+  uint2 e_next;                    // this lane's entry of the next batch to stage
 
   __device__ __forceinline__ uint2 load(int at) const {
     const int i = at + (int)(threadIdx.x & 31);
@@ -225,7 +226,7 @@ struct UnitStream {
 
   // One commit group: records (and, with need_values, value records and
   // features) of the batch at `at`, whose lane entries are e, into buffer `to`.
-  __device__ __forceinline__ void issue(StageBuf<CMAX>& sb, const WsView& v, const SceneDev& S, uint2 e,
+  __device__ __forceinline__ void issue(StageBuf<CMAX, NB>& sb, const WsView& v, const SceneDev& S, uint2 e,
                                         int at, int to, bool need_values) const {
     const int lane = threadIdx.x & 31;
     if (at + lane < n) {
@@ -253,33 +254,37 @@ struct UnitStream {
     cp_async_commit();
   }
 
-  // Starts the block list of `unit`.  Feature channels beyond C stay zero.
-  __device__ __forceinline__ void start(StageBuf<CMAX>& sb, const WsView& v, const SceneDev& S,
+  // Starts the block list of the unit: the first NB - 1 batches are staged
+  // ahead.  Feature channels beyond C stay zero.
+  __device__ __forceinline__ void start(StageBuf<CMAX, NB>& sb, const WsView& v, const SceneDev& S,
                                         const ItemCtx& it, bool need_values) {
     const int lane = threadIdx.x & 31;
     if (need_values && S.n_channels < CMAX)
-      for (int e = lane; e < 2 * 32 * CMAX; e += 32) (&sb.feat[0][0])[e] = 0.0f;
+      for (int e = lane; e < NB * 32 * CMAX; e += 32) (&sb.feat[0][0])[e] = 0.0f;
     __syncwarp();
     src = v.unit_list + (size_t)it.block * v.capacity + it.b0;
     n = v.unit_count[it.slot];
     base = 0;
     buf = 0;
-    issue(sb, v, S, load(0), 0, 0, need_values);
-    e_next = load(32);
+#pragma unroll
+    for (int k = 0; k < NB - 1; ++k) issue(sb, v, S, load(32 * k), 32 * k, k, need_values);
+    e_next = load(32 * (NB - 1));
   }
 
   __device__ __forceinline__ int count() const { return min(32, n - base); }
 
-  // Waits for the current batch's staging, starts the next batch's, and
-  // returns the entries of the current batch that hit this lane's pixel.
-  __device__ __forceinline__ uint32_t begin(StageBuf<CMAX>& sb, const WsView& v, const SceneDev& S,
+  // Waits for the current batch's staging, starts staging the batch NB - 1
+  // ahead, and returns the entries of the current batch that hit this lane's
+  // pixel.
+  __device__ __forceinline__ uint32_t begin(StageBuf<CMAX, NB>& sb, const WsView& v, const SceneDev& S,
                                             bool need_values) {
-    cp_async_wait<0>();
+    cp_async_wait<NB - 2>();
     __syncwarp();
     const int lane = threadIdx.x & 31;
     const uint32_t hits = transpose32(base + lane < n ? sb.hm[buf][lane] : 0u);
-    issue(sb, v, S, e_next, base + 32, buf ^ 1, need_values);
-    e_next = load(base + 64);
+    const int to = buf + NB - 1 < NB ? buf + NB - 1 : buf - 1;
+    issue(sb, v, S, e_next, base + 32 * (NB - 1), to, need_values);
+    e_next = load(base + 32 * NB);
     return hits;
   }
 
@@ -287,7 +292,7 @@ struct UnitStream {
   __device__ __forceinline__ void advance() {
     __syncwarp();
     base += 32;
-    buf ^= 1;
+    buf = buf + 1 < NB ? buf + 1 : 0;
   }
 
   // Waits for every copy still in flight (before the warp leaves).

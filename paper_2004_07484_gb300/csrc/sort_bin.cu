@@ -230,7 +230,11 @@ __global__ void __launch_bounds__(1024) count_scan(WsView v, int n_blocks) {
   }
 }
 
-// Emits the (tile, sphere) pairs of each depth-sorted sphere at its scanned offset.
+// Emits the (tile, sphere) pairs of each depth-sorted sphere at its scanned
+// offset.  A pair's key is the global tile index in its low kTileKeyBits bits
+// and, above them, the 8-bit set of the tile's 8 x 4 pixel blocks the
+// sphere's rectangle meets (bit 2 r + c for block column c, row r).  The sort
+// by tile reads only the low bits, so the block set rides along.
 __global__ void __launch_bounds__(kThreads) emit_pairs(WsView v) {
   __shared__ uint32_t warp_tot[33];
   const int n = (int)v.n_spheres;
@@ -262,12 +266,20 @@ __global__ void __launch_bounds__(kThreads) emit_pairs(WsView v) {
     int tx0 = (int)(bx & 0xffffu) / kTile, tx1 = (int)(bx >> 16) / kTile;
     int ty0 = (int)(by & 0xffffu) / kTile, ty1 = (int)(by >> 16) / kTile;
     uint32_t tb = (uint32_t)S.tile_begin;
-    for (int ty = ty0; ty <= ty1; ++ty)
+    const int x0 = (int)(bx & 0xffffu), x1 = (int)(bx >> 16);
+    const int y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
+    for (int ty = ty0; ty <= ty1; ++ty) {
+      // rows of 8 x 4 pixel blocks the rectangle meets in this tile row
+      const int r0 = (max(y0 - ty * kTile, 0)) >> 2, r1 = (min(y1 - ty * kTile, kTile - 1)) >> 2;
+      const uint32_t rows = ((1u << (2 * r1 + 2)) - (1u << (2 * r0))) / 3u;   // sum of 4^r, r0..r1
       for (int tx = tx0; tx <= tx1; ++tx) {
-        v.pkey[0][off] = tb + (uint32_t)(ty * S.tiles_x + tx);
+        const int c0 = (max(x0 - tx * kTile, 0)) >> 3, c1 = (min(x1 - tx * kTile, kTile - 1)) >> 3;
+        const uint32_t blocks = ((2u << c1) - (1u << c0)) * rows;   // bit 2 r + c: block (c, r)
+        v.pkey[0][off] = (tb + (uint32_t)(ty * S.tiles_x + tx)) | (blocks << kTileKeyBits);
         v.pval[0][off] = i;
         ++off;
       }
+    }
   }
 }
 
@@ -276,9 +288,9 @@ __global__ void __launch_bounds__(kThreads) tile_ranges(WsView v, int buf) {
   const int n = v.hdr->n_pairs;
   const uint32_t* keys = v.pkey[buf];
   for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
-    uint32_t t = keys[i];
-    if (i == 0 || keys[i - 1] != t) v.ranges[t].x = i;
-    if (i == n - 1 || keys[i + 1] != t) v.ranges[t].y = i + 1;
+    const uint32_t t = keys[i] & kTileKeyMask;
+    if (i == 0 || (keys[i - 1] & kTileKeyMask) != t) v.ranges[t].x = i;
+    if (i == n - 1 || (keys[i + 1] & kTileKeyMask) != t) v.ranges[t].y = i + 1;
   }
 }
 
