@@ -85,9 +85,10 @@ def peaks():
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples during the timed region.
 
-    A reader thread collects the samples; entering waits for the first one so
-    that sampling has started before the region begins, and only samples taken
-    between entry and exit are summarised."""
+    nvidia-smi writes its samples to a file (no reader thread competes with
+    the timed loop for the interpreter); entering waits for the first sample
+    so that sampling has started before the region begins, and only samples
+    taken between entry and exit are summarised."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -98,37 +99,43 @@ class ClockSampler:
         self.period_ms = period_ms
         self.proc = None
         self.lines: list[str] = []
-        self.active = False
 
-    def _reader(self):
-        for line in self.proc.stdout:
-            if self.active:
-                self.lines.append(line)
-            self.first.set()
+    def _read(self) -> list[str]:
+        try:
+            with open(self.path) as f:
+                return f.read().splitlines()
+        except OSError:
+            return []
 
     def __enter__(self):
-        import threading
-        self.first = threading.Event()
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", str(self.period_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.period_ms), "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
             return self
-        threading.Thread(target=self._reader, daemon=True).start()
-        self.first.wait(timeout=5.0)
-        self.active = True
+        t0 = time.perf_counter()
+        while not self._read() and time.perf_counter() - t0 < 5.0:
+            time.sleep(0.01)
+        self.skip = len(self._read())
         return self
 
     def __exit__(self, *a):
-        self.active = False
         if self.proc is not None:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+            self.lines = self._read()[self.skip:]
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
 
     def summary(self):
         rows = [r.split(",") for r in self.lines if r.count(",") >= 8]
@@ -384,11 +391,14 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    import gc
+    gc.disable()   # no collector pauses between the timed launches
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
         ms_store, fr_last = timed_steps(not args.recompute, args.steps)
         ms_rec, _ = timed_steps(args.recompute, max(3, args.steps // 2))
         t_wall = time.perf_counter() - t_wall
+    gc.enable()
     st, _ = _lib.read_status(fr_last.ws.data_ptr(), fr_last.ws_bytes, stream.cuda_stream)
     assert st == _lib.OK, f"pair list overflow during timing (status {st})"
     if world > 1:

@@ -2,9 +2,10 @@
 // background term alone: F = bg, D = e^{eps/gamma} (log D = eps / gamma), no
 // tracked hits, and every pixel's background weight is w_B = 1.  The binning
 // pass gives such tiles no work items, so the render passes never visit them;
-// this pass writes their forward outputs and, in the backward pass, their
-// per-block dL/dbg partials (the layout the render passes use), reading and
-// writing each pixel row of a tile as one contiguous run.
+// this pass writes their forward outputs (coalesced, row by row) and, in the
+// backward pass, their share of dL/dbg, with one warp per 8 x 4 pixel block
+// as the render passes use, so the background-gradient partials of all tiles
+// sum alike.
 #include "render_common.cuh"
 
 namespace pulsar {
@@ -48,50 +49,30 @@ __global__ void __launch_bounds__(256) background_fwd_kernel(const WsView v) {
   }
 }
 
-// Background-gradient partials of an empty tile's eight 8 x 4 pixel blocks,
-// one CTA per tile: the upstream gradient is read row by row as contiguous
-// runs, each thread sums w_B G of one (pixel column, channel) over the four
-// rows of a block row, and shared-memory atomics gather the block sums.
+// Background-gradient partials of an empty tile's 8 x 4 pixel blocks, one
+// warp per block as the backward render pass does.
 __global__ void __launch_bounds__(256) background_bwd_kernel(const WsView v) {
-  __shared__ float acc[kBlocksPerTile * 32];
-  __shared__ float wb[kTile];
   const int64_t tile = blockIdx.x;
   const int2 rg = v.ranges[tile];
   if (rg.y > rg.x) return;   // the render passes own this tile
+  const int block = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const SceneDev& S = v.scenes[scene_of_tile(v.scenes, v.n_scenes, tile)];
-  const int64_t lt = tile - S.tile_begin;
-  const int ty = (int)(lt / S.tiles_x), tx = (int)(lt - (int64_t)ty * S.tiles_x);
-  const int x0 = tx * kTile, nx = min(kTile, S.width - x0);
-  const int y0 = ty * kTile, ny = min(kTile, S.height - y0);
+  const PixelCtx pc = pixel_ctx(S, tile, block);
   const int C = S.n_channels;
-  const float inv_gamma = 1.0f / S.gamma;
-  for (int e = threadIdx.x; e < kBlocksPerTile * C; e += blockDim.x) acc[e] = 0.0f;
-  for (int br = 0; br < 4; ++br) {   // block rows of the tile
-    float sum[2] = {0.0f, 0.0f};     // this thread's elements f and f + 256 of each row
-    for (int r = 4 * br; r < min(4 * br + 4, ny); ++r) {
-      const int64_t p0 = (int64_t)(y0 + r) * S.width + x0;
-      __syncthreads();
-      if ((int)threadIdx.x < nx) wb[threadIdx.x] = __expf(S.eps * inv_gamma - S.log_norm_in[p0 + threadIdx.x]);
-      __syncthreads();
-      const float* g = S.grad_image + p0 * C;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int f = threadIdx.x + 256 * h;
-        if (f < nx * C) sum[h] = fmaf(wb[f / C], g[f], sum[h]);
-      }
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int f = threadIdx.x + 256 * h;
-      if (f < nx * C) {
-        const int x = f / C, c = f - x * C;
-        atomicAdd(&acc[(br * 2 + (x >> 3)) * C + c], sum[h]);
-      }
-    }
+  const int64_t pix = (int64_t)pc.py * S.width + pc.px;
+  float wB = 0.0f;
+  const float* g = S.grad_image;
+  if (pc.inside) {
+    wB = __expf(S.eps * (1.0f / S.gamma) - S.log_norm_in[pix]);
+    g += pix * C;
   }
-  __syncthreads();
-  float* dst = v.tile_bg + (size_t)tile * kBlocksPerTile * C;
-  for (int e = threadIdx.x; e < kBlocksPerTile * C; e += blockDim.x) dst[e] = acc[e];
+  float* dst = v.tile_bg + ((size_t)tile * kBlocksPerTile + block) * C;
+  for (int c = 0; c < C; ++c) {
+    float y = 0.0f;
+    if (pc.inside) y = wB * g[c];
+    const float x = warp_sum(y);
+    if (lane == 0) dst[c] = x;
+  }
 }
 
 }  // namespace
