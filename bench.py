@@ -527,12 +527,13 @@ def main():
         dt, frac = cpu_oracle_sample(sc, 16)
         cpu = {"value": frac / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": "16x16-pixel window of the workload, fwd + bwd, FP64 brute force over all 1M spheres"}
-    # kernels per step: project 2 (setup, project), binning 23 (four 8-bit radix
+    # kernels per step: project 2 (setup, project); binning 24 (four 8-bit radix
     # passes of the 32-bit depth keys and two of the 12-bit tile keys, 3 kernels
-    # each, then count, scan, emit, ranges, items), forward 2 (setup, render),
-    # backward 5 (setup, render, finalize, camera partials, camera reduce), plus
-    # the track pass in recompute mode
-    launches_store, launches_rec = 32, 33
+    # each, then count, scan, emit, ranges, items, block lists); forward 3
+    # (setup, render, background); backward 7 (setup, zeroing, render,
+    # background, finalize, camera partials, camera reduce); plus the track pass
+    # in recompute mode
+    launches_store, launches_rec = 36, 37
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step,
             "ms_per_step_median": ms_sorted[len(ms_sorted) // 2], "ms_per_step_max": ms_sorted[-1], "higher_is_better": True, "scaling": "weak",

@@ -29,6 +29,7 @@ struct BlockListWarp {
   uint32_t geom[32];   // overlap with the block: x0 | y0 << 8 | width << 16
   uint32_t wdiv[32];   // ceil(2^16 / width): test index / width = (index * wdiv) >> 16
   uint32_t hm[32];     // hit masks being built
+  uint8_t owner[1024]; // entry of each test number of the batch
 };
 
 // Tests the pixels of the first cnt gathered entries against the block and
@@ -52,12 +53,14 @@ __device__ __forceinline__ void block_batch(BlockListWarp& W, int cnt, const WsV
     W.wdiv[lane] = (65536u + (uint32_t)w - 1u) / (uint32_t)w;
   }
   int total;
-  W.first[lane] = warp_exclusive_scan(ntest, total);
+  const int first = warp_exclusive_scan(ntest, total);
+  W.first[lane] = first;
   W.hm[lane] = 0u;
+  for (int k = 0; k < ntest; ++k) W.owner[first + k] = (uint8_t)lane;
   __syncwarp();
   // the batch's pixel tests, spread evenly over the lanes
   for (int k = lane; k < total; k += 32) {
-    const int e = item_owner(W.first, k);
+    const int e = W.owner[k];
     const uint32_t r = (uint32_t)(k - W.first[e]);
     const uint32_t g = W.geom[e];
     const uint32_t dy = (r * W.wdiv[e]) >> 16;
