@@ -176,7 +176,7 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
       // exponent may exceed log D by any amount
       const float E = __expf(fminf(s - logD, 80.0f));
       const float w = o * d * E;
-      const float* f = &sb.feat[cur][j * CMAX];
+      const float* f = &sb.feat[cur][j * StageBuf<CMAX, kBwdBuffers>::FS];
       float gdot;   // G.(f_i - F)
       if (id == dom) {
         gdot = -GFres;

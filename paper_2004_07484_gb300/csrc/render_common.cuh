@@ -187,10 +187,13 @@ __device__ __forceinline__ int item_owner(const int* first, int k) {
 
 template <int CMAX, int NB = 2>
 struct StageBuf {
+  // feature rows are padded so that lanes reading the rows of different
+  // spheres with 16-byte loads spread over all shared-memory banks
+  static constexpr int FS = CMAX >= 8 ? CMAX + 4 : CMAX;
   float4 rec0[NB][32];
   float4 rec1[NB][32];
   float4 rec2[NB][32];
-  float feat[NB][32 * CMAX];
+  float feat[NB][32 * FS];
   int32_t id[NB][32];
   uint32_t hm[NB][32];
 };
@@ -239,7 +242,7 @@ struct UnitStream {
         cp_async16(&sb.rec2[to][lane], v.rec2 + id);
         const int C = S.n_channels;
         const float* __restrict__ f = S.feat + (int64_t)(id - S.sphere_begin) * C;
-        float* dst = &sb.feat[to][lane * CMAX];
+        float* dst = &sb.feat[to][lane * StageBuf<CMAX, NB>::FS];
         if ((C & 3) == 0 && (reinterpret_cast<uintptr_t>(f) & 15) == 0) {
 #pragma unroll
           for (int c = 0; c < CMAX; c += 4)
@@ -260,7 +263,7 @@ struct UnitStream {
                                         const ItemCtx& it, bool need_values) {
     const int lane = threadIdx.x & 31;
     if (need_values && S.n_channels < CMAX)
-      for (int e = lane; e < NB * 32 * CMAX; e += 32) (&sb.feat[0][0])[e] = 0.0f;
+      for (int e = lane; e < NB * 32 * StageBuf<CMAX, NB>::FS; e += 32) (&sb.feat[0][0])[e] = 0.0f;
     __syncwarp();
     src = v.unit_list + (size_t)it.block * v.capacity + it.b0;
     n = v.unit_count[it.slot];

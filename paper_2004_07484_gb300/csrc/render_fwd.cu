@@ -176,7 +176,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
         const float od = b.y * d;
         if (od != 0.0f) {   // a zero weight adds nothing and must not move the shift
           const float z = (((zfar - a.z) - c2.z) + vg.off) * inv_range;
-          blend_hit<CMAX>(bs, b.y * z * inv_gamma, od, &sb.feat[cur][j * CMAX], id);
+          blend_hit<CMAX>(bs, b.y * z * inv_gamma, od, &sb.feat[cur][j * StageBuf<CMAX>::FS], id);
         }
       }
       if (may_queue) {
@@ -280,13 +280,14 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
     // of the block is one contiguous run of the row-major outputs
     float* st_img = &sb.feat[0][0];
     float* st_res = &sb.feat[1][0];
+    constexpr int SS = CMAX >= 8 ? CMAX + 1 : CMAX;   // staging row stride (bank-conflict free)
     const float inv = 1.0f / bs.den;
 #pragma unroll
     for (int c = 0; c < CMAX; ++c)
       if (c < C) {
         const float r = bs.res[c] * inv;
-        st_img[lane * CMAX + c] = bs.fref[32 * c] + r;
-        st_res[lane * CMAX + c] = r;
+        st_img[lane * SS + c] = bs.fref[32 * c] + r;
+        st_res[lane * SS + c] = r;
       }
     __syncwarp();
     const int bx0 = pc.tile_x0 + (it.block & 1) * 8, by0 = pc.tile_y0 + (it.block >> 1) * 4;
@@ -297,7 +298,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
       float* fr = v.fres + (S.pixel_begin + p0) * C;
       for (int f = lane; f < nx * C; f += 32) {
         const int pxl = f / C;
-        const int src = (r * 8 + pxl) * CMAX + (f - pxl * C);
+        const int src = (r * 8 + pxl) * SS + (f - pxl * C);
         img[f] = st_img[src];
         fr[f] = st_res[src];
       }

@@ -41,7 +41,7 @@ def test_two_rank_timing_exchange_and_throughput():
     import torch.multiprocessing as mp
     world, port = 2, _free_port()
     times = [12.5, 20.0]   # milliseconds for 10 renders on each rank
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank_main, args=(world, port, times, out), nprocs=world, join=True)
         res = dict(out)
