@@ -27,25 +27,36 @@ __global__ void __launch_bounds__(256) background_fwd_kernel(const WsView v) {
   const int C = S.n_channels, K = S.n_track, nx = x1 - x0;
   const float log_d = S.eps * (1.0f / S.gamma) + __logf(1.0f);
   const float4 aux = make_float4(__int_as_float(0x7f800000), __int_as_float(0x7fffffff), __int_as_float(-1), 0.0f);
-  for (int y = y0; y < y1; ++y) {
-    const int64_t p0 = (int64_t)y * S.width + x0;   // first pixel of the row run
-    float* img = S.image + p0 * C;
-    float* fr = v.fres + (S.pixel_begin + p0) * C;
-    for (int f = threadIdx.x; f < nx * C; f += blockDim.x) {
-      img[f] = S.bg[f % C];
-      fr[f] = 0.0f;
+  const int ny = y1 - y0;
+  float* const img0 = S.image + ((int64_t)y0 * S.width + x0) * C;
+  float* const fr0 = v.fres + (S.pixel_begin + (int64_t)y0 * S.width + x0) * C;
+  const int64_t row = (int64_t)S.width * C;   // floats between pixel rows
+  const bool vec = (C & 3) == 0 && ((reinterpret_cast<uintptr_t>(img0) | reinterpret_cast<uintptr_t>(fr0) |
+                                     reinterpret_cast<uintptr_t>(S.bg)) & 15) == 0 && (row & 3) == 0;
+  if (vec) {   // 16-byte stores, consecutive threads on consecutive vectors of a row
+    const int c4 = C >> 2, per_row = nx * c4;
+    const float4* bg4 = reinterpret_cast<const float4*>(S.bg);
+    for (int e = threadIdx.x; e < ny * per_row; e += blockDim.x) {
+      const int r = e / per_row, q = e - r * per_row;
+      reinterpret_cast<float4*>(img0 + r * row)[q] = bg4[q % c4];
+      reinterpret_cast<float4*>(fr0 + r * row)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (S.tracked) {
-      int32_t* tr = S.tracked + p0 * K;
-      for (int f = threadIdx.x; f < nx * K; f += blockDim.x) tr[f] = -1;
+  } else {
+    for (int e = threadIdx.x; e < ny * nx * C; e += blockDim.x) {
+      const int r = e / (nx * C), f = e - r * (nx * C);
+      img0[r * row + f] = S.bg[f % C];
+      fr0[r * row + f] = 0.0f;
     }
-    if ((int)threadIdx.x < nx) {
-      const int64_t p = p0 + threadIdx.x;
-      S.log_norm[p] = log_d;
-      if (S.n_hits) S.n_hits[p] = 0;
-      if (S.n_tests) S.n_tests[p] = 0;
-      v.pix_aux[S.pixel_begin + p] = aux;
-    }
+  }
+  for (int e = threadIdx.x; e < ny * nx; e += blockDim.x) {
+    const int r = e / nx, x = e - r * nx;
+    const int64_t p = (int64_t)(y0 + r) * S.width + x0 + x;
+    S.log_norm[p] = log_d;
+    if (S.n_hits) S.n_hits[p] = 0;
+    if (S.n_tests) S.n_tests[p] = 0;
+    v.pix_aux[S.pixel_begin + p] = aux;
+    if (S.tracked)
+      for (int k = 0; k < K; ++k) S.tracked[p * K + k] = -1;
   }
 }
 
