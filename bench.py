@@ -30,6 +30,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd renders/sec at 1M spheres 1024x1024"
+# other single-scene workloads (--config), for the table of measured rates
+OTHER_WORKLOADS = {
+    0: ("fwd+bwd renders/sec at 1,000 spheres 64x64",
+        "1,000 spheres uniform in a box, 64x64, C=3 U[0,1], gamma=0.1, n_track=5"),
+    1: ("fwd+bwd renders/sec at 100k spheres 512x512",
+        "100k spheres in 8 Gaussian clusters, 512x512, C=3, gamma=1e-2, n_track=10"),
+}
 UNIT = "renders/s"
 WORKLOAD = "1M spheres on 20 ellipsoid surfaces, 1024x1024, C=16 N(0,1), gamma=1e-2, n_track=16"
 FP32_LANES_PER_SM = 128
@@ -39,7 +46,7 @@ N_SMS = 152
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only
 # for the kernel sources with this digest, reported as null otherwise.
 FWD_KERNEL_SOURCES = ("render_fwd.cu", "render_common.cuh", "pulsar_internal.cuh")
-FWD_TRAFFIC = {"sha256": "05261fa5185b4b1016210ce7130802e8e19ef4eca4cab6b014449110ae732a5a", "bytes": 167737600 + 194724608}
+FWD_TRAFFIC = {"sha256": "f7c95c722e2c0f0ed8da68625b08c9ea7405e21287b2be6326ceab96254a5f8d", "bytes": 213577728 + 14089984}
 
 
 def fwd_kernel_digest() -> str:
@@ -150,8 +157,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_scene(rank: int, n: int | None = None, res: int | None = None):
+def make_scene(rank: int, n: int | None = None, res: int | None = None, config: int = 2):
     from paper_2004_07484_gb300 import scenes
+    if config != 2:
+        return scenes.config_scene(config, gamma=1e-2 if config == 1 else None)
     if rank == 0:
         return scenes.config_scene(2, n=n, res=res)
     return scenes.ellipsoid_surfaces(1002 + 7919 * rank, n or 1_000_000, res or 1024, res or 1024,
@@ -164,7 +173,8 @@ def cpu_oracle_sample(sc, n_side: int):
     from oracle import oracle
     from paper_2004_07484_gb300 import scenes
     oracle.build()
-    v0, u0 = 448, 448
+    n_side = min(n_side, sc.width, sc.height)
+    v0, u0 = (sc.height - n_side) // 2, (sc.width - n_side) // 2
     pix = [(u, v) for v in range(v0, v0 + n_side) for u in range(u0, u0 + n_side)]
     G = np.zeros((sc.height, sc.width, sc.n_channels))
     G[v0:v0 + n_side, u0:u0 + n_side] = scenes.grad_image(5, n_side, n_side, sc.n_channels)
@@ -295,6 +305,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 32-scene batched comparison")
+    ap.add_argument("--config", type=int, default=2, choices=[0, 1, 2],
+                    help="single-scene workload: 2 = the 1M-sphere headline (default), 0 and 1 = the small ones")
     ap.add_argument("--recompute", action="store_true", help="time recompute mode as the main value")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run one step inside the NVTX range 'pulsar_step' and exit (for ncu)")
@@ -321,7 +333,8 @@ def main():
         dist.barrier()
         __graft_entry__.build()
 
-    sc = make_scene(rank, args.spheres, args.res)
+    sc = make_scene(rank, args.spheres, args.res, args.config)
+    metric, workload = (METRIC, WORKLOAD) if args.config == 2 else OTHER_WORKLOADS[args.config]
     t = {k: torch.from_numpy(np.ascontiguousarray(getattr(sc, k))).to(dev)
          for k in ("pos", "rad", "opa", "feat", "cam", "bg")}
     G = torch.from_numpy(np.ascontiguousarray(
@@ -534,11 +547,11 @@ def main():
     # background, finalize, camera partials, camera reduce); plus the track pass
     # in recompute mode
     launches_store, launches_rec = 36, 37
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step,
             "ms_per_step_median": ms_sorted[len(ms_sorted) // 2], "ms_per_step_max": ms_sorted[-1], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-            "config": {"workload": WORKLOAD, "renders_per_step": world,
+            "config": {"workload": workload, "renders_per_step": world,
                        "parallelism": f"replicas x{world} (independent renders)",
                        "l2": "flushed between steps (256 MB write, untimed)",
                        "hit_lists": "recompute" if args.recompute else "store"},

@@ -79,13 +79,19 @@ __device__ __forceinline__ void block_batch(BlockListWarp& W, int cnt, const WsV
   __syncwarp();   // the batch's shared data is rewritten next
 }
 
-__global__ void __launch_bounds__(256) block_lists_kernel(const WsView v, const uint32_t* __restrict__ keys,
-                                                          const uint32_t* __restrict__ list) {
-  __shared__ BlockListWarp warps[8];
-  const int item = blockIdx.x;
-  const int block = threadIdx.x >> 5;
+// Two warps (two pixel blocks of one item) per CTA: a CTA's warps finish at
+// different times, and smaller CTAs hand their slot back sooner.
+constexpr int kListWarps = 2;
+
+__global__ void __launch_bounds__(32 * kListWarps) block_lists_kernel(const WsView v,
+                                                                       const uint32_t* __restrict__ keys,
+                                                                       const uint32_t* __restrict__ list) {
+  __shared__ BlockListWarp warps[kListWarps];
+  constexpr int kCtasPerItem = kBlocksPerTile / kListWarps;
+  const int item = blockIdx.x / kCtasPerItem;
+  const int block = (blockIdx.x % kCtasPerItem) * kListWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  BlockListWarp& W = warps[block];
+  BlockListWarp& W = warps[threadIdx.x >> 5];
   ItemCtx it;
   if (!item_ctx_direct(v, item, block, it)) return;
   const SceneDev& S = v.scenes[it.scene];
@@ -153,7 +159,8 @@ __global__ void __launch_bounds__(256) count_tests_kernel(const WsView v, const 
 
 cudaError_t launch_block_lists(const WsView& v, cudaStream_t st) {
   if (v.max_items == 0) return cudaSuccess;
-  block_lists_kernel<<<(unsigned)v.max_items, 256, 0, st>>>(v, v.pkey[v.pair_buf], v.pval[v.pair_buf]);
+  block_lists_kernel<<<(unsigned)v.max_items * (kBlocksPerTile / kListWarps), 32 * kListWarps, 0, st>>>(
+      v, v.pkey[v.pair_buf], v.pval[v.pair_buf]);
   return cudaGetLastError();
 }
 
