@@ -539,7 +539,8 @@ def main():
     if not args.no_cpu_baseline:
         dt, frac = cpu_oracle_sample(sc, 16)
         cpu = {"value": frac / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-               "sample": "16x16-pixel window of the workload, fwd + bwd, FP64 brute force over all 1M spheres"}
+               "sample": f"16x16-pixel window at the image centre, fwd + bwd, FP64 brute force over all "
+                         f"{sc.n_spheres} spheres"}
     # kernels per step: project 2 (setup, project); binning 24 (four 8-bit radix
     # passes of the 32-bit depth keys and two of the 12-bit tile keys, 3 kernels
     # each, then count, scan, emit, ranges, items, block lists); forward 3

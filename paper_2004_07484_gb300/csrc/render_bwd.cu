@@ -75,7 +75,12 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
   const bool feat = (mask & PULSAR_GRAD_FEAT) != 0;
   const bool cam = (mask & PULSAR_GRAD_CAM) != 0;
   const bool bgw = (mask & PULSAR_GRAD_BG) != 0;
+  const bool per_hit = geo || opa || feat;
   const int lane = threadIdx.x & 31;
+
+  // the first batches of the block list stage while the pixel data loads
+  UnitStream<CMAX, kBwdBuffers> ws;
+  if (per_hit) ws.start(sb, v, S, it, true);
 
   // per-pixel upstream data
   const int64_t pix = pc.inside ? (int64_t)pc.py * S.width + pc.px : 0;
@@ -129,7 +134,7 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
       if (lane == 0 && c < C) dst[c] = x;
     }
   }
-  if (!(geo || opa || feat)) {
+  if (!per_hit) {
     if (cam && lane == 0) v.item_kappa[it.slot] = 0.0f;
     return;
   }
@@ -137,8 +142,6 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
   const float kstop = next_up(thr_t);
   bool done = !pc.inside;
   float gk_sum = 0.0f;
-  UnitStream<CMAX, kBwdBuffers> ws;
-  ws.start(sb, v, S, it, true);
   for (; ws.base < ws.n; ws.advance()) {
     if (__all_sync(0xffffffffu, done)) break;
     uint32_t hits = ws.begin(sb, v, S, true);

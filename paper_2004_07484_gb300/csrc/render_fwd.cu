@@ -107,6 +107,10 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   const bool literal = (S.flags & PULSAR_FLAG_DIST_LITERAL) != 0;
   const int lane = threadIdx.x;
 
+  // the first batches of the block list stage while the state is set up
+  UnitStream<CMAX> ws;
+  ws.start(sb, v, S, it, BLEND);
+
   // the background term e^{eps/g - m} belongs to the first segment only
   BlendState<CMAX> bs;
   bs.fref = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(&sb) + sizeof(StageBuf<CMAX>)) + lane;
@@ -125,8 +129,6 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   bool done = !pc.inside;
   float kstop1 = __int_as_float(0x7f800000);   // tracked-set bound (i)
 
-  UnitStream<CMAX> ws;
-  ws.start(sb, v, S, it, BLEND);
   if (S.n_tests) ntest = v.unit_tests[(size_t)it.slot * 32 + lane];
   for (; ws.base < ws.n; ws.advance()) {
     if (__all_sync(0xffffffffu, done)) break;

@@ -185,3 +185,32 @@ def test_fma_probe_measures_a_plausible_fp32_rate():
     # 152 SMs x 128 FP32 lanes x 2 flops at 0.5..2.1 GHz
     assert 10e12 < flops < 90e12, flops
     assert float(sink.item()) == 0.0
+
+
+def test_adam_steps_reduce_the_image_loss():
+    """The renderer as a training component: Adam on positions, radii,
+    opacities and colours lowers the L2 distance to a target rendered from
+    perturbed spheres (the shape of the paper's optimisation experiments)."""
+    import torch
+    from paper_2004_07484_gb300 import Renderer
+    sc = S.config_scene(0)
+    r = Renderer(sc.width, sc.height, sc.n_spheres, n_channels=3, n_track=sc.n_track, gamma=sc.gamma)
+    t = {k: torch.from_numpy(getattr(sc, k)).cuda() for k in ("pos", "feat", "rad", "opa", "cam", "bg")}
+    with torch.no_grad():
+        target = r(t["pos"], t["feat"], t["rad"], t["cam"], opa=t["opa"], bg=t["bg"]).clone()
+    g = torch.Generator(device="cuda").manual_seed(3)
+    p = {"pos": (t["pos"] + 0.02 * torch.randn(t["pos"].shape, generator=g, device="cuda")).requires_grad_(True),
+         "feat": (t["feat"] * 0.7).requires_grad_(True),
+         "rad": (t["rad"] * 1.2).requires_grad_(True),
+         "opa": (t["opa"] * 0.9).requires_grad_(True)}
+    opt = torch.optim.Adam(p.values(), lr=1e-2)
+    losses = []
+    for _ in range(30):
+        opt.zero_grad()
+        img = r(p["pos"], p["feat"], p["rad"], t["cam"], opa=p["opa"], bg=t["bg"])
+        loss = ((img - target) ** 2).sum()
+        loss.backward()
+        opt.step()
+        losses.append(float(loss))
+    assert all(np.isfinite(losses))
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])

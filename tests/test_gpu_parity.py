@@ -230,3 +230,25 @@ def test_1m_spheres_1024_sampled(orc):
     for store in (True, False):
         out = gpu if store else gpu_forward(sc, store=False, capacity=16 << 20)
         assert_grads_close(gpu_backward(out, G), want, scene=sc)
+
+
+def test_5m_spheres_1920x1080_sampled(orc):
+    """The largest single-scene workload (5M spheres on ellipsoid surfaces,
+    1920x1080, C=3, n_track 8) at sampled pixels, with a gradient crop."""
+    sc = S.config_scene(4)
+    gpu = gpu_forward(sc, capacity=48 << 20)
+    g = np.random.default_rng(11)
+    n_hits = gpu["n_hits"].cpu().numpy()
+    busy = np.argwhere(n_hits > 0)
+    pix = np.concatenate([busy[g.choice(len(busy), 60, replace=False)][:, ::-1],
+                          np.stack([g.integers(0, 1920, 12), g.integers(0, 1080, 12)], 1)])
+    ref = orc.render_pixels(sc, pix)
+    img = gpu["image"].cpu().numpy()[pix[:, 1], pix[:, 0]]
+    assert np.abs(img - ref.image).max() <= 1e-4
+    np.testing.assert_array_equal(gpu["tracked"].cpu().numpy()[pix[:, 1], pix[:, 0]], ref.tracked)
+    v, u = busy[g.integers(len(busy))]
+    v0, u0 = min(max(v - 6, 0), 1080 - 12), min(max(u - 6, 0), 1920 - 12)
+    G = np.zeros((1080, 1920, 3))
+    G[v0:v0 + 12, u0:u0 + 12] = S.grad_image(6, 12, 12, 3)
+    want = orc.render_backward(sc, G)
+    assert_grads_close(gpu_backward(gpu, G), want, scene=sc)
