@@ -211,6 +211,6 @@ def test_adam_steps_reduce_the_image_loss():
         loss = ((img - target) ** 2).sum()
         loss.backward()
         opt.step()
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     assert all(np.isfinite(losses))
     assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
