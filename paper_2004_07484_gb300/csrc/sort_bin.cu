@@ -209,9 +209,6 @@ __global__ void __launch_bounds__(kThreads) count_reduce(WsView v) {
 // Exclusive scan of the block sums; records the pair total and the overflow flag.
 __global__ void __launch_bounds__(1024) count_scan(WsView v, int n_blocks) {
   __shared__ uint32_t warp_tot[33];
-  __shared__ unsigned long long s_total;
-  if (threadIdx.x == 0) s_total = 0;
-  __syncthreads();
   unsigned long long carry = 0;
   for (int b0 = 0; b0 < n_blocks; b0 += 1024) {
     int b = b0 + threadIdx.x;
