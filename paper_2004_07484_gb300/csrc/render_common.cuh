@@ -162,19 +162,6 @@ __device__ __forceinline__ int warp_exclusive_scan(int x, int& total) {
   return inc - x;
 }
 
-// The lane owning item k of a warp-wide enumeration, given every lane's
-// first item number (ascending): the last lane whose items start at or
-// before k.  A lane without items shares its first number with the next
-// lane, so the last one is the owner.
-__device__ __forceinline__ int item_owner(const int* first, int k) {
-  int l = 0, r = 31;
-  while (l < r) {
-    const int mid = (l + r + 1) >> 1;
-    if (first[mid] <= k) l = mid; else r = mid - 1;
-  }
-  return l;
-}
-
 // ----------------------------------------------------------------------------
 // Asynchronous staging of a work unit's block list.  A warp streams the list
 // (entries: sphere index, hit mask over the block's 32 pixels), 32 entries
@@ -315,12 +302,6 @@ __device__ __forceinline__ bool ray_disc_positive(float cx, float cy, float cz, 
   const float cr2 = __fmaf_rn(ex, ex, __fmaf_rn(ey, ey, __fmul_rn(ez, ez)));
   const float rr = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, 1.0f));
   return __fmaf_rn(rr, R2, -cr2) > 0.0f;
-}
-
-__device__ __forceinline__ bool in_rect(const float4& b, int px, int py) {
-  const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
-  return px >= (int)(bx & 0xffffu) && px <= (int)(bx >> 16) && py >= (int)(by & 0xffffu) &&
-         py <= (int)(by >> 16);
 }
 
 // (t, id) ordering of tracked hits: by depth, then by sphere index.

@@ -54,7 +54,7 @@ template <int CMAX>
 struct BlendState {
   float m, den, adom;
   int dom;            // global index of the reference sphere, -1 = background
-  float* fref;   // this lane's reference feature, in shared memory (channel stride 32)
+  float* fref;   // this lane's reference feature: a padded row in shared memory
   float res[CMAX];
 };
 
@@ -73,14 +73,14 @@ __device__ __forceinline__ void blend_hit(BlendState<CMAX>& b, float s, float od
     // the new hit becomes the reference: re-express the numerator
 #pragma unroll
     for (int c = 0; c < CMAX; ++c) {
-      b.res[c] = fmaf(b.den, b.fref[32 * c] - f[c], b.res[c]);
-      b.fref[32 * c] = f[c];
+      b.res[c] = fmaf(b.den, b.fref[c] - f[c], b.res[c]);
+      b.fref[c] = f[c];
     }
     b.adom = ap;
     b.dom = id;
   } else {
 #pragma unroll
-    for (int c = 0; c < CMAX; ++c) b.res[c] = fmaf(ap, f[c] - b.fref[32 * c], b.res[c]);
+    for (int c = 0; c < CMAX; ++c) b.res[c] = fmaf(ap, f[c] - b.fref[c], b.res[c]);
   }
   b.den += ap;
 }
@@ -113,14 +113,15 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
 
   // the background term e^{eps/g - m} belongs to the first segment only
   BlendState<CMAX> bs;
-  bs.fref = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(&sb) + sizeof(StageBuf<CMAX>)) + lane;
+  bs.fref = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(&sb) + sizeof(StageBuf<CMAX>)) +
+            lane * StageBuf<CMAX>::FS;
   bs.m = S.eps * inv_gamma;
   bs.den = it.seg == 0 ? 1.0f : 0.0f;
   bs.adom = bs.den;
   bs.dom = -1;
 #pragma unroll
   for (int c = 0; c < CMAX; ++c) {
-    if (BLEND) bs.fref[32 * c] = c < C ? S.bg[c] : 0.0f;
+    if (BLEND) bs.fref[c] = c < C ? S.bg[c] : 0.0f;
     bs.res[c] = 0.0f;
   }
   uint64_t q[KMAX];
@@ -249,8 +250,8 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
             if (c < C) {
               const float fb = fB[c];
               bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * 32),
-                               fmaf(bs.den, bs.fref[32 * c] - fb, bs.res[c] * sa));
-              bs.fref[32 * c] = fb;
+                               fmaf(bs.den, bs.fref[c] - fb, bs.res[c] * sa));
+              bs.fref[c] = fb;
             }
           bs.adom = adomB;
           bs.dom = domB;
@@ -259,7 +260,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
           for (int c = 0; c < CMAX; ++c)
             if (c < C)
               bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * 32),
-                               fmaf(denB, fB[c] - bs.fref[32 * c], bs.res[c] * sa));
+                               fmaf(denB, fB[c] - bs.fref[c], bs.res[c] * sa));
         }
         bs.den += denB;
         bs.m = m;
@@ -288,7 +289,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
     for (int c = 0; c < CMAX; ++c)
       if (c < C) {
         const float r = bs.res[c] * inv;
-        st_img[lane * SS + c] = bs.fref[32 * c] + r;
+        st_img[lane * SS + c] = bs.fref[c] + r;
         st_res[lane * SS + c] = r;
       }
     __syncwarp();
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v, int pe
 template <int KMAX, int CMAX, bool BLEND>
 cudaError_t launch_t(const WsView& v, cudaStream_t st) {
   // staging buffers, then (blending) every lane's reference feature
-  const size_t smem = sizeof(StageBuf<CMAX>) + (BLEND ? sizeof(float) * 32 * CMAX : 0);
+  const size_t smem = sizeof(StageBuf<CMAX>) + (BLEND ? sizeof(float) * 32 * StageBuf<CMAX>::FS : 0);
   auto kern = traverse_kernel<KMAX, CMAX, BLEND>;
   unsigned grid = (unsigned)v.max_items * kBlocksPerTile;
   if (v.persistent) {
