@@ -186,6 +186,14 @@ pulsar_status pulsar_read_tile_lists(const pulsar_params* params, void* workspac
 pulsar_status pulsar_read_status(void* workspace, size_t workspace_bytes, int64_t* pairs_needed,
                                  void* stream);
 
+/* The overflow check in workspace terms: synchronises the stream, and when
+ * the last pulsar_bin overflowed list_capacity returns PULSAR_ERR_CAPACITY
+ * and writes through needed_bytes (may be NULL) the workspace bytes these
+ * params need with list_capacity raised to the pairs that binning required.
+ * Returns PULSAR_OK (needed_bytes = the current requirement) otherwise. */
+pulsar_status pulsar_last_overflow(const pulsar_params* params, void* workspace,
+                                   size_t workspace_bytes, size_t* needed_bytes, void* stream);
+
 /* Size of the device array pulsar_render_fwd_static uses as its workspace. */
 #define PULSAR_STATIC_WORKSPACE_BYTES (64u << 20)
 
@@ -276,6 +284,12 @@ pulsar_status pulsar_render_fwd_batched(int n_scenes, const pulsar_params* param
                                         const pulsar_scene* scenes, void* workspace,
                                         size_t workspace_bytes, const pulsar_fwd_out* out,
                                         void* stream);
+
+/* The whole batched forward in one call: pulsar_project_batched,
+ * pulsar_bin_batched and pulsar_render_fwd_batched on the same workspace. */
+pulsar_status pulsar_render_batched(int n_scenes, const pulsar_params* params,
+                                    const pulsar_scene* scenes, void* workspace,
+                                    size_t workspace_bytes, const pulsar_fwd_out* out, void* stream);
 
 /* pulsar_render_bwd over every scene of the batch; io[s] holds scene s's
  * forward outputs, upstream gradient and gradient outputs. */

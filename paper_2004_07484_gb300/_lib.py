@@ -27,7 +27,7 @@ EXPORTED = ("pulsar_workspace_size", "pulsar_project", "pulsar_bin", "pulsar_ren
             "pulsar_status_string", "pulsar_render_fwd_static", "pulsar_workspace_size_batched",
             "pulsar_project_batched", "pulsar_bin_batched", "pulsar_render_fwd_batched",
             "pulsar_render_bwd_batched", "pulsar_read_tile_lists_batched",
-            "pulsar_probe_fma_throughput")
+            "pulsar_probe_fma_throughput", "pulsar_last_overflow", "pulsar_render_batched")
 
 MAX_SCENES = 64
 
@@ -106,6 +106,10 @@ def lib():
         L.pulsar_render_bwd_batched.restype = ctypes.c_int
         L.pulsar_read_tile_lists_batched.argtypes = [i32, P, vp, sz, vp, vp, vp]
         L.pulsar_read_tile_lists_batched.restype = ctypes.c_int
+        L.pulsar_last_overflow.argtypes = [P, vp, sz, ctypes.POINTER(ctypes.c_size_t), vp]
+        L.pulsar_last_overflow.restype = ctypes.c_int
+        L.pulsar_render_batched.argtypes = [i32, P, S, vp, sz, ctypes.POINTER(FwdOut), vp]
+        L.pulsar_render_batched.restype = ctypes.c_int
         L.pulsar_probe_fma_throughput.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
                                                   ctypes.POINTER(ctypes.c_float), vp]
         L.pulsar_probe_fma_throughput.restype = ctypes.c_int
@@ -213,3 +217,14 @@ def probe_fma_throughput(sink: int, iters: int, stream: int) -> tuple[float, flo
     _check(lib().pulsar_probe_fma_throughput(sink, int(iters), ctypes.byref(f), ctypes.byref(ms), stream),
            "pulsar_probe_fma_throughput")
     return float(f.value), float(ms.value)
+
+
+def last_overflow(p: Params, ws: int, ws_bytes: int, stream: int) -> tuple[int, int]:
+    """(status, workspace bytes needed); synchronises the stream."""
+    need = ctypes.c_size_t(0)
+    st = lib().pulsar_last_overflow(ctypes.byref(p), ws, ws_bytes, ctypes.byref(need), stream)
+    return int(st), int(need.value)
+
+
+def render_batched(ps, ss, ws: int, ws_bytes: int, outs, stream: int) -> None:
+    _check(lib().pulsar_render_batched(len(ps), ps, ss, ws, ws_bytes, outs, stream), "pulsar_render_batched")

@@ -468,6 +468,31 @@ extern "C" pulsar_status pulsar_read_status(void* workspace, size_t workspace_by
   return PULSAR_OK;
 }
 
+extern "C" pulsar_status pulsar_last_overflow(const pulsar_params* params, void* workspace,
+                                              size_t workspace_bytes, size_t* needed_bytes, void* stream) {
+  if (validate(params) != PULSAR_OK) return PULSAR_ERR_INVALID_ARG;
+  int64_t pairs = 0;
+  const pulsar_status st = pulsar_read_status(workspace, workspace_bytes, &pairs, stream);
+  if (st != PULSAR_OK && st != PULSAR_ERR_CAPACITY) return st;
+  if (needed_bytes) {
+    pulsar_params p = *params;
+    if (pairs > p.list_capacity) p.list_capacity = pairs;
+    *needed_bytes = pulsar_workspace_size(&p);
+  }
+  return st;
+}
+
+extern "C" pulsar_status pulsar_render_batched(int n_scenes, const pulsar_params* params,
+                                               const pulsar_scene* scenes, void* workspace,
+                                               size_t workspace_bytes, const pulsar_fwd_out* out,
+                                               void* stream) {
+  pulsar_status st = pulsar_project_batched(n_scenes, params, scenes, workspace, workspace_bytes, stream);
+  if (st == PULSAR_OK) st = pulsar_bin_batched(n_scenes, params, workspace, workspace_bytes, stream);
+  if (st == PULSAR_OK)
+    st = pulsar_render_fwd_batched(n_scenes, params, scenes, workspace, workspace_bytes, out, stream);
+  return st;
+}
+
 extern "C" const char* pulsar_status_string(pulsar_status status) {
   switch (status) {
     case PULSAR_OK: return "ok";

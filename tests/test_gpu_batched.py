@@ -250,3 +250,22 @@ def test_autotune_and_graph_replay(orc):
         for a, b in zip(g_grads[k], eager_grads[k]):
             a, b = a.cpu().numpy(), b.cpu().numpy()
             assert np.abs(a - b).max() <= 1e-5 * max(1.0, np.abs(b).max()), sc.name
+
+
+def test_one_call_batched_forward_matches_the_three_calls(batch):
+    import torch
+    from paper_2004_07484_gb300 import _lib
+    from paper_2004_07484_gb300.renderer import BatchFrame, _scene_array
+    scs, out, _ = batch
+    fr = BatchFrame(out["frame"].settings, [sc.n_spheres for sc in scs], out["frame"].capacities(), "cuda")
+    outs = (_lib.FwdOut * len(scs))()
+    imgs, lns = [], []
+    for k, sc in enumerate(scs):
+        imgs.append(torch.empty((sc.height, sc.width, sc.n_channels), device="cuda"))
+        lns.append(torch.empty((sc.height, sc.width), device="cuda"))
+        outs[k] = _lib.FwdOut(imgs[k].data_ptr(), lns[k].data_ptr(), None, None, None)
+    _lib.render_batched(fr.params, _scene_array(out["inputs"]), fr.ws.data_ptr(), fr.ws_bytes, outs,
+                        torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for k, sc in enumerate(scs):
+        assert np.abs(imgs[k].cpu().numpy() - out["images"][k].cpu().numpy()).max() <= 1e-6, sc.name

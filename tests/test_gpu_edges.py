@@ -99,6 +99,10 @@ def test_capacity_overflow_is_reported_and_recovered(orc):
                              16, check_overflow=False)
     st, need = _lib.read_status(fr.ws.data_ptr(), fr.ws_bytes, torch.cuda.current_stream().cuda_stream)
     assert st == _lib.ERR_CAPACITY and need > 16
+    st2, need_bytes = _lib.last_overflow(fr.params, fr.ws.data_ptr(), fr.ws_bytes,
+                                         torch.cuda.current_stream().cuda_stream)
+    assert st2 == _lib.ERR_CAPACITY
+    assert need_bytes == _lib.workspace_size(s.params(sc.n_spheres, need)) > fr.ws_bytes
     fr2, img, _ = forward_frame(s, dev["pos"], dev["feat"], dev["rad"], dev["opa"], dev["cam"], dev["bg"],
                                 16, check_overflow=True)
     assert fr2.params.list_capacity >= need
