@@ -46,7 +46,7 @@ N_SMS = 152
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only
 # for the kernel sources with this digest, reported as null otherwise.
 FWD_KERNEL_SOURCES = ("render_fwd.cu", "render_common.cuh", "pulsar_internal.cuh")
-FWD_TRAFFIC = {"sha256": "f7c95c722e2c0f0ed8da68625b08c9ea7405e21287b2be6326ceab96254a5f8d", "bytes": 213577728 + 14089984}
+FWD_TRAFFIC = {"sha256": "0c18a84c90648613600b139281676a3d7c607c862076b480c4dd1c84c4054fd5", "bytes": 217284864 + 16429568}
 
 
 def fwd_kernel_digest() -> str:
