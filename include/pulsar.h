@@ -71,7 +71,14 @@ enum {
   /* Scheduling only (results are unchanged): the render passes run as
    * persistent kernels, one resident CTA per slot, each taking work items
    * from a counter, instead of one CTA per work item. */
-  PULSAR_FLAG_PERSISTENT = 1u << 3
+  PULSAR_FLAG_PERSISTENT = 1u << 3,
+  /* The backward pass adds its gradients into the caller's gradient buffers
+   * instead of overwriting them (the caller zeroes them when it wants plain
+   * gradients).  Scenes of one batch may then share gradient buffers: views
+   * of one sphere set, rendered as a batch, accumulate the gradient of a loss
+   * summed over views (Sec. 3.4).  Every output is added with atomics, so
+   * shared buffers are safe; the summation order is unspecified. */
+  PULSAR_FLAG_ACCUMULATE = 1u << 4
 };
 
 /* grad_mask bits of pulsar_render_bwd: gradients are computed only where
@@ -156,7 +163,8 @@ pulsar_status pulsar_render_fwd(const pulsar_params* params, const pulsar_scene*
 
 /* Backward pass (App. B, "The Backward Pass"): given G = dL/dF, returns the
  * gradients through each pixel's tracked hits.  Outputs selected by grad_mask
- * are overwritten (zeroed in-stream first); the others may be NULL.
+ * are overwritten (zeroed in-stream first), or added into with
+ * PULSAR_FLAG_ACCUMULATE; the others may be NULL.
  *   image, log_norm   the forward outputs of the same call sequence
  *   grad_image        H x W x C upstream gradient
  *   g_pos M x 3, g_rad M, g_opa M, g_feat M x C, g_cam 11, g_bg C

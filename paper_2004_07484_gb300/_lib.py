@@ -18,6 +18,7 @@ FLAG_STORE_HITS = 1 << 0
 FLAG_DIST_LITERAL = 1 << 1
 FLAG_NO_MIN_SIZE = 1 << 2
 FLAG_PERSISTENT = 1 << 3
+FLAG_ACCUMULATE = 1 << 4
 
 GRAD_POS, GRAD_RAD, GRAD_OPA, GRAD_FEAT, GRAD_CAM, GRAD_BG = (1 << k for k in range(6))
 GRAD_ALL = 63
@@ -27,9 +28,13 @@ EXPORTED = ("pulsar_workspace_size", "pulsar_project", "pulsar_bin", "pulsar_ren
             "pulsar_status_string", "pulsar_render_fwd_static", "pulsar_workspace_size_batched",
             "pulsar_project_batched", "pulsar_bin_batched", "pulsar_render_fwd_batched",
             "pulsar_render_bwd_batched", "pulsar_read_tile_lists_batched",
-            "pulsar_probe_fma_throughput", "pulsar_last_overflow", "pulsar_render_batched")
+            "pulsar_probe_fma_throughput", "pulsar_last_overflow", "pulsar_render_batched",
+            "pulsar_image_loss", "pulsar_adam_step")
 
 MAX_SCENES = 64
+LOSS_L2, LOSS_L1 = 0, 1
+LOSS_SCRATCH_FLOATS = 1024
+ADAM_MAX_TENSORS = 8
 
 
 class Params(ctypes.Structure):
@@ -55,6 +60,19 @@ class FwdOut(ctypes.Structure):
 class BwdIO(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("image", "log_norm", "grad_image", "g_pos", "g_rad",
                                                "g_opa", "g_feat", "g_cam", "g_bg")]
+
+
+class AdamTensor(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("n", ctypes.c_int64), ("lo", ctypes.c_float), ("hi", ctypes.c_float)]
+
+
+class AdamHyper(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("zero_grad", ctypes.c_int32)]
+
+
+ADAM_STATE_BYTES = 16   # pulsar_adam_state: int32 t, float step_size, float inv_sqrt_bc2, int32
 
 
 class PulsarError(RuntimeError):
@@ -113,6 +131,10 @@ def lib():
         L.pulsar_probe_fma_throughput.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
                                                   ctypes.POINTER(ctypes.c_float), vp]
         L.pulsar_probe_fma_throughput.restype = ctypes.c_int
+        L.pulsar_image_loss.argtypes = [i32, vp, vp, ctypes.c_int64, ctypes.c_float, vp, vp, vp, vp]
+        L.pulsar_image_loss.restype = ctypes.c_int
+        L.pulsar_adam_step.argtypes = [i32, ctypes.POINTER(AdamTensor), ctypes.POINTER(AdamHyper), vp, vp]
+        L.pulsar_adam_step.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -228,3 +250,14 @@ def last_overflow(p: Params, ws: int, ws_bytes: int, stream: int) -> tuple[int, 
 
 def render_batched(ps, ss, ws: int, ws_bytes: int, outs, stream: int) -> None:
     _check(lib().pulsar_render_batched(len(ps), ps, ss, ws, ws_bytes, outs, stream), "pulsar_render_batched")
+
+
+def image_loss(kind: int, image: int, target: int, n: int, scale: float, grad: int | None,
+               loss: int | None, scratch: int, stream: int) -> None:
+    _check(lib().pulsar_image_loss(int(kind), image, target, int(n), float(scale), grad, loss, scratch, stream),
+           "pulsar_image_loss")
+
+
+def adam_step(tensors, hyper: AdamHyper, state: int, stream: int) -> None:
+    """`tensors`: ctypes array of AdamTensor."""
+    _check(lib().pulsar_adam_step(len(tensors), tensors, ctypes.byref(hyper), state, stream), "pulsar_adam_step")

@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(kThreads) zero_grads_kernel(WsView v, uint32_t
   v.gacc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   const int s = scene_of_sphere(v.scenes, v.n_scenes, i);
   const SceneDev& S = v.scenes[s];
+  if (S.flags & PULSAR_FLAG_ACCUMULATE) return;   // the caller's buffers are added into
   const int64_t li = i - S.sphere_begin;
   if (mask & PULSAR_GRAD_OPA) S.g_opa[li] = 0.0f;
   if (mask & PULSAR_GRAD_FEAT) {
@@ -208,12 +209,25 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(WsView v, ui
     float gp0 = B[0] * gc0 + B[3] * gc1 + B[6] * gc2;
     float gp1 = B[1] * gc0 + B[4] * gc1 + B[7] * gc2;
     float gp2 = B[2] * gc0 + B[5] * gc1 + B[8] * gc2;
+    const bool acc = (S.flags & PULSAR_FLAG_ACCUMULATE) != 0;
     if (mask & PULSAR_GRAD_POS) {
-      S.g_pos[3 * li] = gp0;
-      S.g_pos[3 * li + 1] = gp1;
-      S.g_pos[3 * li + 2] = gp2;
+      float* gp = S.g_pos + 3 * li;
+      if (acc) {
+        atomicAdd(gp, gp0);
+        atomicAdd(gp + 1, gp1);
+        atomicAdd(gp + 2, gp2);
+      } else {
+        gp[0] = gp0;
+        gp[1] = gp1;
+        gp[2] = gp2;
+      }
     }
-    if (mask & PULSAR_GRAD_RAD) S.g_rad[li] = grad_r;
+    if (mask & PULSAR_GRAD_RAD) {
+      if (acc)
+        atomicAdd(S.g_rad + li, grad_r);
+      else
+        S.g_rad[li] = grad_r;
+    }
     if (mask & PULSAR_GRAD_CAM) {
       float d0 = p[0] - S.cam[0], d1 = p[1] - S.cam[1], d2 = p[2] - S.cam[2];
       cam_part[0] = gc0 * d0; cam_part[1] = gc0 * d1; cam_part[2] = gc0 * d2;
@@ -295,6 +309,7 @@ __global__ void __launch_bounds__(256) camera_partials_kernel(WsView v, uint32_t
 // and the Gram-Schmidt map of the 6D rotation.
 __global__ void __launch_bounds__(64) camera_reduce_kernel(WsView v, uint32_t mask) {
   __shared__ float tot[kRedValues];
+  __shared__ float gcam[11];
   const SceneDev& S = v.scenes[blockIdx.x];
   const int C = S.n_channels;
   if (threadIdx.x < kRedValues) {
@@ -302,7 +317,12 @@ __global__ void __launch_bounds__(64) camera_reduce_kernel(WsView v, uint32_t ma
     for (int p = 0; p < kRedParts; ++p)
       x += v.red_part[((size_t)blockIdx.x * kRedParts + p) * kRedValues + threadIdx.x];
     tot[threadIdx.x] = x;
-    if ((mask & PULSAR_GRAD_BG) && threadIdx.x >= 13 && threadIdx.x < 13 + C) S.g_bg[threadIdx.x - 13] = x;
+    if ((mask & PULSAR_GRAD_BG) && threadIdx.x >= 13 && threadIdx.x < 13 + C) {
+      if (S.flags & PULSAR_FLAG_ACCUMULATE)
+        atomicAdd(S.g_bg + threadIdx.x - 13, x);
+      else
+        S.g_bg[threadIdx.x - 13] = x;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0 && (mask & PULSAR_GRAD_CAM)) {
@@ -338,13 +358,19 @@ __global__ void __launch_bounds__(64) camera_reduce_kernel(WsView v, uint32_t ma
     float pa = dot3(b1, gb1);
     float ga1[3];
     for (int k = 0; k < 3; ++k) ga1[k] = (gb1[k] - b1[k] * pa) / n1;
-    float* out = S.g_cam;
-    out[0] = tot[9]; out[1] = tot[10]; out[2] = tot[11];
-    out[3] = ga1[0]; out[4] = ga1[1]; out[5] = ga1[2];
-    out[6] = ga2[0]; out[7] = ga2[1]; out[8] = ga2[2];
     const float f = S.cam[9];
-    out[9] = -tot[12] * S.kappa / f;
-    out[10] = tot[12] / ((float)S.width * f);
+    gcam[0] = tot[9]; gcam[1] = tot[10]; gcam[2] = tot[11];
+    gcam[3] = ga1[0]; gcam[4] = ga1[1]; gcam[5] = ga1[2];
+    gcam[6] = ga2[0]; gcam[7] = ga2[1]; gcam[8] = ga2[2];
+    gcam[9] = -tot[12] * S.kappa / f;
+    gcam[10] = tot[12] / ((float)S.width * f);
+  }
+  __syncthreads();
+  if ((mask & PULSAR_GRAD_CAM) && threadIdx.x < 11) {
+    if (S.flags & PULSAR_FLAG_ACCUMULATE)
+      atomicAdd(S.g_cam + threadIdx.x, gcam[threadIdx.x]);
+    else
+      S.g_cam[threadIdx.x] = gcam[threadIdx.x];
   }
 }
 

@@ -291,7 +291,10 @@ __device__ __forceinline__ ValueRay value_ray(int u, int v, int width, int heigh
 // the sphere radius even where |c| is large.
 struct ValueGeom {
   float ex, ey, ez;   // c x r = (-ey, ex, ez)
-  float cr2, rr, sq, off, dist;
+  float cr2, rr;      // |c x r|^2, |r|^2
+  float qd;           // dist / R
+  float sq;           // sqrt(|r|^2 R^2 - |c x r|^2) = sqrt(disc)
+  float off;          // c_z - t_h
 };
 
 // Value-path square root and quotient: hardware approximations (about 2 ulp),
@@ -299,43 +302,27 @@ struct ValueGeom {
 __device__ __forceinline__ float vsqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 __device__ __forceinline__ float vdiv(float a, float b) { return __fdividef(a, b); }
 
+// The forward pass blends with these values and the backward pass
+// differentiates the same ones: every operation that sets dist / R and the
+// depth offset is an explicitly rounded intrinsic, so the compiler fuses none
+// of them differently in the two kernels and both passes see bit-identical
+// d and z.  (At the rim, d = 1 - dist/R is a difference of nearly equal
+// numbers; two differently rounded evaluations would differ in d by a large
+// relative amount there, and the backward pass's weight a'/D' would no longer
+// match the forward pass's denominator.)  dist / R = sqrt(|c x r|^2 /
+// (|r|^2 R^2)) takes one correctly rounded division and square root.
 __device__ __forceinline__ ValueGeom value_geom(const float4& a, const float4& c2, const ValueRay& r) {
   ValueGeom g;
-  g.ex = fmaf(a.z, r.rx, -a.x) + fmaf(a.z, r.rx_lo, fmaf(c2.z, r.rx, -c2.x));
-  g.ey = fmaf(a.z, r.ry, -a.y) + fmaf(a.z, r.ry_lo, fmaf(c2.z, r.ry, -c2.y));
-  // d = 1 - dist/R is ill-conditioned at the rim, where a sphere blending
-  // with what lies behind it makes the image change like 1/d: the terms that
-  // set dist use correctly rounded division and square root.
-  g.ez = fmaf(a.x, g.ey, -a.y * g.ex) / a.z;
-  g.cr2 = fmaf(g.ex, g.ex, fmaf(g.ey, g.ey, g.ez * g.ez));
-  g.rr = fmaf(r.rx, r.rx, fmaf(r.ry, r.ry, 1.0f));
+  g.ex = __fadd_rn(__fmaf_rn(a.z, r.rx, -a.x), __fmaf_rn(a.z, r.rx_lo, __fmaf_rn(c2.z, r.rx, -c2.x)));
+  g.ey = __fadd_rn(__fmaf_rn(a.z, r.ry, -a.y), __fmaf_rn(a.z, r.ry_lo, __fmaf_rn(c2.z, r.ry, -c2.y)));
+  g.ez = __fdiv_rn(__fmaf_rn(a.x, g.ey, -__fmul_rn(a.y, g.ex)), a.z);
+  g.cr2 = __fmaf_rn(g.ex, g.ex, __fmaf_rn(g.ey, g.ey, __fmul_rn(g.ez, g.ez)));
+  g.rr = __fmaf_rn(r.rx, r.rx, __fmaf_rn(r.ry, r.ry, 1.0f));
   const float R = c2.w;
-  g.sq = vsqrt(fmaf(g.rr, R * R, -g.cr2));
-  g.off = vdiv(fmaf(r.rx, g.ex, fmaf(r.ry, g.ey, g.sq)), g.rr);
-  g.dist = sqrtf(g.cr2 / g.rr);
-  return g;
-}
-
-// The forward pass's value path: dist / R and the depth offset only.  dist/R
-// = sqrt(|c x r|^2 / (|r|^2 R^2)) takes one correctly rounded division and
-// square root.
-struct ValueFwd {
-  float qd;    // dist / R
-  float off;   // c_z - t_h
-};
-
-__device__ __forceinline__ ValueFwd value_fwd(const float4& a, const float4& c2, const ValueRay& r) {
-  ValueFwd g;
-  const float ex = fmaf(a.z, r.rx, -a.x) + fmaf(a.z, r.rx_lo, fmaf(c2.z, r.rx, -c2.x));
-  const float ey = fmaf(a.z, r.ry, -a.y) + fmaf(a.z, r.ry_lo, fmaf(c2.z, r.ry, -c2.y));
-  const float ez = fmaf(a.x, ey, -a.y * ex) / a.z;
-  const float cr2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-  const float rr = fmaf(r.rx, r.rx, fmaf(r.ry, r.ry, 1.0f));
-  const float R = c2.w;
-  const float rR2 = rr * (R * R);
-  g.qd = sqrtf(cr2 / rR2);
-  const float sq = vsqrt(rR2 - cr2);
-  g.off = vdiv(fmaf(r.rx, ex, fmaf(r.ry, ey, sq)), rr);
+  const float R2 = __fmul_rn(R, R);
+  g.qd = __fsqrt_rn(__fdiv_rn(g.cr2, __fmul_rn(g.rr, R2)));
+  g.sq = vsqrt(__fmaf_rn(g.rr, R2, -g.cr2));
+  g.off = vdiv(__fmaf_rn(r.rx, g.ex, __fmaf_rn(r.ry, g.ey, g.sq)), g.rr);
   return g;
 }
 

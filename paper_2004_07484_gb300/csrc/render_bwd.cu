@@ -167,8 +167,8 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
       const ValueGeom g = value_geom(a, c2, pc.vr);
       const float R = c2.w;
       const float inv_rr = vdiv(1.0f, g.rr);
-      const float dist = g.dist;
-      const float qd = dist / R;
+      const float qd = g.qd;            // as the forward pass blended it
+      const float dist = qd * R;
       const float qdc = fminf(qd, 1.0f);
       const float d = literal ? qdc : 1.0f - qdc;
       const float z = (((zfar - a.z) - c2.z) + g.off) * inv_range;

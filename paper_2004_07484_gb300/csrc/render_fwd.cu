@@ -173,7 +173,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
       ++nhit;
       const int id = sb.id[cur][j];
       if (BLEND) {
-        const ValueFwd vg = value_fwd(a, c2, pc.vr);
+        const ValueGeom vg = value_geom(a, c2, pc.vr);
         const float qd = fminf(vg.qd, 1.0f);
         const float d = literal ? qd : 1.0f - qd;
         const float od = b.y * d;

@@ -35,6 +35,7 @@ class RenderSettings:
     tile: int = 16
     segment: int = 0                 # scheduling: list entries per work item (0 = library default)
     persistent: bool = False         # scheduling: persistent render kernels
+    accumulate: bool = False         # backward adds into the gradient buffers (views sharing them)
 
     def flags(self) -> int:
         f = 0
@@ -46,6 +47,8 @@ class RenderSettings:
             f |= _lib.FLAG_NO_MIN_SIZE
         if self.persistent:
             f |= _lib.FLAG_PERSISTENT
+        if self.accumulate:
+            f |= _lib.FLAG_ACCUMULATE
         return f
 
     def params(self, n_spheres: int, capacity: int) -> _lib.Params:
@@ -197,8 +200,12 @@ def forward_batch(settings: list[RenderSettings], inputs, capacities: list[int],
 
 
 def backward_batch(fr: BatchFrame, inputs, images, log_norms, grad_images,
-                   grad_mask: int = _lib.GRAD_ALL):
-    """Batched render_bwd.  Returns, per scene, the six gradients (None where not asked)."""
+                   grad_mask: int = _lib.GRAD_ALL, out=None):
+    """Batched render_bwd.  Returns, per scene, the six gradients (None where not asked).
+
+    ``out[s]``, when given, holds scene s's six gradient tensors (None where
+    not asked) and receives the result; with ``accumulate`` settings several
+    scenes may share them and the gradients are added into them."""
     dev = inputs[0][0].device
     stream = torch.cuda.current_stream(dev).cuda_stream
     ios = (_lib.BwdIO * len(inputs))()
@@ -209,8 +216,18 @@ def backward_batch(fr: BatchFrame, inputs, images, log_norms, grad_images,
         def alloc(flag, shape):
             return torch.empty(shape, dtype=torch.float32, device=dev) if grad_mask & flag else None
 
-        g = (alloc(_lib.GRAD_POS, (M, 3)), alloc(_lib.GRAD_RAD, (M,)), alloc(_lib.GRAD_OPA, (M,)),
-             alloc(_lib.GRAD_FEAT, (M, C)), alloc(_lib.GRAD_CAM, (11,)), alloc(_lib.GRAD_BG, (C,)))
+        if out is not None:
+            g = tuple(out[k])
+            shapes = ((M, 3), (M,), (M,), (M, C), (11,), (C,))
+            for t, shape, flag in zip(g, shapes, (_lib.GRAD_POS, _lib.GRAD_RAD, _lib.GRAD_OPA,
+                                                  _lib.GRAD_FEAT, _lib.GRAD_CAM, _lib.GRAD_BG)):
+                if grad_mask & flag:
+                    _dev_f32("gradient output", t, shape)
+                    if not t.is_contiguous():
+                        raise ValueError("gradient outputs must be contiguous")
+        else:
+            g = (alloc(_lib.GRAD_POS, (M, 3)), alloc(_lib.GRAD_RAD, (M,)), alloc(_lib.GRAD_OPA, (M,)),
+                 alloc(_lib.GRAD_FEAT, (M, C)), alloc(_lib.GRAD_CAM, (11,)), alloc(_lib.GRAD_BG, (C,)))
         grads.append(g)
         ios[k] = _lib.BwdIO(images[k].data_ptr(), log_norms[k].data_ptr(), grad_images[k].data_ptr(),
                             *[_ptr(t) for t in g])

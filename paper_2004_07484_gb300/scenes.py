@@ -179,6 +179,32 @@ def batch_scenes(seed: int, n_scenes: int = 32, n_channels: int = 8, n_track: in
     return scenes
 
 
+def orbit_cameras(seed: int, centre, n_views: int = 4, distance: float = 8.0, focal: float = 1.0,
+                  sensor_width: float = 2.0) -> list[np.ndarray]:
+    """Cameras at random rotations about ``centre``, each ``distance`` behind it
+    on its own optical axis (the views of the scene fit)."""
+    g = _rng(seed)
+    c = np.asarray(centre, dtype=np.float64)
+    cams = []
+    for _ in range(n_views):
+        rows = random_rotation(g).T
+        cams.append(make_cam(t=c - distance * rows[2], rot6=rot6_from_matrix(rows), focal=focal,
+                             sensor_width=sensor_width))
+    return cams
+
+
+def perturbed(scene: Scene, seed: int, pos_sigma: float = 0.05, rad_frac: float = 0.3) -> Scene:
+    """Initial guess of the scene fit: positions + N(0, pos_sigma^2), radii
+    times U[1 - rad_frac, 1 + rad_frac]; opacities, features and camera kept."""
+    g = _rng(seed)
+    n = scene.n_spheres
+    pos = scene.pos.astype(np.float64) + pos_sigma * g.standard_normal((n, 3))
+    rad = scene.rad.astype(np.float64) * g.uniform(1.0 - rad_frac, 1.0 + rad_frac, n)
+    return Scene(_f32(pos), _f32(rad), scene.opa.copy(), scene.feat.copy(), scene.cam.copy(), scene.bg.copy(),
+                 scene.width, scene.height, scene.gamma, scene.n_track, scene.eps, scene.znear, scene.zfar,
+                 name=scene.name + "_perturbed")
+
+
 def config_scene(index: int, gamma: float | None = None, n: int | None = None,
                  res: int | None = None) -> Scene:
     """The synthetic stand-in for each benchmark workload, seeded with 1000 + index.

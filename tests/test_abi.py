@@ -128,3 +128,32 @@ def test_batched_entry_points_reject_bad_arguments_on_the_host(lib):
     assert L.pulsar_render_fwd_batched(2, ps, ss, 256, n, outs, None) == lib.ERR_INVALID_ARG
     ios = (lib.BwdIO * 2)()
     assert L.pulsar_render_bwd_batched(2, ps, ss, 256, n, ios, lib.GRAD_ALL, None) == lib.ERR_INVALID_ARG
+
+
+def test_fit_entry_points_reject_bad_arguments_on_the_host(lib):
+    L = lib.lib()
+    # image loss: unknown kind, negative size, missing buffers
+    assert L.pulsar_image_loss(7, 256, 256, 4, 1.0, None, None, 256, None) == lib.ERR_INVALID_ARG
+    assert L.pulsar_image_loss(lib.LOSS_L2, 256, 256, -1, 1.0, None, None, 256, None) == lib.ERR_INVALID_ARG
+    assert L.pulsar_image_loss(lib.LOSS_L1, None, 256, 4, 1.0, None, None, 256, None) == lib.ERR_INVALID_ARG
+    assert L.pulsar_image_loss(lib.LOSS_L1, 256, 256, 4, 1.0, None, None, None, None) == lib.ERR_INVALID_ARG
+    # Adam: tensor count, hyper-parameters, tensor descriptors
+    inf = float("inf")
+    good = lib.AdamTensor(256, 512, 768, 1024, 10, -inf, inf)
+    ts = (lib.AdamTensor * 1)(good)
+    hp = lib.AdamHyper(1e-3, 0.9, 0.999, 1e-8, 1)
+    assert L.pulsar_adam_step(0, ts, ctypes.byref(hp), 256, None) == lib.ERR_INVALID_ARG
+    assert L.pulsar_adam_step(lib.ADAM_MAX_TENSORS + 1, ts, ctypes.byref(hp), 256, None) == lib.ERR_INVALID_ARG
+    assert L.pulsar_adam_step(1, ts, ctypes.byref(hp), None, None) == lib.ERR_INVALID_ARG
+    for bad in (lib.AdamHyper(-1.0, 0.9, 0.999, 1e-8, 1), lib.AdamHyper(1e-3, 1.0, 0.999, 1e-8, 1),
+                lib.AdamHyper(1e-3, 0.9, -0.1, 1e-8, 1), lib.AdamHyper(1e-3, 0.9, 0.999, -1.0, 1),
+                lib.AdamHyper(float("nan"), 0.9, 0.999, 1e-8, 1)):
+        assert L.pulsar_adam_step(1, ts, ctypes.byref(bad), 256, None) == lib.ERR_INVALID_ARG
+    for bad in (lib.AdamTensor(256, 512, 768, 1024, -1, -inf, inf),
+                lib.AdamTensor(256, 512, 768, 1024, 10, 1.0, 0.0),
+                lib.AdamTensor(256, None, 768, 1024, 10, -inf, inf),
+                lib.AdamTensor(256, 512, 768, 1024, 10, float("nan"), inf)):
+        assert L.pulsar_adam_step(1, (lib.AdamTensor * 1)(bad), ctypes.byref(hp), 256, None) == lib.ERR_INVALID_ARG
+    # the accumulate flag is a valid setting
+    assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=lib.FLAG_ACCUMULATE))) > 0
+    assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=1 << 5))) == 0
