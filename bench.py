@@ -297,6 +297,66 @@ def bench_batched(dev, steps: int, warmup: int, flush):
             "steps": k, "l2": "flushed between steps (256 MB write, untimed)"}
 
 
+def bench_batched_headline(dev, steps: int, warmup: int, flush, n_renders: int = 4):
+    """The headline workload batched: n_renders different 1M-sphere, 1024x1024
+    scenes (same distribution, own seeds) rendered and back-propagated as one
+    batch with autotuned scheduling, eagerly and as a CUDA-graph replay;
+    renders/s = n_renders / step."""
+    import torch
+    from paper_2004_07484_gb300 import autotune, backward_batch, forward_batch, RenderSettings, scenes
+    scs = [scenes.config_scene(2) if k == 0 else
+           scenes.ellipsoid_surfaces(1002 + 7919 * k, 1_000_000, 1024, 1024, n_channels=16, gamma=1e-2,
+                                     n_track=16) for k in range(n_renders)]
+    inputs = [tuple(torch.from_numpy(np.ascontiguousarray(getattr(sc, k))).to(dev)
+                    for k in ("pos", "feat", "rad", "opa", "cam", "bg")) for sc in scs]
+    g = np.random.default_rng(13)
+    grads = [torch.from_numpy(g.standard_normal((sc.height, sc.width, sc.n_channels)).astype(np.float32)).to(dev)
+             for sc in scs]
+    sets = [RenderSettings(sc.width, sc.height, sc.n_channels, sc.n_track, sc.gamma, sc.eps, sc.znear, sc.zfar,
+                           store_hits=True) for sc in scs]
+    choice = autotune.tune(sets, inputs, grads)
+    tuned = autotune.apply(sets, choice)
+    caps = choice.capacities
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        fr, images, log_norms = forward_batch(tuned, inputs, caps, check_overflow=False)
+        backward_batch(fr, inputs, images, log_norms, grads)
+
+    def timed(fn, k):
+        ms = []
+        for i in range(k):
+            flush.fill_(i & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    for _ in range(max(warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    k = max(3, min(steps, 20))
+    eager_ms = timed(step, k)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        step()
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    graph_ms = timed(graph.replay, k)
+    return {"workload": f"{n_renders} different scenes of the headline workload (1M spheres, 1024x1024, "
+                        "own seeds) as one batch", "renders_per_step": n_renders,
+            "batched_renders_per_s": n_renders * 1e3 / eager_ms, "graph_renders_per_s": n_renders * 1e3 / graph_ms,
+            "batched_ms_per_step": eager_ms, "graph_ms_per_step": graph_ms,
+            "autotune": {"segment": choice.segment, "persistent": choice.persistent}, "steps": k,
+            "l2": "flushed between steps (256 MB write, untimed)"}
+
+
 FIT_METRIC = "scene-fit steps/sec (4 views fwd+bwd + Adam) at 5M spheres 1920x1080"
 FIT_WORKLOAD = ("scene fit: 5M spheres on 20 ellipsoid surfaces (hidden scene), 1920x1080, C=3 U[0,1], "
                 "gamma=1e-2, n_track=8, 4 views at random rotations about the centroid (distance 8), "
@@ -362,6 +422,16 @@ def bench_fit(args):
         vf.state.zero_()
 
     initial = float(vf.evaluate().item())
+    if args.profile_step:
+        for _ in range(max(args.warmup, 3)):
+            vf.step()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("pulsar_step")
+        vf.step()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": "done", "workload": "scene fit", "capacities": vf.capacities()}))
+        return
     vf.capture()
     for _ in range(max(args.warmup, 3)):
         vf.replay()
@@ -681,6 +751,9 @@ def main():
                 "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "dominant": dominant,
                 "ray_tests": tests, "hits": hits, "pairs": pairs_needed}
     batched = None if args.no_batched else bench_batched(dev, args.steps, args.warmup, flush)
+    batched_headline = None
+    if not args.no_batched and args.config == 2 and args.spheres is None and args.res is None:
+        batched_headline = bench_batched_headline(dev, args.steps, args.warmup, flush)
     cpu = None
     if not args.no_cpu_baseline:
         dt, frac = cpu_oracle_sample(sc, 16)
@@ -711,7 +784,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": (launches_store * args.steps + launches_rec * len(ms_rec)) if not args.recompute
             else (launches_rec * args.steps + launches_store * len(ms_rec)),
-            "wall_s_timed": t_wall, "batched": batched,
+            "wall_s_timed": t_wall, "batched": batched, "batched_headline": batched_headline,
             "autotune": {"segment": tuned.segment, "persistent": tuned.persistent,
                          "candidates_ms": {f"{a}/{'persistent' if b else 'per-unit'}": v
                                            for (a, b), v in tuned.ms.items()}}}
