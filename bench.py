@@ -297,7 +297,7 @@ def bench_batched(dev, steps: int, warmup: int, flush):
             "steps": k, "l2": "flushed between steps (256 MB write, untimed)"}
 
 
-def bench_batched_headline(dev, steps: int, warmup: int, flush, n_renders: int = 4):
+def bench_batched_headline(dev, steps: int, warmup: int, flush, n_renders: int = 4, profile: bool = False):
     """The headline workload batched: n_renders different 1M-sphere, 1024x1024
     scenes (same distribution, own seeds) rendered and back-propagated as one
     batch with autotuned scheduling, eagerly and as a CUDA-graph replay;
@@ -338,6 +338,12 @@ def bench_batched_headline(dev, steps: int, warmup: int, flush, n_renders: int =
     for _ in range(max(warmup, 3)):
         step()
     torch.cuda.synchronize(dev)
+    if profile:
+        torch.cuda.nvtx.range_push("pulsar_step")
+        step()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize(dev)
+        return {"profile_step": "done", "renders": n_renders}
     k = max(3, min(steps, 20))
     eager_ms = timed(step, k)
     side = torch.cuda.Stream(dev)
@@ -524,6 +530,8 @@ def main():
                     help="warm up, run one step inside the NVTX range 'pulsar_step' and exit (for ncu)")
     ap.add_argument("--spheres", type=int, default=None, help="override the sphere count (profiling)")
     ap.add_argument("--res", type=int, default=None, help="override the square resolution (profiling)")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="with --profile-step: profile the headline workload as a batch of this many scenes")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -609,6 +617,10 @@ def main():
         step(True, False)
         step(False, False)
     torch.cuda.synchronize()
+    if args.profile_step and args.profile_batch > 0:
+        if rank == 0:
+            print(json.dumps(bench_batched_headline(dev, 1, args.warmup, flush, args.profile_batch, profile=True)))
+        return
     if args.profile_step:
         torch.cuda.nvtx.range_push("pulsar_step")
         step(not args.recompute, True)

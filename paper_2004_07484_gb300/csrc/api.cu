@@ -15,7 +15,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t hdr, scenes, rec0, rec1, rec2, key0, key1, val0, val1, hist, block_sums, pkey0, pkey1, pval0,
-      pval1, radix_tot, ranges, item_begin, item_desc, item_order, unit_list, unit_count, unit_tests, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
+      pval1, radix_tot, ranges, item_begin, item_desc, item_order, unit_list, unit_count, unit_cost, unit_order, unit_tests, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
       gacc, fin_part, red_part, total;
   int64_t n_spheres, n_tiles, n_pixels, capacity, max_items;
   int32_t sort_blocks, fin_blocks, tile_bits, segment, part_fields;
@@ -103,6 +103,8 @@ Layout make_layout(const pulsar_params* ps, int n) {
   // block lists: per pixel block, one slot per pair of capacity; per work unit a count
   L.unit_list = take(8 * 8 * (size_t)cap);
   L.unit_count = take(4 * 8 * (size_t)L.max_items);
+  L.unit_cost = take(4 * 8 * (size_t)L.max_items);
+  L.unit_order = take(4 * 8 * (size_t)L.max_items);
   L.unit_tests = take(4 * 8 * 32 * (size_t)L.max_items);
   // per (tile or work item) x 8 pixel blocks of 32 pixels
   L.tile_done = take(4 * 8 * (size_t)NT);
@@ -158,6 +160,8 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.item_order = reinterpret_cast<int32_t*>(b + L.item_order);
   v.unit_list = reinterpret_cast<uint2*>(b + L.unit_list);
   v.unit_count = reinterpret_cast<int32_t*>(b + L.unit_count);
+  v.unit_cost = reinterpret_cast<uint32_t*>(b + L.unit_cost);
+  v.unit_order = reinterpret_cast<int32_t*>(b + L.unit_order);
   v.unit_tests = reinterpret_cast<int32_t*>(b + L.unit_tests);
   v.tile_done = reinterpret_cast<int32_t*>(b + L.tile_done);
   v.partial = reinterpret_cast<float*>(b + L.partial);

@@ -36,7 +36,7 @@ struct BlockListWarp {
 // appends the entries with hits, in order, to out (n entries so far).
 __device__ __forceinline__ void block_batch(BlockListWarp& W, int cnt, const WsView& v, const SceneDev& S,
                                             const WarpRect& wr, const uint32_t* __restrict__ list,
-                                            uint2* out, int& n) {
+                                            uint2* out, int& n, uint32_t& hits) {
   const int lane = threadIdx.x & 31;
   uint32_t id = 0u;
   int ntest = 0;
@@ -76,6 +76,7 @@ __device__ __forceinline__ void block_batch(BlockListWarp& W, int cnt, const WsV
   const uint32_t bal = __ballot_sync(0xffffffffu, hm != 0u);
   if (hm) out[n + __popc(bal & lane_lt_mask())] = make_uint2(id, hm);
   n += __popc(bal);
+  hits += __popc(hm);
   __syncwarp();   // the batch's shared data is rewritten next
 }
 
@@ -88,7 +89,9 @@ __global__ void __launch_bounds__(32 * kListWarps) block_lists_kernel(const WsVi
                                                                        const uint32_t* __restrict__ list) {
   __shared__ BlockListWarp warps[kListWarps];
   constexpr int kCtasPerItem = kBlocksPerTile / kListWarps;
-  const int item = blockIdx.x / kCtasPerItem;
+  const int rank = blockIdx.x / kCtasPerItem;   // longest items first
+  if (rank >= v.hdr->n_items) return;
+  const int item = v.item_order[rank];
   const int block = (blockIdx.x % kCtasPerItem) * kListWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   BlockListWarp& W = warps[threadIdx.x >> 5];
@@ -100,6 +103,7 @@ __global__ void __launch_bounds__(32 * kListWarps) block_lists_kernel(const WsVi
   uint2* out = v.unit_list + (size_t)it.block * v.capacity + it.b0;
   const uint32_t mine = 1u << (kTileKeyBits + block);
   int n = 0, pending = 0;
+  uint32_t hits = 0u;   // this lane's share of the unit's pixel hits
   uint32_t key_next = it.b0 + lane < it.b1 ? __ldg(keys + it.b0 + lane) : 0u;
   for (int base = it.b0; base < it.b1; base += 32) {
     const uint32_t key = key_next;
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(32 * kListWarps) block_lists_kernel(const WsVi
     pending += __popc(bal);
     if (pending >= 32) {
       __syncwarp();
-      block_batch(W, 32, v, S, wr, list, out, n);
+      block_batch(W, 32, v, S, wr, list, out, n, hits);
       const int rest = pending - 32;
       if (lane < rest) W.pos[lane] = W.pos[32 + lane];
       pending = rest;
@@ -120,9 +124,45 @@ __global__ void __launch_bounds__(32 * kListWarps) block_lists_kernel(const WsVi
   }
   if (pending > 0) {
     __syncwarp();
-    block_batch(W, pending, v, S, wr, list, out, n);
+    block_batch(W, pending, v, S, wr, list, out, n, hits);
   }
-  if (lane == 0) v.unit_count[item * kBlocksPerTile + it.block] = n;
+  hits = __reduce_add_sync(0xffffffffu, hits);
+  if (lane == 0) {
+    v.unit_count[item * kBlocksPerTile + it.block] = n;
+    v.unit_cost[item * kBlocksPerTile + it.block] = (uint32_t)n + hits;
+  }
+}
+
+// Launch order of the render passes' work units: decreasing cost (block-list
+// length plus pixel hits), by a counting sort over kCostClasses logarithmic
+// cost classes (four per octave; the order within a class is arbitrary).
+constexpr int kCostClasses = 64;
+
+__device__ __forceinline__ int cost_class(uint32_t c) {
+  if (c < 4u) return kCostClasses - 1 - (int)c;
+  const int lg = 31 - __clz(c);                            // >= 2
+  const int cls = 4 * lg - 4 + (int)((c >> (lg - 2)) & 3u);  // 4 .. 4 * 31 - 1
+  return max(kCostClasses - 1 - cls, 0);
+}
+
+__global__ void __launch_bounds__(1024) order_units_kernel(const WsView v) {
+  __shared__ uint32_t bucket[kCostClasses];
+  const uint32_t n = (uint32_t)v.hdr->n_items * kBlocksPerTile;
+  if (threadIdx.x < kCostClasses) bucket[threadIdx.x] = 0u;
+  __syncthreads();
+  for (uint32_t u = threadIdx.x; u < n; u += 1024) atomicAdd(&bucket[cost_class(v.unit_cost[u])], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = 0; b < kCostClasses; ++b) {
+      const uint32_t c = bucket[b];
+      bucket[b] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (uint32_t u = threadIdx.x; u < n; u += 1024)
+    v.unit_order[atomicAdd(&bucket[cost_class(v.unit_cost[u])], 1u)] = (int32_t)u;
 }
 
 // The n_tests diagnostic: per work unit and pixel, the spheres of the
@@ -161,6 +201,7 @@ cudaError_t launch_block_lists(const WsView& v, cudaStream_t st) {
   if (v.max_items == 0) return cudaSuccess;
   block_lists_kernel<<<(unsigned)v.max_items * (kBlocksPerTile / kListWarps), 32 * kListWarps, 0, st>>>(
       v, v.pkey[v.pair_buf], v.pval[v.pair_buf]);
+  order_units_kernel<<<1, 1024, 0, st>>>(v);
   return cudaGetLastError();
 }
 

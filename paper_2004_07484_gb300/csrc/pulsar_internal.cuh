@@ -134,9 +134,11 @@ struct WsView {
   int2* ranges;              // per tile [begin, end)
   int32_t* item_begin;       // per tile (+1): first work item
   ItemDesc* item_desc;       // per work item
-  int32_t* item_order;       // work items by decreasing segment length (launch order)
+  int32_t* item_order;       // work items by decreasing segment length (block-list launch order)
   uint2* unit_list;          // block lists: [pixel block][capacity] (sphere, hit mask)
   int32_t* unit_count;       // per work unit (item x 8 + block): block-list length
+  uint32_t* unit_cost;       // per work unit: block-list length + pixel hits in its masks
+  int32_t* unit_order;       // work units by decreasing cost (render-pass launch order)
   int32_t* unit_tests;       // per work unit x 32 pixels: rectangle tests made
   int32_t* tile_done;        // per tile: finished segments (last-finisher merge)
   float* partial;            // per work item: partial forward state, [field][pixel]

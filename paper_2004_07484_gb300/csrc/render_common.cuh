@@ -58,12 +58,13 @@ __device__ __forceinline__ bool item_ctx_direct(const WsView& v, int item, int b
   return true;
 }
 
-// Work unit w of a render pass: pixel block w % 8 of the (w / 8)-th longest
-// work item.
+// Work unit w of a render pass: the w-th most costly (item, pixel block)
+// unit by its block list (length plus pixel hits), so that the longest units
+// start first and the passes end with short ones.
 __device__ __forceinline__ bool item_ctx(const WsView& v, int w, ItemCtx& c) {
-  const int rank = w / kBlocksPerTile;
-  if (rank >= v.hdr->n_items) return false;
-  return item_ctx_direct(v, v.item_order[rank], w % kBlocksPerTile, c);
+  if (w >= v.hdr->n_items * kBlocksPerTile) return false;
+  const int u = v.unit_order[w];
+  return item_ctx_direct(v, u / kBlocksPerTile, u % kBlocksPerTile, c);
 }
 
 // Next work unit of a persistent render kernel (one atomic per warp).
