@@ -156,25 +156,10 @@ __global__ void __launch_bounds__(kThreads) zero_grads_kernel(WsView v, uint32_t
   }
 }
 
-__device__ __forceinline__ float block_sum(float x, float* sh) {
-  x = warp_sum(x);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) sh[warp] = x;
-  __syncthreads();
-  float r = 0.0f;
-  if (warp == 0) {
-    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0f;
-    r = warp_sum(r);
-  }
-  return r;   // valid in thread 0
-}
-
 // One thread per sphere: dL/dc and dL/dR from the pixel pass become dL/dp,
 // dL/dr and the sphere's camera contribution (App. B: camera gradients are
 // gathered per sphere and reduced device-wide afterwards).
 __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(WsView v, uint32_t mask) {
-  __shared__ float sh[32];
   const int blk = blockIdx.x;
   int s = 0;
   for (int k = 1; k < v.n_scenes; ++k)
@@ -238,10 +223,20 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(WsView v, ui
     }
   }
   if (mask & PULSAR_GRAD_CAM) {
+    // the 13 sums at once: warp sums into shared memory, one barrier, then
+    // thread k adds up the warps' k-th sums
+    __shared__ float part[kFinalizeThreads / 32][13];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < 13; ++k) {
-      float t = block_sum(cam_part[k], sh);
-      if (threadIdx.x == 0) v.fin_part[(size_t)blk * kCamPartials + k] = t;
+      const float t = warp_sum(cam_part[k]);
+      if (lane == 0) part[warp][k] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 13) {
+      float t = 0.0f;
+      for (int w = 0; w < kFinalizeThreads / 32; ++w) t += part[w][threadIdx.x];
+      v.fin_part[(size_t)blk * kCamPartials + threadIdx.x] = t;
     }
   }
 }
