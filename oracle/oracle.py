@@ -28,7 +28,7 @@ class OrcParams(ctypes.Structure):
         ("width", ctypes.c_int32), ("height", ctypes.c_int32),
         ("n_spheres", ctypes.c_int32), ("n_channels", ctypes.c_int32),
         ("n_track", ctypes.c_int32), ("tile", ctypes.c_int32),
-        ("min_size", ctypes.c_int32), ("dist_literal", ctypes.c_int32),
+        ("min_size", ctypes.c_int32), ("dist_literal", ctypes.c_int32), ("paper_grad", ctypes.c_int32),
         ("gamma", ctypes.c_double), ("eps", ctypes.c_double),
         ("znear", ctypes.c_double), ("zfar", ctypes.c_double),
     ]
@@ -85,10 +85,10 @@ def _d(a) -> np.ndarray:
 
 
 def params(scene, tile: int = 16, min_size: bool = True, dist_literal: bool = False,
-           n_track: int | None = None) -> OrcParams:
+           n_track: int | None = None, paper_grad: bool = False) -> OrcParams:
     return OrcParams(int(scene.width), int(scene.height), int(scene.pos.shape[0]),
                      int(scene.feat.shape[1]), int(n_track if n_track is not None else scene.n_track),
-                     int(tile), int(bool(min_size)), int(bool(dist_literal)),
+                     int(tile), int(bool(min_size)), int(bool(dist_literal)), int(bool(paper_grad)),
                      float(np.float32(scene.gamma)), float(np.float32(scene.eps)),
                      float(np.float32(scene.znear)), float(np.float32(scene.zfar)))
 
@@ -189,9 +189,11 @@ class Gradients:
 
 
 def render_backward(scene, grad: np.ndarray, n_track: int | None = None, min_size: bool = True,
-                    dist_literal: bool = False, **override) -> Gradients:
-    """Analytic gradients of L = <grad, F> through the tracked hits."""
-    p = params(scene, n_track=n_track, min_size=min_size, dist_literal=dist_literal)
+                    dist_literal: bool = False, paper_grad: bool = False, **override) -> Gradients:
+    """Analytic gradients of L = <grad, F> through the tracked hits; with
+    paper_grad, the paper's normalisations (per-pixel averaging, the 3-pixel
+    position gate, camera scaled by 1e-3)."""
+    p = params(scene, n_track=n_track, min_size=min_size, dist_literal=dist_literal, paper_grad=paper_grad)
     M, C = p.n_spheres, p.n_channels
     arrs = _scene_arrays(scene, **override)
     G = _d(grad)

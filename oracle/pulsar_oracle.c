@@ -39,6 +39,16 @@
  *               sphere index) are kept for the backward pass (App. B, Step 2
  *               and "Preparing for the Backward Pass"); all hits contribute to
  *               the image; gradients flow through the tracked hits only.
+ *   paper       optional gradient normalisations of App. B (end of "The
+ *   gradients   Backward Pass") and Sec. 3.2 / Sec. 6: every sphere gradient
+ *               is divided by n_i, the number of pixels at which sphere i is
+ *               a tracked hit; position and radius gradients are zero unless
+ *               the sphere's projected radius R / (c_z k) exceeds 3 pixels
+ *               (float32 decision); the camera gradient is the sum over
+ *               spheres of the averaged per-sphere terms weighted by the
+ *               sphere's area, taken as n_i pixels, times 1e-3 -- that is,
+ *               1e-3 times the plain camera gradient.  The background
+ *               gradient is unchanged.
  */
 #include <math.h>
 #include <stdint.h>
@@ -53,6 +63,7 @@ typedef struct {
   int32_t tile;          /* edge length of the square screen tiles of the tile lists */
   int32_t min_size;      /* 1: apply the one-pixel minimum size rule */
   int32_t dist_literal;  /* 1: d = min(1, dist/R) instead of 1 - min(1, dist/R) */
+  int32_t paper_grad;    /* 1: the paper's gradient normalisations (header) */
   double gamma, eps, znear, zfar;
 } orc_params;
 
@@ -469,6 +480,8 @@ void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
   double g = P->gamma, zr = P->zfar - P->znear;
   /* per-sphere accumulators: dL/dc (3), dL/dR (1) */
   double* gc = (double*)calloc((size_t)(M > 0 ? M : 1) * 4, sizeof(double));
+  /* paper gradients: pixels at which each sphere is a tracked hit */
+  int* n_px = (int*)calloc((size_t)(M > 0 ? M : 1), sizeof(int));
   double g_kappa = 0.0;
   memset(g_pos, 0, sizeof(double) * 3 * (size_t)M);
   memset(g_rad, 0, sizeof(double) * (size_t)M);
@@ -489,7 +502,9 @@ void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
         const double* G = grad + px * Cn;
         int nz = 0;
         for (int c = 0; c < Cn; ++c) nz |= G[c] != 0.0;
-        if (!nz) continue;  /* every contribution of this pixel is a multiple of G */
+        /* every contribution of this pixel is a multiple of G; the paper
+         * normalisation still counts the pixel's tracked hits */
+        if (!nz && !P->paper_grad) continue;
         int n = pixel_hits(P, &C, u, v, hits);
         double logD = blend_pixel(P, &C, u, v, hits, n, F, NULL);
         double wB = exp(P->eps / g - logD);
@@ -499,6 +514,11 @@ void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
         int nt = n < K ? n : K;
         for (int j = 0; j < nt; ++j) {
           int i = hits[j].id;
+          if (P->paper_grad) {
+#pragma omp atomic
+            n_px[i] += 1;
+          }
+          if (!nz) continue;
           const sph64* s = &C.sv[i];
           rayq q;
           ray_values(P, s, rx, ry, &q);
@@ -574,17 +594,27 @@ void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
     const sph64* s = &C.sv[i];
     double* a = gc + 4 * (size_t)i;
     if (!C.pj[i].visible) continue;
+    /* paper gradients: 1 / n_i, and positions and radii only for spheres of
+     * more than 3 pixels projected radius (float32 decision) */
+    double scale = 1.0, geo_scale = 1.0;
+    if (P->paper_grad) {
+      scale = 1.0 / (double)(n_px[i] > 1 ? n_px[i] : 1);
+      const float rpx = C.pj[i].R / (C.pj[i].cz * C.kappaf);
+      geo_scale = rpx > 3.0f ? scale : 0.0;
+      g_opa[i] *= scale;
+      for (int c = 0; c < Cn; ++c) g_feat[(size_t)i * Cn + c] *= scale;
+    }
     if (s->clamped) {
       double cn = sqrt(s->c[0] * s->c[0] + s->c[1] * s->c[1] + s->c[2] * s->c[2]);
       for (int k = 0; k < 3; ++k) a[k] += a[3] * 0.75 * C.kappa * s->c[k] / cn;
       g_kappa += a[3] * 0.75 * cn;
     } else {
-      g_rad[i] = a[3];
+      g_rad[i] = geo_scale * a[3];
     }
     double d[3] = {pos[3 * i] - cam[0], pos[3 * i + 1] - cam[1], pos[3 * i + 2] - cam[2]};
     for (int k = 0; k < 3; ++k) {
       double gp = C.B[k] * a[0] + C.B[3 + k] * a[1] + C.B[6 + k] * a[2];
-      g_pos[3 * i + k] = gp;
+      g_pos[3 * i + k] = geo_scale * gp;
       g_cam[k] -= gp;
     }
     for (int r = 0; r < 3; ++r)
@@ -604,7 +634,10 @@ void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
   /* kappa = s / (W f) */
   g_cam[9] = -g_kappa * C.kappa / cam[9];
   g_cam[10] = g_kappa / ((double)W * cam[9]);
+  if (P->paper_grad)
+    for (int k = 0; k < 11; ++k) g_cam[k] *= 1e-3;
   free(gc);
+  free(n_px);
   ctx_free(&C);
 }
 

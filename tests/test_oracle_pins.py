@@ -401,3 +401,40 @@ def test_untracked_hits_get_no_gradient(orc):
     untracked = np.setdiff1d(np.arange(sc.n_spheres), tracked)
     assert np.all(gr.opa[untracked] == 0) and np.all(gr.feat[untracked] == 0)
     assert np.any(gr.opa[tracked] != 0)
+
+
+# ---------------------------------------------------------------- paper gradient normalisations
+
+def test_paper_gradients_are_the_exact_ones_averaged_and_gated(orc):
+    """The paper mode (App. B, end of "The Backward Pass"; Sec. 6) against the
+    exact gradients, which the finite-difference pins fix: sphere gradients
+    divided by the number of pixels at which the sphere is tracked (counted
+    here from the forward pass's tracked lists), positions and radii only for
+    spheres of more than 3 pixels projected radius, camera times 1e-3."""
+    from paper_2004_07484_gb300.scenes import uniform_cloud
+    sc = uniform_cloud(71, 60, 64, 48, n_channels=3, gamma=0.05, n_track=6, rad=(0.05, 1.2))
+    rng = np.random.default_rng(3)
+    G = rng.standard_normal((sc.height, sc.width, 3))
+    G[::5, ::3] = 0.0                       # pixels without upstream gradient still count
+    K = 6
+    exact = orc.render_backward(sc, G, n_track=K)
+    paper = orc.render_backward(sc, G, n_track=K, paper_grad=True)
+    fwd = orc.render(sc, n_track=K)
+    tr = fwd.tracked.reshape(-1)
+    n_px = np.bincount(tr[tr >= 0], minlength=sc.n_spheres).astype(np.float64)
+    n = np.maximum(n_px, 1.0)
+    pr = orc.project(sc)
+    kf = np.float32(sc.cam[10]) / (np.float32(sc.width) * np.float32(sc.cam[9]))
+    rpx = pr.R.astype(np.float32) / (pr.c[:, 2].astype(np.float32) * kf)
+    gate = rpx > np.float32(3.0)
+    seen = n_px > 0
+    assert (gate & seen).sum() >= 3 and (~gate & seen).sum() >= 3 and n_px.max() > 1
+    np.testing.assert_allclose(paper.opa * n, exact.opa, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(paper.feat * n[:, None], exact.feat, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(paper.pos * n[:, None], np.where(gate[:, None], exact.pos, 0.0), rtol=1e-12,
+                               atol=1e-15)
+    clamped = pr.R != sc.rad
+    want_rad = np.where(gate & ~clamped, exact.rad, 0.0)
+    np.testing.assert_allclose(paper.rad * n, want_rad, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(paper.cam, 1e-3 * exact.cam, rtol=1e-12, atol=1e-18)
+    np.testing.assert_allclose(paper.bg, exact.bg, rtol=1e-12)
