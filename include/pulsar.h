@@ -78,7 +78,16 @@ enum {
    * of one sphere set, rendered as a batch, accumulate the gradient of a loss
    * summed over views (Sec. 3.4).  Every output is added with atomics, so
    * shared buffers are safe; the summation order is unspecified. */
-  PULSAR_FLAG_ACCUMULATE = 1u << 4
+  PULSAR_FLAG_ACCUMULATE = 1u << 4,
+  /* The paper's gradient normalisations (App. B, end of "The Backward Pass";
+   * Sec. 6), in place of the plain gradients: every sphere gradient is
+   * divided by the number of pixels at which the sphere is a tracked hit;
+   * position and radius gradients are zero unless the sphere's projected
+   * radius R / (c_z k) exceeds 3 pixels; the camera gradient is the
+   * area-weighted sum of the averaged per-sphere terms times 1e-3, which with
+   * the area taken as the sphere's tracked pixels is 1e-3 times the plain
+   * camera gradient.  The background gradient is unchanged. */
+  PULSAR_FLAG_PAPER_GRADIENTS = 1u << 5
 };
 
 /* grad_mask bits of pulsar_render_bwd: gradients are computed only where

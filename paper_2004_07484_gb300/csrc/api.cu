@@ -16,7 +16,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
   size_t hdr, scenes, rec0, rec1, rec2, key0, key1, val0, val1, hist, block_sums, pkey0, pkey1, pval0,
       pval1, radix_tot, ranges, item_begin, item_desc, item_order, unit_list, unit_count, unit_cost, unit_order, unit_tests, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
-      gacc, fin_part, red_part, total;
+      gacc, pg_cnt, pg_opa, pg_feat, fin_part, red_part, total;
   int64_t n_spheres, n_tiles, n_pixels, capacity, max_items;
   int32_t sort_blocks, fin_blocks, tile_bits, segment, part_fields;
 };
@@ -39,7 +39,7 @@ pulsar_status validate(const pulsar_params* p) {
   if (!(p->gamma >= 1e-5f && p->gamma <= 1.0f)) return PULSAR_ERR_INVALID_ARG;
   if (!(p->eps >= 0.0f) || !(p->znear > 0.0f) || !(p->zfar > p->znear)) return PULSAR_ERR_INVALID_ARG;
   if (p->flags & ~(uint32_t)(PULSAR_FLAG_STORE_HITS | PULSAR_FLAG_DIST_LITERAL | PULSAR_FLAG_NO_MIN_SIZE |
-                             PULSAR_FLAG_PERSISTENT | PULSAR_FLAG_ACCUMULATE))
+                             PULSAR_FLAG_PERSISTENT | PULSAR_FLAG_ACCUMULATE | PULSAR_FLAG_PAPER_GRADIENTS))
     return PULSAR_ERR_INVALID_ARG;
   if (p->segment != 0 && (p->segment < 32 || p->segment > 65536 || p->segment % 32 != 0))
     return PULSAR_ERR_INVALID_ARG;
@@ -114,6 +114,11 @@ Layout make_layout(const pulsar_params* ps, int n) {
   L.pix_aux = take(16 * (size_t)P);
   L.fres = take(4 * (size_t)P * C);
   L.gacc = take(16 * (size_t)M);
+  // paper gradients: per sphere its tracked pixels and the opacity and feature sums
+  const bool paper = (ps[0].flags & PULSAR_FLAG_PAPER_GRADIENTS) != 0;
+  L.pg_cnt = take(paper ? 4 * (size_t)M : 0);
+  L.pg_opa = take(paper ? 4 * (size_t)M : 0);
+  L.pg_feat = take(paper ? 4 * (size_t)M * C : 0);
   L.fin_part = take(4 * (size_t)kCamPartials * std::max(fin, 1));
   L.red_part = take(4 * (size_t)n * 64 * 45);
   L.total = off;
@@ -140,6 +145,7 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.max_items = (int32_t)L.max_items;
   v.part_fields = L.part_fields;
   v.persistent = (ps[0].flags & PULSAR_FLAG_PERSISTENT) ? 1 : 0;
+  v.paper = (ps[0].flags & PULSAR_FLAG_PAPER_GRADIENTS) ? 1 : 0;
   v.rec0 = reinterpret_cast<float4*>(b + L.rec0);
   v.rec1 = reinterpret_cast<float4*>(b + L.rec1);
   v.rec2 = reinterpret_cast<float4*>(b + L.rec2);
@@ -170,6 +176,9 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.pix_aux = reinterpret_cast<float4*>(b + L.pix_aux);
   v.fres = reinterpret_cast<float*>(b + L.fres);
   v.gacc = reinterpret_cast<float4*>(b + L.gacc);
+  v.pg_cnt = reinterpret_cast<int32_t*>(b + L.pg_cnt);
+  v.pg_opa = reinterpret_cast<float*>(b + L.pg_opa);
+  v.pg_feat = reinterpret_cast<float*>(b + L.pg_feat);
   v.fin_part = reinterpret_cast<float*>(b + L.fin_part);
   v.red_part = reinterpret_cast<float*>(b + L.red_part);
   return v;

@@ -142,6 +142,13 @@ __global__ void __launch_bounds__(kThreads) zero_grads_kernel(WsView v, uint32_t
   v.gacc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   const int s = scene_of_sphere(v.scenes, v.n_scenes, i);
   const SceneDev& S = v.scenes[s];
+  if (S.flags & PULSAR_FLAG_PAPER_GRADIENTS) {   // sums in the workspace; finalize writes the outputs
+    v.pg_cnt[i] = 0;
+    if (mask & PULSAR_GRAD_OPA) v.pg_opa[i] = 0.0f;
+    if (mask & PULSAR_GRAD_FEAT)
+      for (int c = 0; c < S.n_channels; ++c) v.pg_feat[i * S.n_channels + c] = 0.0f;
+    return;
+  }
   if (S.flags & PULSAR_FLAG_ACCUMULATE) return;   // the caller's buffers are added into
   const int64_t li = i - S.sphere_begin;
   if (mask & PULSAR_GRAD_OPA) S.g_opa[li] = 0.0f;
@@ -195,23 +202,49 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(WsView v, ui
     float gp1 = B[1] * gc0 + B[4] * gc1 + B[7] * gc2;
     float gp2 = B[2] * gc0 + B[5] * gc1 + B[8] * gc2;
     const bool acc = (S.flags & PULSAR_FLAG_ACCUMULATE) != 0;
+    // paper gradients: averages over the pixels that track the sphere, and
+    // positions and radii only above 3 pixels projected radius (the camera
+    // terms below keep the plain per-sphere sums)
+    float geo_scale = 1.0f;
+    if (S.flags & PULSAR_FLAG_PAPER_GRADIENTS) {
+      const int np = v.pg_cnt[i];
+      const float inv = 1.0f / (float)(np > 1 ? np : 1);
+      geo_scale = __fdiv_rn(pr.R, __fmul_rn(pr.cz, S.kappa)) > 3.0f ? inv : 0.0f;
+      if (mask & PULSAR_GRAD_OPA) {
+        const float go = v.pg_opa[i] * inv;
+        if (acc)
+          atomicAdd(S.g_opa + li, go);
+        else
+          S.g_opa[li] = go;
+      }
+      if (mask & PULSAR_GRAD_FEAT) {
+        const int C = S.n_channels;
+        for (int c = 0; c < C; ++c) {
+          const float gf = v.pg_feat[i * C + c] * inv;
+          if (acc)
+            atomicAdd(S.g_feat + li * C + c, gf);
+          else
+            S.g_feat[li * C + c] = gf;
+        }
+      }
+    }
     if (mask & PULSAR_GRAD_POS) {
       float* gp = S.g_pos + 3 * li;
       if (acc) {
-        atomicAdd(gp, gp0);
-        atomicAdd(gp + 1, gp1);
-        atomicAdd(gp + 2, gp2);
+        atomicAdd(gp, geo_scale * gp0);
+        atomicAdd(gp + 1, geo_scale * gp1);
+        atomicAdd(gp + 2, geo_scale * gp2);
       } else {
-        gp[0] = gp0;
-        gp[1] = gp1;
-        gp[2] = gp2;
+        gp[0] = geo_scale * gp0;
+        gp[1] = geo_scale * gp1;
+        gp[2] = geo_scale * gp2;
       }
     }
     if (mask & PULSAR_GRAD_RAD) {
       if (acc)
-        atomicAdd(S.g_rad + li, grad_r);
+        atomicAdd(S.g_rad + li, geo_scale * grad_r);
       else
-        S.g_rad[li] = grad_r;
+        S.g_rad[li] = geo_scale * grad_r;
     }
     if (mask & PULSAR_GRAD_CAM) {
       float d0 = p[0] - S.cam[0], d1 = p[1] - S.cam[1], d2 = p[2] - S.cam[2];
@@ -362,10 +395,13 @@ __global__ void __launch_bounds__(64) camera_reduce_kernel(WsView v, uint32_t ma
   }
   __syncthreads();
   if ((mask & PULSAR_GRAD_CAM) && threadIdx.x < 11) {
+    // paper gradients: the area-weighted average of the per-sphere terms times
+    // 1e-3, with the area taken as the tracked pixels: 1e-3 of the plain sum
+    const float g = (S.flags & PULSAR_FLAG_PAPER_GRADIENTS) ? 1e-3f * gcam[threadIdx.x] : gcam[threadIdx.x];
     if (S.flags & PULSAR_FLAG_ACCUMULATE)
-      atomicAdd(S.g_cam + threadIdx.x, gcam[threadIdx.x]);
+      atomicAdd(S.g_cam + threadIdx.x, g);
     else
-      S.g_cam[threadIdx.x] = gcam[threadIdx.x];
+      S.g_cam[threadIdx.x] = g;
   }
 }
 
@@ -409,7 +445,9 @@ cudaError_t launch_zero_grads(const WsView& v, uint32_t mask, cudaStream_t st) {
 }
 
 cudaError_t launch_finalize(const WsView& v, uint32_t mask, cudaStream_t st) {
-  if (v.fin_blocks > 0 && (mask & (PULSAR_GRAD_POS | PULSAR_GRAD_RAD | PULSAR_GRAD_CAM)))
+  const uint32_t fin_mask = PULSAR_GRAD_POS | PULSAR_GRAD_RAD | PULSAR_GRAD_CAM |
+                            (v.paper ? (PULSAR_GRAD_OPA | PULSAR_GRAD_FEAT) : 0u);
+  if (v.fin_blocks > 0 && (mask & fin_mask))
     finalize_kernel<<<v.fin_blocks, kFinalizeThreads, 0, st>>>(v, mask);
   if (mask & (PULSAR_GRAD_CAM | PULSAR_GRAD_BG)) {
     camera_partials_kernel<<<dim3(v.n_scenes, kRedParts), 256, 0, st>>>(v, mask);

@@ -121,6 +121,7 @@ struct WsView {
   int32_t max_items;         // bound on work items: n_tiles + capacity / segment
   int32_t part_fields;       // floats per pixel of a partial forward state
   int32_t persistent;        // render passes run as persistent kernels
+  int32_t paper;             // the paper's gradient normalisations
   float4* rec0;              // per sphere: c.x, c.y, c.z, R^2
   float4* rec1;              // per sphere: key, o, x-range (x0 | x1 << 16), y-range
   float4* rec2;              // per sphere: c - c.xyz (low-order part of the double centre), R
@@ -147,6 +148,9 @@ struct WsView {
   float4* pix_aux;           // per pixel: (t_K, id_K bits, reference sphere bits, 0)
   float* fres;               // per pixel x C: F - f_ref, the image relative to its reference feature
   float4* gacc;              // per sphere: dL/dc (3), dL/dR
+  int32_t* pg_cnt;           // paper gradients: per sphere, pixels that track it
+  float* pg_opa;             // paper gradients: per sphere, dL/do before averaging
+  float* pg_feat;            // paper gradients: per sphere x C, dL/df before averaging
   float* fin_part;           // per finalize block: camera partials
   float* red_part;           // per scene x 64: first-stage camera / background sums (45)
 };

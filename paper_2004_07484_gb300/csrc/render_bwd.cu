@@ -41,9 +41,13 @@ __device__ __forceinline__ void add_hit_grads(int id_global, int64_t id_local, f
                                               int C, const WsView& v, const SceneDev& S, bool geo,
                                               bool opa, bool feat) {
   if (geo) atomicAdd(&v.gacc[id_global], make_float4(gc0, gc1, gc2, gR));
-  if (opa) atomicAdd(S.g_opa + id_local, go);
+  // paper gradients: opacity and feature sums stay in the workspace, with the
+  // count of pixels that track the sphere, until finalize averages them
+  const bool paper = v.paper != 0;
+  if (paper) atomicAdd(v.pg_cnt + id_global, 1);
+  if (opa) atomicAdd(paper ? v.pg_opa + id_global : S.g_opa + id_local, go);
   if (feat) {
-    float* dst = S.g_feat + id_local * C;
+    float* dst = paper ? v.pg_feat + (int64_t)id_global * C : S.g_feat + id_local * C;
     if ((C & 3) == 0) {
 #pragma unroll
       for (int c = 0; c < CMAX; c += 4)

@@ -36,6 +36,7 @@ class RenderSettings:
     segment: int = 0                 # scheduling: list entries per work item (0 = library default)
     persistent: bool = False         # scheduling: persistent render kernels
     accumulate: bool = False         # backward adds into the gradient buffers (views sharing them)
+    paper_gradients: bool = False    # the paper's gradient normalisations (App. B, Sec. 6)
 
     def flags(self) -> int:
         f = 0
@@ -49,6 +50,8 @@ class RenderSettings:
             f |= _lib.FLAG_PERSISTENT
         if self.accumulate:
             f |= _lib.FLAG_ACCUMULATE
+        if self.paper_gradients:
+            f |= _lib.FLAG_PAPER_GRADIENTS
         return f
 
     def params(self, n_spheres: int, capacity: int) -> _lib.Params:

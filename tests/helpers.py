@@ -17,20 +17,20 @@ def to_dev(scene: Scene):
 
 
 def settings_of(scene: Scene, store=True, dist_literal=False, min_size=True, n_track=None, segment=0,
-                persistent=False):
+                persistent=False, paper=False):
     from paper_2004_07484_gb300 import RenderSettings
     return RenderSettings(scene.width, scene.height, scene.n_channels,
                           n_track or scene.n_track, float(scene.gamma), float(scene.eps),
                           float(scene.znear), float(scene.zfar), store, dist_literal, min_size,
-                          segment=segment, persistent=persistent)
+                          segment=segment, persistent=persistent, paper_gradients=paper)
 
 
 def gpu_forward(scene: Scene, store=True, dist_literal=False, min_size=True, capacity=None,
-                n_track=None, dev=None, segment=0, persistent=False):
+                n_track=None, dev=None, segment=0, persistent=False, paper=False):
     import torch
     from paper_2004_07484_gb300 import forward_frame
     dev = dev or to_dev(scene)
-    s = settings_of(scene, store, dist_literal, min_size, n_track, segment, persistent)
+    s = settings_of(scene, store, dist_literal, min_size, n_track, segment, persistent, paper)
     H, W, K = scene.height, scene.width, s.n_track
     n_hits = torch.empty((H, W), dtype=torch.int32, device="cuda")
     tracked = torch.empty((H, W, K), dtype=torch.int32, device="cuda")

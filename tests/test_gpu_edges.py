@@ -218,3 +218,55 @@ def test_adam_steps_reduce_the_image_loss():
         losses.append(float(loss.detach()))
     assert all(np.isfinite(losses))
     assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+
+
+@pytest.mark.parametrize("store", [True, False], ids=["store", "recompute"])
+def test_paper_gradients_match_oracle(orc, store):
+    """The paper's gradient normalisations (App. B, end of "The Backward
+    Pass"; Sec. 6) against the oracle's: spheres of 0.3 to 7 pixels projected
+    radius under a rotated camera, upstream gradient zero on some pixels (they
+    still count), one sphere set seen by two views of a batch adding into one
+    set of buffers."""
+    from paper_2004_07484_gb300.scenes import uniform_cloud
+    sc = uniform_cloud(71, 300, 96, 72, n_channels=4, gamma=0.05, n_track=6, rad=(0.02, 1.0))
+    rows = S.random_rotation(np.random.default_rng(5)).T
+    centre = sc.pos.astype(np.float64).mean(axis=0)
+    sc.cam = S.make_cam(t=centre - 8.0 * rows[2], rot6=S.rot6_from_matrix(rows))
+    G = S.grad_image(13, sc.height, sc.width, sc.n_channels)
+    G[::4, ::3] = 0.0
+    gpu = gpu_forward(sc, store=store, paper=True)
+    want = orc.render_backward(sc, G, paper_grad=True)
+    got = gpu_backward(gpu, G)
+    assert_grads_close(got, want, scene=sc)
+    hit = np.abs(want.opa) > 0
+    gated = np.abs(want.pos).sum(axis=1) == 0
+    assert (hit & gated).any() and (hit & ~gated).any()   # both sides of the 3-pixel gate
+
+
+def test_paper_gradients_accumulate_over_views(orc):
+    import torch
+    from dataclasses import replace
+    from paper_2004_07484_gb300 import _lib, backward_batch, forward_batch
+    from helpers import settings_of
+    from paper_2004_07484_gb300.scenes import uniform_cloud
+    sc = uniform_cloud(72, 200, 64, 64, n_channels=4, gamma=0.05, n_track=6, rad=(0.02, 1.0))
+    centre = sc.pos.astype(np.float64).mean(axis=0)
+    cams = S.orbit_cameras(9, centre, n_views=2, distance=6.0)
+    d = {k: torch.from_numpy(np.ascontiguousarray(getattr(sc, k))).cuda() for k in ("pos", "feat", "rad", "opa", "bg")}
+    inputs = [(d["pos"], d["feat"], d["rad"], d["opa"], torch.from_numpy(c).cuda(), d["bg"]) for c in cams]
+    s = replace(settings_of(sc, paper=True), accumulate=True)
+    fr, images, log_norms = forward_batch([s, s], inputs, [1 << 16] * 2)
+    Gs = [S.grad_image(20 + k, sc.height, sc.width, sc.n_channels) for k in range(2)]
+    M, C = sc.n_spheres, sc.n_channels
+    shared = (torch.zeros((M, 3), device="cuda"), torch.zeros(M, device="cuda"), torch.zeros(M, device="cuda"),
+              torch.zeros((M, C), device="cuda"))
+    out = [shared + (None, None)] * 2
+    mask = _lib.GRAD_POS | _lib.GRAD_RAD | _lib.GRAD_OPA | _lib.GRAD_FEAT
+    backward_batch(fr, inputs, images, log_norms, [torch.from_numpy(G).cuda() for G in Gs], mask, out=out)
+    torch.cuda.synchronize()
+    from types import SimpleNamespace
+    refs = [orc.render_backward(SimpleNamespace(**{**sc.__dict__, "cam": c}), G, paper_grad=True)
+            for c, G in zip(cams, Gs)]
+    tot = SimpleNamespace(**{n: getattr(refs[0], n) + getattr(refs[1], n) for n in ("pos", "rad", "opa", "feat")})
+    got = {n: t.cpu().numpy().astype(np.float64) for n, t in zip(("pos", "rad", "opa", "feat"), shared)}
+    assert_grads_close(got, tot, names=("pos", "rad", "opa", "feat"))
