@@ -29,6 +29,7 @@ class OrcParams(ctypes.Structure):
         ("n_spheres", ctypes.c_int32), ("n_channels", ctypes.c_int32),
         ("n_track", ctypes.c_int32), ("tile", ctypes.c_int32),
         ("min_size", ctypes.c_int32), ("dist_literal", ctypes.c_int32), ("paper_grad", ctypes.c_int32),
+        ("ortho", ctypes.c_int32),
         ("gamma", ctypes.c_double), ("eps", ctypes.c_double),
         ("znear", ctypes.c_double), ("zfar", ctypes.c_double),
     ]
@@ -85,10 +86,14 @@ def _d(a) -> np.ndarray:
 
 
 def params(scene, tile: int = 16, min_size: bool = True, dist_literal: bool = False,
-           n_track: int | None = None, paper_grad: bool = False) -> OrcParams:
+           n_track: int | None = None, paper_grad: bool = False, ortho: bool | None = None) -> OrcParams:
+    """ortho=None takes the scene's own ``ortho`` attribute (False when absent)."""
+    if ortho is None:
+        ortho = bool(getattr(scene, "ortho", False))
     return OrcParams(int(scene.width), int(scene.height), int(scene.pos.shape[0]),
                      int(scene.feat.shape[1]), int(n_track if n_track is not None else scene.n_track),
                      int(tile), int(bool(min_size)), int(bool(dist_literal)), int(bool(paper_grad)),
+                     int(bool(ortho)),
                      float(np.float32(scene.gamma)), float(np.float32(scene.eps)),
                      float(np.float32(scene.znear)), float(np.float32(scene.zfar)))
 

@@ -27,6 +27,13 @@
  *               the camera-space centre is c = (b1.(p-t), b2.(p-t), b3.(p-t)).
  *   pinhole     pixel (u, v) has the ray (rho_x, rho_y, 1) with
  *               rho = ((u + 1/2 - W/2) k, (v + 1/2 - H/2) k), k = s / (W f).
+ *   orthographic (option; Sec. 1: "pinhole and orthogonal camera model")
+ *               pixel (u, v) has the ray from (rho_x, rho_y, 0) along +z,
+ *               with k = s / W (the sensor width in scene units across the
+ *               image; the focal length does not enter).  Everything below
+ *               then holds for the shifted centre c' = c - (rho_x, rho_y, 0)
+ *               and the ray (0, 0, 1); the minimum size is R = max(r, 0.75 k)
+ *               and the rectangle is the centre -+ R in pixels.
  *   min size    every sphere is drawn with at least one pixel (App. B,
  *               Step 0): R = max(r, 0.75 |c| k).
  *   depth       z = (zfar - t_h) / (zfar - znear) in [0, 1], 0 = max depth
@@ -64,6 +71,7 @@ typedef struct {
   int32_t min_size;      /* 1: apply the one-pixel minimum size rule */
   int32_t dist_literal;  /* 1: d = min(1, dist/R) instead of 1 - min(1, dist/R) */
   int32_t paper_grad;    /* 1: the paper's gradient normalisations (header) */
+  int32_t ortho;         /* 1: orthographic camera (header) */
   double gamma, eps, znear, zfar;
 } orc_params;
 
@@ -97,8 +105,8 @@ typedef struct {
   int x0, x1, y0, y1; /* inclusive pixel rectangle, valid when visible */
 } proj32;
 
-static float kappa_f32(const float* cam, int width) {
-  return cam[10] / ((float)width * cam[9]);
+static float kappa_f32(const float* cam, int width, int ortho) {
+  return ortho ? cam[10] / (float)width : cam[10] / ((float)width * cam[9]);
 }
 
 /* One axis of the enclosing rectangle.  In the (axis, z) plane the sphere is a
@@ -124,17 +132,34 @@ static void axis_range_f32(float cx, float cz, float R, float R2, float kappa, i
   *hi = (int)floorf(fhi) + 1;
 }
 
+/* One axis of the rectangle of the orthographic camera: the centre -+ R in
+ * pixels, widened by one pixel on each side. */
+static void axis_range_ortho_f32(float cx, float R, float kappa, int n, int* lo, int* hi) {
+  float half = (float)(n - 1) * 0.5f;
+  float flo = (cx - R) / kappa + half;
+  float fhi = (cx + R) / kappa + half;
+  flo = fmaxf(fminf(flo, (float)n + 2.0f), -4.0f);
+  fhi = fmaxf(fminf(fhi, (float)n + 2.0f), -4.0f);
+  *lo = (int)ceilf(flo) - 1;
+  *hi = (int)floorf(fhi) + 1;
+}
+
 static void project_f32(const orc_params* P, const float* cam, const float B[9],
                         const float p[3], float r, proj32* o) {
-  float kappa = kappa_f32(cam, P->width);
+  float kappa = kappa_f32(cam, P->width, P->ortho);
   float dx = p[0] - cam[0], dy = p[1] - cam[1], dz = p[2] - cam[2];
   o->cx = fmaf(B[0], dx, fmaf(B[1], dy, B[2] * dz));
   o->cy = fmaf(B[3], dx, fmaf(B[4], dy, B[5] * dz));
   o->cz = fmaf(B[6], dx, fmaf(B[7], dy, B[8] * dz));
   float R = r;
   if (P->min_size) {
-    float cn = sqrtf(fmaf(o->cx, o->cx, fmaf(o->cy, o->cy, o->cz * o->cz)));
-    float rmin = 0.75f * (cn * kappa);
+    float rmin;
+    if (P->ortho) {
+      rmin = 0.75f * kappa;
+    } else {
+      float cn = sqrtf(fmaf(o->cx, o->cx, fmaf(o->cy, o->cy, o->cz * o->cz)));
+      rmin = 0.75f * (cn * kappa);
+    }
     if (rmin > r) R = rmin;
   }
   o->R = R;
@@ -147,8 +172,13 @@ static void project_f32(const orc_params* P, const float* cam, const float B[9],
   float znear = (float)P->znear, zfar = (float)P->zfar;
   if (!(R > 0.0f) || !(key > znear) || !(key < zfar)) return;
   int x0, x1, y0, y1;
-  axis_range_f32(o->cx, o->cz, R, o->R2, kappa, P->width, &x0, &x1);
-  axis_range_f32(o->cy, o->cz, R, o->R2, kappa, P->height, &y0, &y1);
+  if (P->ortho) {
+    axis_range_ortho_f32(o->cx, R, kappa, P->width, &x0, &x1);
+    axis_range_ortho_f32(o->cy, R, kappa, P->height, &y0, &y1);
+  } else {
+    axis_range_f32(o->cx, o->cz, R, o->R2, kappa, P->width, &x0, &x1);
+    axis_range_f32(o->cy, o->cz, R, o->R2, kappa, P->height, &y0, &y1);
+  }
   if (x1 < 0 || x0 > P->width - 1 || y1 < 0 || y0 > P->height - 1) return;
   o->x0 = x0 < 0 ? 0 : x0;
   o->x1 = x1 > P->width - 1 ? P->width - 1 : x1;
@@ -181,6 +211,17 @@ static int hit_f32(const proj32* s, float rx, float ry, float zfar, float* t_out
   if (!(t < zfar)) return 0;
   *t_out = t;
   return 1;
+}
+
+/* The hit predicate of either camera: the orthographic ray from
+ * (rho_x, rho_y, 0) along +z is the pinhole test of the shifted centre
+ * c - (rho_x, rho_y, 0) with the ray (0, 0, 1). */
+static int hit_px(const orc_params* P, const proj32* s, float rx, float ry, float zfar, float* t_out) {
+  if (!P->ortho) return hit_f32(s, rx, ry, zfar, t_out);
+  proj32 q = *s;
+  q.cx = s->cx - rx;
+  q.cy = s->cy - ry;
+  return hit_f32(&q, 0.0f, 0.0f, zfar, t_out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -261,9 +302,9 @@ static void ctx_init(const orc_params* P, const double* pos, const double* rad,
   if (!dcam) dcam = cam;
   for (int k = 0; k < 11; ++k) C->camf[k] = (float)dcam[k];
   rows_f32(C->camf + 3, C->Bf);
-  C->kappaf = kappa_f32(C->camf, P->width);
+  C->kappaf = kappa_f32(C->camf, P->width, P->ortho);
   rows_f64(cam + 3, C->B);
-  C->kappa = cam[10] / ((double)P->width * cam[9]);
+  C->kappa = P->ortho ? cam[10] / (double)P->width : cam[10] / ((double)P->width * cam[9]);
   C->pj = (proj32*)malloc(sizeof(proj32) * (size_t)(M > 0 ? M : 1));
   C->sv = (sph64*)malloc(sizeof(sph64) * (size_t)(M > 0 ? M : 1));
   for (int i = 0; i < M; ++i) {
@@ -276,7 +317,7 @@ static void ctx_init(const orc_params* P, const double* pos, const double* rad,
     /* the branch of the minimum-size rule is a decision: take it from float32 */
     s->clamped = P->min_size && (C->pj[i].R != (float)drad[i]);
     double cn = sqrt(s->c[0] * s->c[0] + s->c[1] * s->c[1] + s->c[2] * s->c[2]);
-    s->R = s->clamped ? 0.75 * cn * C->kappa : rad[i];
+    s->R = s->clamped ? (P->ortho ? 0.75 * C->kappa : 0.75 * cn * C->kappa) : rad[i];
   }
 }
 
@@ -290,11 +331,21 @@ static void ctx_free(ctx_t* C) {
  *   t = (b - sqrt(disc)) / rr (front root), dist^2 = |c|^2 - b^2 / rr. */
 typedef struct {
   double r[3], b, rr, q, disc, sq, t, dist, z, d, s, dq;
+  double cs[3];   /* the centre the ray meets: c, or c - (rho_x, rho_y, 0) orthographic */
 } rayq;
 
 static void ray_values(const orc_params* P, const sph64* s, double rx, double ry, rayq* o) {
+  if (P->ortho) {   /* ray from (rx, ry, 0) along +z: shifted centre, ray (0, 0, 1) */
+    o->cs[0] = s->c[0] - rx;
+    o->cs[1] = s->c[1] - ry;
+    rx = ry = 0.0;
+  } else {
+    o->cs[0] = s->c[0];
+    o->cs[1] = s->c[1];
+  }
+  o->cs[2] = s->c[2];
   o->r[0] = rx; o->r[1] = ry; o->r[2] = 1.0;
-  const double* c = s->c;
+  const double* c = o->cs;
   double cc = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
   o->b = rx * c[0] + ry * c[1] + c[2];
   o->rr = rx * rx + ry * ry + 1.0;
@@ -319,7 +370,7 @@ static int pixel_hits(const orc_params* P, const ctx_t* C, int u, int v, hit_rec
   for (int i = 0; i < M; ++i) {
     if (!C->pj[i].visible) continue;
     float t;
-    if (hit_f32(&C->pj[i], rx, ry, (float)P->zfar, &t)) {
+    if (hit_px(P, &C->pj[i], rx, ry, (float)P->zfar, &t)) {
       hits[n].id = i;
       hits[n].t32 = t;
       ++n;
@@ -545,8 +596,9 @@ void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
             dL_ddist = sgn * dL_dd / s->R;
             dL_dR = -sgn * dL_dd * q.dist / (s->R * s->R);
           }
-          /* derivatives of t = (b - sqrt(disc)) / rr and dist^2 = |c|^2 - b^2/rr */
-          const double* c = s->c;
+          /* derivatives of t = (b - sqrt(disc)) / rr and dist^2 = |c|^2 - b^2/rr
+           * (c the centre the ray meets; orthographic: shifted, ray (0, 0, 1)) */
+          const double* c = q.cs;
           double dc[3] = {0, 0, 0}, dr[3] = {0, 0, 0};
           if (q.sq > 0.0) {
             for (int k = 0; k < 3; ++k) {
@@ -566,7 +618,9 @@ void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
               dr[k] += dL_ddist * (-tc * e / q.dist);
             }
           }
-          gk_local += dr[0] * pxo + dr[1] * pyo;
+          /* the pitch k enters through the ray slopes (pinhole) or through the
+           * shift c - k (pxo, pyo, 0) of the centre (orthographic) */
+          gk_local += P->ortho ? -(dc[0] * pxo + dc[1] * pyo) : dr[0] * pxo + dr[1] * pyo;
 #pragma omp atomic
           gc[4 * (size_t)i] += dc[0];
 #pragma omp atomic
@@ -604,7 +658,9 @@ void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
       g_opa[i] *= scale;
       for (int c = 0; c < Cn; ++c) g_feat[(size_t)i * Cn + c] *= scale;
     }
-    if (s->clamped) {
+    if (s->clamped && P->ortho) {
+      g_kappa += a[3] * 0.75;   /* R = 0.75 k */
+    } else if (s->clamped) {
       double cn = sqrt(s->c[0] * s->c[0] + s->c[1] * s->c[1] + s->c[2] * s->c[2]);
       for (int k = 0; k < 3; ++k) a[k] += a[3] * 0.75 * C.kappa * s->c[k] / cn;
       g_kappa += a[3] * 0.75 * cn;
@@ -631,9 +687,14 @@ void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
     for (int j = 0; j < 9; ++j) acc += gB[j] * cimag(Bc[j]) / h;
     g_cam[3 + k] = acc;
   }
-  /* kappa = s / (W f) */
-  g_cam[9] = -g_kappa * C.kappa / cam[9];
-  g_cam[10] = g_kappa / ((double)W * cam[9]);
+  /* kappa = s / (W f), orthographic s / W */
+  if (P->ortho) {
+    g_cam[9] = 0.0;
+    g_cam[10] = g_kappa / (double)W;
+  } else {
+    g_cam[9] = -g_kappa * C.kappa / cam[9];
+    g_cam[10] = g_kappa / ((double)W * cam[9]);
+  }
   if (P->paper_grad)
     for (int k = 0; k < 11; ++k) g_cam[k] *= 1e-3;
   free(gc);
@@ -657,7 +718,7 @@ int orc_hit_f32(const orc_params* P, const double* pos3, double rad, const doubl
   if (C.pj[0].visible || ignore_cull) {
     float rx = ray_coord_f32(u, P->width, C.kappaf);
     float ry = ray_coord_f32(v, P->height, C.kappaf);
-    hit = hit_f32(&C.pj[0], rx, ry, (float)P->zfar, t_out);
+    hit = hit_px(P, &C.pj[0], rx, ry, (float)P->zfar, t_out);
   }
   ctx_free(&C);
   return hit;
@@ -680,7 +741,7 @@ void orc_hit_map(const orc_params* P, const double* pos3, double rad, const doub
       if (C.pj[0].visible || ignore_cull) {
         float rx = ray_coord_f32(u, P->width, C.kappaf);
         float ry = ray_coord_f32(v, P->height, C.kappaf);
-        hit = hit_f32(&C.pj[0], rx, ry, (float)P->zfar, &t);
+        hit = hit_px(P, &C.pj[0], rx, ry, (float)P->zfar, &t);
       }
       map[(size_t)v * P->width + u] = (uint8_t)hit;
     }

@@ -45,6 +45,7 @@ class Scene:
     zfar: float = 20.0
     name: str = ""
     meta: dict = field(default_factory=dict)
+    ortho: bool = False      # orthographic camera (rays along +z from the sensor plane)
 
     @property
     def n_spheres(self) -> int:
