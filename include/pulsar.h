@@ -87,7 +87,12 @@ enum {
    * area-weighted sum of the averaged per-sphere terms times 1e-3, which with
    * the area taken as the sphere's tracked pixels is 1e-3 times the plain
    * camera gradient.  The background gradient is unchanged. */
-  PULSAR_FLAG_PAPER_GRADIENTS = 1u << 5
+  PULSAR_FLAG_PAPER_GRADIENTS = 1u << 5,
+  /* Orthographic camera (Sec. 1: "pinhole and orthogonal camera model"):
+   * pixel (u, v) sees along +z from (rho_x, rho_y, 0) in camera space, rho =
+   * ((u + 1/2 - W/2) k, (v + 1/2 - H/2) k) with k = sensor_width / W; the
+   * focal length does not enter.  The minimum size is R = max(r, 0.75 k). */
+  PULSAR_FLAG_ORTHOGRAPHIC = 1u << 6
 };
 
 /* grad_mask bits of pulsar_render_bwd: gradients are computed only where

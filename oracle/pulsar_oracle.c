@@ -653,7 +653,8 @@ void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
     double scale = 1.0, geo_scale = 1.0;
     if (P->paper_grad) {
       scale = 1.0 / (double)(n_px[i] > 1 ? n_px[i] : 1);
-      const float rpx = C.pj[i].R / (C.pj[i].cz * C.kappaf);
+      const float px_size = P->ortho ? C.kappaf : C.pj[i].cz * C.kappaf;
+      const float rpx = C.pj[i].R / px_size;
       geo_scale = rpx > 3.0f ? scale : 0.0;
       g_opa[i] *= scale;
       for (int c = 0; c < Cn; ++c) g_feat[(size_t)i * Cn + c] *= scale;

@@ -20,6 +20,7 @@ FLAG_NO_MIN_SIZE = 1 << 2
 FLAG_PERSISTENT = 1 << 3
 FLAG_ACCUMULATE = 1 << 4
 FLAG_PAPER_GRADIENTS = 1 << 5
+FLAG_ORTHOGRAPHIC = 1 << 6
 
 GRAD_POS, GRAD_RAD, GRAD_OPA, GRAD_FEAT, GRAD_CAM, GRAD_BG = (1 << k for k in range(6))
 GRAD_ALL = 63

@@ -39,7 +39,8 @@ pulsar_status validate(const pulsar_params* p) {
   if (!(p->gamma >= 1e-5f && p->gamma <= 1.0f)) return PULSAR_ERR_INVALID_ARG;
   if (!(p->eps >= 0.0f) || !(p->znear > 0.0f) || !(p->zfar > p->znear)) return PULSAR_ERR_INVALID_ARG;
   if (p->flags & ~(uint32_t)(PULSAR_FLAG_STORE_HITS | PULSAR_FLAG_DIST_LITERAL | PULSAR_FLAG_NO_MIN_SIZE |
-                             PULSAR_FLAG_PERSISTENT | PULSAR_FLAG_ACCUMULATE | PULSAR_FLAG_PAPER_GRADIENTS))
+                             PULSAR_FLAG_PERSISTENT | PULSAR_FLAG_ACCUMULATE | PULSAR_FLAG_PAPER_GRADIENTS |
+                             PULSAR_FLAG_ORTHOGRAPHIC))
     return PULSAR_ERR_INVALID_ARG;
   if (p->segment != 0 && (p->segment < 32 || p->segment > 65536 || p->segment % 32 != 0))
     return PULSAR_ERR_INVALID_ARG;

@@ -67,8 +67,8 @@ __device__ __forceinline__ void block_batch(BlockListWarp& W, int cnt, const WsV
     const uint32_t dx = r - dy * (g >> 16);
     const int px = (int)(g & 0xffu) + (int)dx, py = (int)((g >> 8) & 0xffu) + (int)dy;
     const float4 a = W.rec0[e];
-    if (ray_disc_positive(a.x, a.y, a.z, a.w, ray_coord(wr.x0 + px, S.width, S.kappa),
-                          ray_coord(wr.y0 + py, S.height, S.kappa)))
+    if (pixel_disc_positive(a, ray_coord(wr.x0 + px, S.width, S.kappa), ray_coord(wr.y0 + py, S.height, S.kappa),
+                            (S.flags & PULSAR_FLAG_ORTHOGRAPHIC) != 0))
       atomicOr(&W.hm[e], 1u << (py * 8 + px));
   }
   __syncwarp();

@@ -38,13 +38,15 @@ __global__ void setup_kernel(WsView v, const SetupPack<N> pk) {
     SceneDev d = pk.s[i];
     if (pk.full) {
       rows_from_rot6(d.cam + 3, d.rows);
-      d.kappa = pixel_pitch(d.cam, d.width);
+      const bool ortho = (d.flags & PULSAR_FLAG_ORTHOGRAPHIC) != 0;
+      d.kappa = pixel_pitch(d.cam, d.width, ortho);
       rows_from_rot6_f64(d.cam + 3, d.rows64);
       for (int k = 0; k < 9; ++k) {
         d.rows_hi[k] = (float)d.rows64[k];
         d.rows_lo[k] = (float)(d.rows64[k] - (double)d.rows_hi[k]);
       }
-      d.kappa64 = (double)d.cam[10] / ((double)d.width * (double)d.cam[9]);
+      d.kappa64 = ortho ? (double)d.cam[10] / (double)d.width
+                        : (double)d.cam[10] / ((double)d.width * (double)d.cam[9]);
       d.kappa_hi = (float)d.kappa64;
       d.kappa_lo = (float)(d.kappa64 - (double)d.kappa_hi);
       d.omax_bits = 0u;
@@ -86,7 +88,8 @@ __global__ void __launch_bounds__(kThreads) project_kernel(WsView v) {
     const float r = S.rad[li];
     const float o = S.opa[li];
     Projected pr = project_sphere(S.rows, S.cam, S.kappa, p[0], p[1], p[2], r, S.width, S.height,
-                                  S.znear, S.zfar, !(S.flags & PULSAR_FLAG_NO_MIN_SIZE));
+                                  S.znear, S.zfar, !(S.flags & PULSAR_FLAG_NO_MIN_SIZE),
+                                  (S.flags & PULSAR_FLAG_ORTHOGRAPHIC) != 0);
     v.rec0[i] = make_float4(pr.cx, pr.cy, pr.cz, pr.R2);
     v.rec1[i] = make_float4(pr.key, o, __uint_as_float(pack_range(pr.x0, pr.x1)),
                             __uint_as_float(pack_range(pr.y0, pr.y1)));
@@ -107,7 +110,10 @@ __global__ void __launch_bounds__(kThreads) project_kernel(WsView v) {
       }
     }
     float Rv = r;
-    if (pr.R != r) {   // R = 0.75 |c| kappa
+    if (pr.R != r && (S.flags & PULSAR_FLAG_ORTHOGRAPHIC)) {   // R = 0.75 kappa
+      const FF q = two_prod(S.kappa_hi, 0.75f);
+      Rv = __fadd_rn(q.hi, __fmaf_rn(0.75f, S.kappa_lo, q.lo));
+    } else if (pr.R != r) {   // R = 0.75 |c| kappa
       FF n2 = two_prod(c[0].hi, c[0].hi);
       n2.lo = __fmaf_rn(2.0f * c[0].hi, c[0].lo, n2.lo);
 #pragma unroll
@@ -182,11 +188,14 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(WsView v, ui
     const float* p = S.pos + 3 * li;
     const float r = S.rad[li];
     Projected pr = project_sphere(S.rows, S.cam, S.kappa, p[0], p[1], p[2], r, S.width, S.height,
-                                  S.znear, S.zfar, !(S.flags & PULSAR_FLAG_NO_MIN_SIZE));
+                                  S.znear, S.zfar, !(S.flags & PULSAR_FLAG_NO_MIN_SIZE),
+                                  (S.flags & PULSAR_FLAG_ORTHOGRAPHIC) != 0);
     float gc0 = g.x, gc1 = g.y, gc2 = g.z;
     float gk = 0.0f, grad_r = 0.0f;
     const bool clamped = pr.R != r;
-    if (clamped) {
+    if (clamped && (S.flags & PULSAR_FLAG_ORTHOGRAPHIC)) {
+      gk = g.w * 0.75f;   // R = 0.75 kappa
+    } else if (clamped) {
       // R = 0.75 |c| kappa
       float cn = sqrtf(pr.cx * pr.cx + pr.cy * pr.cy + pr.cz * pr.cz);
       float f = g.w * 0.75f * S.kappa / cn;
@@ -209,7 +218,8 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(WsView v, ui
     if (S.flags & PULSAR_FLAG_PAPER_GRADIENTS) {
       const int np = v.pg_cnt[i];
       const float inv = 1.0f / (float)(np > 1 ? np : 1);
-      geo_scale = __fdiv_rn(pr.R, __fmul_rn(pr.cz, S.kappa)) > 3.0f ? inv : 0.0f;
+      const float px_size = (S.flags & PULSAR_FLAG_ORTHOGRAPHIC) ? S.kappa : __fmul_rn(pr.cz, S.kappa);
+      geo_scale = __fdiv_rn(pr.R, px_size) > 3.0f ? inv : 0.0f;
       if (mask & PULSAR_GRAD_OPA) {
         const float go = v.pg_opa[i] * inv;
         if (acc)
@@ -390,8 +400,13 @@ __global__ void __launch_bounds__(64) camera_reduce_kernel(WsView v, uint32_t ma
     gcam[0] = tot[9]; gcam[1] = tot[10]; gcam[2] = tot[11];
     gcam[3] = ga1[0]; gcam[4] = ga1[1]; gcam[5] = ga1[2];
     gcam[6] = ga2[0]; gcam[7] = ga2[1]; gcam[8] = ga2[2];
-    gcam[9] = -tot[12] * S.kappa / f;
-    gcam[10] = tot[12] / ((float)S.width * f);
+    if (S.flags & PULSAR_FLAG_ORTHOGRAPHIC) {   // kappa = s / W
+      gcam[9] = 0.0f;
+      gcam[10] = tot[12] / (float)S.width;
+    } else {                                    // kappa = s / (W f)
+      gcam[9] = -tot[12] * S.kappa / f;
+      gcam[10] = tot[12] / ((float)S.width * f);
+    }
   }
   __syncthreads();
   if ((mask & PULSAR_GRAD_CAM) && threadIdx.x < 11) {

@@ -175,8 +175,8 @@ __device__ __forceinline__ void rows_from_rot6(const float* a, float* B) {
   B[8] = __fmaf_rn(b1x, b2y, -__fmul_rn(b1y, b2x));
 }
 
-__device__ __forceinline__ float pixel_pitch(const float* cam, int width) {
-  return __fdiv_rn(cam[10], __fmul_rn((float)width, cam[9]));
+__device__ __forceinline__ float pixel_pitch(const float* cam, int width, bool ortho) {
+  return ortho ? __fdiv_rn(cam[10], (float)width) : __fdiv_rn(cam[10], __fmul_rn((float)width, cam[9]));
 }
 
 struct Projected {
@@ -205,12 +205,24 @@ __device__ __forceinline__ void axis_range(float cx, float cz, float R, float R2
   hi = (int)floorf(fhi) + 1;
 }
 
+// One axis of the rectangle of the orthographic camera: the centre -+ R in
+// pixels, widened by one pixel.
+__device__ __forceinline__ void axis_range_ortho(float cx, float R, float kappa, int n, int& lo, int& hi) {
+  float half = __fmul_rn((float)(n - 1), 0.5f);
+  float flo = __fadd_rn(__fdiv_rn(__fsub_rn(cx, R), kappa), half);
+  float fhi = __fadd_rn(__fdiv_rn(__fadd_rn(cx, R), kappa), half);
+  flo = fmaxf(fminf(flo, (float)n + 2.0f), -4.0f);
+  fhi = fmaxf(fminf(fhi, (float)n + 2.0f), -4.0f);
+  lo = (int)ceilf(flo) - 1;
+  hi = (int)floorf(fhi) + 1;
+}
+
 // Step 0 for one sphere: camera-space centre, effective radius (one-pixel
 // minimum size), culling, rectangle and sort key.
 __device__ __forceinline__ Projected project_sphere(const float* B, const float* cam, float kappa,
                                                     float px, float py, float pz, float r,
                                                     int width, int height, float znear, float zfar,
-                                                    bool min_size) {
+                                                    bool min_size, bool ortho) {
   Projected o;
   float dx = __fsub_rn(px, cam[0]), dy = __fsub_rn(py, cam[1]), dz = __fsub_rn(pz, cam[2]);
   o.cx = __fmaf_rn(B[0], dx, __fmaf_rn(B[1], dy, __fmul_rn(B[2], dz)));
@@ -218,8 +230,13 @@ __device__ __forceinline__ Projected project_sphere(const float* B, const float*
   o.cz = __fmaf_rn(B[6], dx, __fmaf_rn(B[7], dy, __fmul_rn(B[8], dz)));
   float R = r;
   if (min_size) {
-    float cn = __fsqrt_rn(__fmaf_rn(o.cx, o.cx, __fmaf_rn(o.cy, o.cy, __fmul_rn(o.cz, o.cz))));
-    float rmin = __fmul_rn(0.75f, __fmul_rn(cn, kappa));
+    float rmin;
+    if (ortho) {
+      rmin = __fmul_rn(0.75f, kappa);
+    } else {
+      float cn = __fsqrt_rn(__fmaf_rn(o.cx, o.cx, __fmaf_rn(o.cy, o.cy, __fmul_rn(o.cz, o.cz))));
+      rmin = __fmul_rn(0.75f, __fmul_rn(cn, kappa));
+    }
     if (rmin > r) R = rmin;
   }
   o.R = R;
@@ -230,8 +247,13 @@ __device__ __forceinline__ Projected project_sphere(const float* B, const float*
   float key = __fsub_rn(o.cz, R);
   if (!(R > 0.0f) || !(key > znear) || !(key < zfar)) return o;
   int x0, x1, y0, y1;
-  axis_range(o.cx, o.cz, R, o.R2, kappa, width, x0, x1);
-  axis_range(o.cy, o.cz, R, o.R2, kappa, height, y0, y1);
+  if (ortho) {
+    axis_range_ortho(o.cx, R, kappa, width, x0, x1);
+    axis_range_ortho(o.cy, R, kappa, height, y0, y1);
+  } else {
+    axis_range(o.cx, o.cz, R, o.R2, kappa, width, x0, x1);
+    axis_range(o.cy, o.cz, R, o.R2, kappa, height, y0, y1);
+  }
   if (x1 < 0 || x0 > width - 1 || y1 < 0 || y0 > height - 1) return o;
   o.x0 = max(x0, 0);
   o.x1 = min(x1, width - 1);

@@ -74,6 +74,7 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
   const float inv_gamma = 1.0f / gamma;
   const float inv_range = 1.0f / (zfar - znear);
   const bool literal = (S.flags & PULSAR_FLAG_DIST_LITERAL) != 0;
+  const bool ortho = (S.flags & PULSAR_FLAG_ORTHOGRAPHIC) != 0;
   const bool geo = (mask & (PULSAR_GRAD_POS | PULSAR_GRAD_RAD | PULSAR_GRAD_CAM)) != 0;
   const bool opa = (mask & PULSAR_GRAD_OPA) != 0;
   const bool feat = (mask & PULSAR_GRAD_FEAT) != 0;
@@ -162,13 +163,13 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
         break;
       }
       RayHit h;
-      if (!ray_hit(a.x, a.y, a.z, a.w, b.x, pc.rx, pc.ry, zfar, h)) continue;
+      if (!pixel_ray_hit(a, b.x, pc.rx, pc.ry, zfar, ortho, h)) continue;
       const int id = sb.id[cur][j];
       if (hit_less(thr_t, thr_i, h.t, id)) continue;   // beyond the tracked set
       float gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, gR = 0.f, go = 0.f;
       float gf[CMAX];
       const float4 c2 = sb.rec2[cur][j];
-      const ValueGeom g = value_geom(a, c2, pc.vr);
+      const ValueGeom g = pixel_value_geom(a, c2, pc.vr, ortho);
       const float R = c2.w;
       const float inv_rr = vdiv(1.0f, g.rr);
       const float qd = g.qd;            // as the forward pass blended it
@@ -204,8 +205,9 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
         gdist = sgn * vdiv(gd, R);
         gR = -sgn * gd * vdiv(qd, R);
       }
-      // e = (r x (c x r)) / |r|^2 with c x r = (-ey, ex, ez)
-      const float rx = pc.vr.rx, ry = pc.vr.ry;
+      // e = (r x (c x r)) / |r|^2 with c x r = (-ey, ex, ez); orthographic:
+      // c the shifted centre and r = (0, 0, 1)
+      const float rx = ortho ? 0.0f : pc.vr.rx, ry = ortho ? 0.0f : pc.vr.ry;
       const float e0 = (ry * g.ez - g.ex) * inv_rr;
       const float e1 = (-g.ey - rx * g.ez) * inv_rr;
       const float e2 = (rx * g.ex + ry * g.ey) * inv_rr;
@@ -240,7 +242,9 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
       }
       const float pxo = (float)(2 * pc.px + 1 - S.width) * 0.5f;
       const float pyo = (float)(2 * pc.py + 1 - S.height) * 0.5f;
-      gk_sum += grx * pxo + gry * pyo;
+      // the pitch enters through the ray slopes (pinhole) or through the
+      // shift c - k (pxo, pyo, 0) of the centre (orthographic)
+      gk_sum += ortho ? -(gc0 * pxo + gc1 * pyo) : grx * pxo + gry * pyo;
       add_hit_grads<CMAX>(id, (int64_t)id - S.sphere_begin, gc0, gc1, gc2, gR, go, gf, C, v, S, geo,
                           opa, feat);
     }

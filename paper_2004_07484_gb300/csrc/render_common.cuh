@@ -305,6 +305,34 @@ __device__ __forceinline__ bool ray_disc_positive(float cx, float cy, float cz, 
   return __fmaf_rn(rr, R2, -cr2) > 0.0f;
 }
 
+// The pixel ray of either camera.  An orthographic ray starts at
+// (rx, ry, 0) and runs along +z: the pinhole routines then apply to the
+// shifted centre c - (rx, ry, 0) and the ray (0, 0, 1), in the same float32
+// operations (the shift is one rounded subtraction).
+__device__ __forceinline__ bool pixel_disc_positive(const float4& a, float rx, float ry, bool ortho) {
+  return ortho ? ray_disc_positive(__fsub_rn(a.x, rx), __fsub_rn(a.y, ry), a.z, a.w, 0.0f, 0.0f)
+               : ray_disc_positive(a.x, a.y, a.z, a.w, rx, ry);
+}
+
+__device__ __forceinline__ bool pixel_ray_hit(const float4& a, float tmin, float rx, float ry, float zfar,
+                                              bool ortho, RayHit& h) {
+  return ortho ? ray_hit(__fsub_rn(a.x, rx), __fsub_rn(a.y, ry), a.z, a.w, tmin, 0.0f, 0.0f, zfar, h)
+               : ray_hit(a.x, a.y, a.z, a.w, tmin, rx, ry, zfar, h);
+}
+
+// Value-path geometry for either camera: the orthographic shift of the
+// float-float centre is exact in its leading part (TwoSum).
+__device__ __forceinline__ ValueGeom pixel_value_geom(const float4& a, const float4& c2, const ValueRay& r,
+                                                      bool ortho) {
+  if (!ortho) return value_geom(a, c2, r);
+  const FF sx = two_sum(a.x, -r.rx), sy = two_sum(a.y, -r.ry);
+  const float4 a2 = make_float4(sx.hi, sy.hi, a.z, a.w);
+  const float4 c22 = make_float4(__fadd_rn(__fsub_rn(c2.x, r.rx_lo), sx.lo),
+                                 __fadd_rn(__fsub_rn(c2.y, r.ry_lo), sy.lo), c2.z, c2.w);
+  const ValueRay axis = {0.0f, 0.0f, 0.0f, 0.0f};
+  return value_geom(a2, c22, axis);
+}
+
 // (t, id) ordering of tracked hits: by depth, then by sphere index.
 __device__ __forceinline__ bool hit_less(float t, int id, float qt, int qi) {
   return t < qt || (t == qt && id < qi);

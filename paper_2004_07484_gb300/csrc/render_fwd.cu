@@ -105,6 +105,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   const float range = zfar - znear, inv_range = 1.0f / range;
   const float omax = __uint_as_float(S.omax_bits);
   const bool literal = (S.flags & PULSAR_FLAG_DIST_LITERAL) != 0;
+  const bool ortho = (S.flags & PULSAR_FLAG_ORTHOGRAPHIC) != 0;
   const int lane = threadIdx.x;
 
   // the first batches of the block list stage while the state is set up
@@ -167,13 +168,13 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
       float t = 0.0f;
       if (may_queue || !(fmaf(1.0001f, a.z, 1.001f * c2.w) < zfar)) {
         RayHit h;
-        if (!ray_hit(a.x, a.y, a.z, a.w, b.x, pc.rx, pc.ry, zfar, h)) continue;
+        if (!pixel_ray_hit(a, b.x, pc.rx, pc.ry, zfar, ortho, h)) continue;
         t = h.t;
       }
       ++nhit;
       const int id = sb.id[cur][j];
       if (BLEND) {
-        const ValueGeom vg = value_geom(a, c2, pc.vr);
+        const ValueGeom vg = pixel_value_geom(a, c2, pc.vr, ortho);
         const float qd = fminf(vg.qd, 1.0f);
         const float d = literal ? qd : 1.0f - qd;
         const float od = b.y * d;

@@ -37,6 +37,7 @@ class RenderSettings:
     persistent: bool = False         # scheduling: persistent render kernels
     accumulate: bool = False         # backward adds into the gradient buffers (views sharing them)
     paper_gradients: bool = False    # the paper's gradient normalisations (App. B, Sec. 6)
+    orthographic: bool = False       # orthographic camera: pitch = sensor width / W (Sec. 1)
 
     def flags(self) -> int:
         f = 0
@@ -52,6 +53,8 @@ class RenderSettings:
             f |= _lib.FLAG_ACCUMULATE
         if self.paper_gradients:
             f |= _lib.FLAG_PAPER_GRADIENTS
+        if self.orthographic:
+            f |= _lib.FLAG_ORTHOGRAPHIC
         return f
 
     def params(self, n_spheres: int, capacity: int) -> _lib.Params:

@@ -22,7 +22,8 @@ def settings_of(scene: Scene, store=True, dist_literal=False, min_size=True, n_t
     return RenderSettings(scene.width, scene.height, scene.n_channels,
                           n_track or scene.n_track, float(scene.gamma), float(scene.eps),
                           float(scene.znear), float(scene.zfar), store, dist_literal, min_size,
-                          segment=segment, persistent=persistent, paper_gradients=paper)
+                          segment=segment, persistent=persistent, paper_gradients=paper,
+                          orthographic=bool(getattr(scene, "ortho", False)))
 
 
 def gpu_forward(scene: Scene, store=True, dist_literal=False, min_size=True, capacity=None,

@@ -158,4 +158,5 @@ def test_fit_entry_points_reject_bad_arguments_on_the_host(lib):
     assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=lib.FLAG_ACCUMULATE))) > 0
     assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=lib.FLAG_PAPER_GRADIENTS))) > \
         L.pulsar_workspace_size(ctypes.byref(_params(lib)))   # per-sphere sums of the paper mode
-    assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=1 << 6))) == 0
+    assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=lib.FLAG_ORTHOGRAPHIC))) > 0
+    assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=1 << 7))) == 0
