@@ -31,7 +31,8 @@ EXPORTED = ("pulsar_workspace_size", "pulsar_project", "pulsar_bin", "pulsar_ren
             "pulsar_project_batched", "pulsar_bin_batched", "pulsar_render_fwd_batched",
             "pulsar_render_bwd_batched", "pulsar_read_tile_lists_batched",
             "pulsar_probe_fma_throughput", "pulsar_last_overflow", "pulsar_render_batched",
-            "pulsar_image_loss", "pulsar_adam_step")
+            "pulsar_image_loss", "pulsar_adam_step", "pulsar_camera_from_axis_angle",
+            "pulsar_camera_axis_angle_backward", "pulsar_prune_scratch_bytes", "pulsar_prune", "pulsar_subdivide")
 
 MAX_SCENES = 64
 LOSS_L2, LOSS_L1 = 0, 1
@@ -137,6 +138,17 @@ def lib():
         L.pulsar_image_loss.restype = ctypes.c_int
         L.pulsar_adam_step.argtypes = [i32, ctypes.POINTER(AdamTensor), ctypes.POINTER(AdamHyper), vp, vp]
         L.pulsar_adam_step.restype = ctypes.c_int
+        L.pulsar_camera_from_axis_angle.argtypes = [vp, vp, i32, vp]
+        L.pulsar_camera_from_axis_angle.restype = ctypes.c_int
+        L.pulsar_camera_axis_angle_backward.argtypes = [vp, vp, vp, i32, vp]
+        L.pulsar_camera_axis_angle_backward.restype = ctypes.c_int
+        i64, f32 = ctypes.c_int64, ctypes.c_float
+        L.pulsar_prune_scratch_bytes.argtypes = [i64]
+        L.pulsar_prune_scratch_bytes.restype = sz
+        L.pulsar_prune.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, f32, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.pulsar_prune.restype = ctypes.c_int
+        L.pulsar_subdivide.argtypes = [i64, i32, vp, vp, vp, vp, f32, f32, vp, vp, vp, vp, vp]
+        L.pulsar_subdivide.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -263,3 +275,28 @@ def image_loss(kind: int, image: int, target: int, n: int, scale: float, grad: i
 def adam_step(tensors, hyper: AdamHyper, state: int, stream: int) -> None:
     """`tensors`: ctypes array of AdamTensor."""
     _check(lib().pulsar_adam_step(len(tensors), tensors, ctypes.byref(hyper), state, stream), "pulsar_adam_step")
+
+
+def camera_from_axis_angle(cam8: int, cam11: int, n: int, stream: int) -> None:
+    _check(lib().pulsar_camera_from_axis_angle(cam8, cam11, int(n), stream), "pulsar_camera_from_axis_angle")
+
+
+def camera_axis_angle_backward(cam8: int, g_cam11: int, g_cam8: int, n: int, stream: int) -> None:
+    _check(lib().pulsar_camera_axis_angle_backward(cam8, g_cam11, g_cam8, int(n), stream),
+           "pulsar_camera_axis_angle_backward")
+
+
+def prune_scratch_bytes(n: int) -> int:
+    return int(lib().pulsar_prune_scratch_bytes(int(n)))
+
+
+def prune(n, C, pos, rad, opa, feat, bg, activity, color_tol, out_pos, out_rad, out_opa, out_feat, n_out,
+          scratch, scratch_bytes, stream) -> None:
+    _check(lib().pulsar_prune(int(n), int(C), pos, rad, opa, feat, bg, activity, float(color_tol), out_pos, out_rad,
+                              out_opa, out_feat, n_out, scratch, int(scratch_bytes), stream), "pulsar_prune")
+
+
+def subdivide(n, C, pos, rad, opa, feat, offset_scale, radius_scale, out_pos, out_rad, out_opa, out_feat,
+              stream) -> None:
+    _check(lib().pulsar_subdivide(int(n), int(C), pos, rad, opa, feat, float(offset_scale), float(radius_scale),
+                                  out_pos, out_rad, out_opa, out_feat, stream), "pulsar_subdivide")

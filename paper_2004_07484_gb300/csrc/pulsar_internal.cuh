@@ -411,6 +411,37 @@ __device__ __forceinline__ int scene_of_sphere(const SceneDev* scenes, int n_sce
   return lo;
 }
 
+// Block-wide exclusive scan of one value per thread (kThreads or 1024 threads).
+template <int NT>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot,
+                                                         uint32_t& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < NT / 32 ? warp_tot[lane] : 0;
+    uint32_t s = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < NT / 32) warp_tot[lane] = s - w;
+    if (lane == NT / 32 - 1) warp_tot[32] = s;
+  }
+  __syncthreads();
+  uint32_t r = warp_tot[warp] + x - v;
+  total = warp_tot[32];
+  __syncthreads();
+  return r;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -50,37 +50,6 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __rest
   hist[threadIdx.x * stride + blockIdx.x] = h[threadIdx.x];
 }
 
-// Block-wide exclusive scan of one value per thread (kThreads or 1024 threads).
-template <int NT>
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot,
-                                                         uint32_t& total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) warp_tot[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < NT / 32 ? warp_tot[lane] : 0;
-    uint32_t s = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane < NT / 32) warp_tot[lane] = s - w;
-    if (lane == NT / 32 - 1) warp_tot[32] = s;
-  }
-  __syncthreads();
-  uint32_t r = warp_tot[warp] + x - v;
-  total = warp_tot[32];
-  __syncthreads();
-  return r;
-}
-
 // Exclusive scan, in place, of one digit's row of per-CTA counts
 // (row r = blockIdx.x, cols = ceil(n / kSortTile) entries at data[r * stride]),
 // and the row's total into row_tot[r].  One CTA per digit.

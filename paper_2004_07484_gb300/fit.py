@@ -178,3 +178,44 @@ class ViewFit:
                 self.replay()
             else:
                 self.step()
+
+
+# Pruning and subdivision between fit stages (Sec. 5, head reconstruction):
+# spheres whose colour converged to the background or that received no
+# gradient are removed; every sphere can be refined into 12 in a face-centred
+# cubic arrangement.  The printed child radius ("sqrt 2 r") cannot be a
+# refinement; the defaults below place the 12 children at distance r / sqrt 2
+# with radius r / (2 sqrt 2), so neighbouring children touch and all stay
+# within about the parent's radius.
+SUBDIVIDE_OFFSET = 2.0 ** -0.5
+SUBDIVIDE_RADIUS = 2.0 ** -1.5
+
+
+def prune_spheres(pos, rad, opa, feat, bg, activity=None, color_tol: float = -1.0):
+    """The kept spheres, in order: (pos, rad, opa, feat)."""
+    M, C = int(pos.shape[0]), int(feat.shape[1])
+    dev = pos.device
+    outs = (torch.empty_like(pos), torch.empty_like(rad), torch.empty_like(opa), torch.empty_like(feat))
+    n_out = torch.zeros((1,), dtype=torch.int64, device=dev)
+    nb = _lib.prune_scratch_bytes(M)
+    scratch = torch.empty((max(nb, 16),), dtype=torch.uint8, device=dev)
+    args = [t.contiguous() for t in (pos, rad, opa, feat, bg)]
+    act = None if activity is None else activity.contiguous()
+    _lib.prune(M, C, *[t.data_ptr() for t in args], None if act is None else act.data_ptr(), color_tol,
+               *[t.data_ptr() for t in outs], n_out.data_ptr(), scratch.data_ptr(), scratch.numel(),
+               torch.cuda.current_stream(dev).cuda_stream)
+    n = int(n_out.item())
+    return tuple(t[:n].clone() for t in outs)
+
+
+def subdivide_spheres(pos, rad, opa, feat, offset_scale: float = SUBDIVIDE_OFFSET,
+                      radius_scale: float = SUBDIVIDE_RADIUS):
+    """Each sphere as 12 children: (pos, rad, opa, feat) with 12 M spheres."""
+    M, C = int(pos.shape[0]), int(feat.shape[1])
+    dev = pos.device
+    outs = (torch.empty((12 * M, 3), device=dev), torch.empty((12 * M,), device=dev),
+            torch.empty((12 * M,), device=dev), torch.empty((12 * M, C), device=dev))
+    args = [t.contiguous() for t in (pos, rad, opa, feat)]
+    _lib.subdivide(M, C, *[t.data_ptr() for t in args], offset_scale, radius_scale, *[t.data_ptr() for t in outs],
+                   torch.cuda.current_stream(dev).cuda_stream)
+    return outs

@@ -271,11 +271,41 @@ class _RenderFunction(torch.autograd.Function):
         return None, g_pos, g_feat, g_rad, g_opa, g_cam, g_bg
 
 
+class _AxisAngleCamera(torch.autograd.Function):
+    """Listing 1's 8-vector camera [t, axis-angle rotation, focal, sensor
+    width] as the renderer's 11-vector, with the gradient back through the
+    conversion (both in the library)."""
+
+    @staticmethod
+    def forward(ctx, cam8):
+        cam8 = cam8.contiguous()
+        cam11 = torch.empty((11,), dtype=torch.float32, device=cam8.device)
+        _lib.camera_from_axis_angle(cam8.data_ptr(), cam11.data_ptr(), 1,
+                                    torch.cuda.current_stream(cam8.device).cuda_stream)
+        ctx.save_for_backward(cam8)
+        return cam11
+
+    @staticmethod
+    def backward(ctx, g11):
+        (cam8,) = ctx.saved_tensors
+        g11 = g11.contiguous()
+        g8 = torch.empty((8,), dtype=torch.float32, device=cam8.device)
+        _lib.camera_axis_angle_backward(cam8.data_ptr(), g11.data_ptr(), g8.data_ptr(), 1,
+                                        torch.cuda.current_stream(cam8.device).cuda_stream)
+        return g8
+
+
+def camera_from_axis_angle(cam8: torch.Tensor) -> torch.Tensor:
+    """The 11-vector camera of an 8-vector [t(3), axis-angle(3), focal, sensor width]."""
+    return _AxisAngleCamera.apply(_dev_f32("cam", cam8, (8,)))
+
+
 class Renderer(torch.nn.Module):
     """Differentiable sphere renderer for a fixed image size (Listing 1).
 
     ``forward(pos, feat, rad, cam, opa=None, bg=None)`` returns the H x W x C
     feature image.  ``cam`` is the 11-vector [t, 6D rotation, focal, sensor
+    width] or Listing 1's 8-vector [t, axis-angle rotation, focal, sensor
     width]; opacities default to 1 and the background to 0.
     """
 
@@ -312,6 +342,8 @@ class Renderer(torch.nn.Module):
         feat = _dev_f32("feat", feat, (M, C))
         rad = _dev_f32("rad", rad, (M,))
         opa = _dev_f32("opa", opa, (M,))
+        if cam.numel() == 8:
+            cam = camera_from_axis_angle(cam.reshape(8))
         cam = _dev_f32("cam", cam, (11,))
         bg = _dev_f32("bg", bg, (C,))
         image, log_norm = _RenderFunction.apply(self, pos, feat, rad, opa, cam, bg)

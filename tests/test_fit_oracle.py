@@ -5,7 +5,9 @@
   - the box projection against clipping of the unconstrained step;
   - the losses against hand-computed values and central differences;
   - the multi-view gradient of the fit (loss gradient through every view's
-    backward pass, summed) against central differences of the total loss.
+    backward pass, summed) against central differences of the total loss;
+  - the camera of Listing 1: Rodrigues' rotation against scipy's rotation
+    vectors, and the renderer's Gram-Schmidt giving the rotation back.
 """
 import numpy as np
 import pytest
@@ -139,3 +141,59 @@ def test_fit_loop_lowers_the_loss(orc, fit_orc):
     assert len(losses) == 4 and final < losses[0]
     assert p["opa"].min() >= 0.0 and p["opa"].max() <= 1.0 and p["rad"].min() >= 1e-4
     assert all(p[k].dtype == np.float32 for k in p)
+
+
+# ---------------------------------------------------------------- camera of Listing 1
+
+def test_axis_angle_rotation_matches_scipy_and_gram_schmidt(orc):
+    from scipy.spatial.transform import Rotation
+    from oracle import scene_utils
+    rng = np.random.default_rng(4)
+    for w in [np.zeros(3), np.array([1e-9, 0.0, 0.0]), *rng.normal(size=(6, 3)) * 1.5]:
+        B = scene_utils.rotation(w)
+        np.testing.assert_allclose(B, Rotation.from_rotvec(w).as_matrix(), atol=1e-14)
+        cam = scene_utils.cam11_from_cam8(np.concatenate([[0.1, 0.2, 0.3], w, [1.5, 2.0]]))
+        # the renderer's Gram-Schmidt of the two rows gives back B
+        np.testing.assert_allclose(orc.rows(cam[3:9]).reshape(3, 3), B, atol=1e-14)
+        assert cam[9] == 1.5 and cam[10] == 2.0 and np.array_equal(cam[:3], [0.1, 0.2, 0.3])
+
+
+# ---------------------------------------------------------------- pruning and subdivision
+
+def test_fcc_directions_are_a_cuboctahedron():
+    """The 12 nearest neighbours of a face-centred cubic site: unit vectors
+    summing to zero, whose nearest pairwise distance equals the radius (the
+    cuboctahedron's edge equals its circumradius), each with 4 such neighbours."""
+    from oracle import scene_utils
+    u = scene_utils.FCC_DIRECTIONS
+    assert u.shape == (12, 3) and len({tuple(np.round(x, 12)) for x in u}) == 12
+    np.testing.assert_allclose(np.linalg.norm(u, axis=1), 1.0, atol=1e-15)
+    np.testing.assert_allclose(u.sum(axis=0), 0.0, atol=1e-14)
+    d = np.linalg.norm(u[:, None] - u[None], axis=2) + np.eye(12) * 9
+    np.testing.assert_allclose(d.min(axis=1), 1.0, atol=1e-14)
+    assert np.all((np.abs(d - 1.0) < 1e-12).sum(axis=1) == 4)
+
+
+def test_subdivision_and_pruning_properties():
+    from oracle import scene_utils
+    rng = np.random.default_rng(7)
+    pos, rad = rng.normal(size=(5, 3)), rng.uniform(0.1, 1.0, 5)
+    opa, feat = rng.uniform(0, 1, 5), rng.uniform(0, 1, (5, 3))
+    cp, cr, co, cf = scene_utils.subdivide(pos, rad, opa, feat, 0.7, 0.3)
+    assert cp.shape == (60, 3)
+    np.testing.assert_allclose(cp.reshape(5, 12, 3).mean(axis=1), pos, atol=1e-14)   # centred on the parent
+    np.testing.assert_allclose(np.linalg.norm(cp.reshape(5, 12, 3) - pos[:, None], axis=2),
+                               0.7 * rad[:, None].repeat(12, 1), rtol=1e-14)
+    assert np.all(cr == np.repeat(0.3 * rad, 12)) and np.all(co == np.repeat(opa, 12))
+    # pruning: no criterion keeps everything; a larger tolerance keeps a subset; the
+    # float32 decision agrees with float64 away from the threshold
+    f = rng.uniform(0, 1, (500, 4)).astype(np.float32)
+    bg = np.float32([0.5, 0.5, 0.5, 0.5])
+    assert scene_utils.prune_keep(f, bg).all()
+    k1, k2 = scene_utils.prune_keep(f, bg, color_tol=0.4), scene_utils.prune_keep(f, bg, color_tol=0.6)
+    assert np.all(k2 <= k1) and k1.sum() > k2.sum() > 0
+    dist = np.linalg.norm(f.astype(np.float64) - bg, axis=1)
+    far = np.abs(dist - 0.4) > 1e-5
+    assert np.array_equal(k1[far], dist[far] > 0.4)
+    act = rng.uniform(-1, 1, 500).astype(np.float32)
+    assert np.array_equal(scene_utils.prune_keep(f, bg, act), act > 0)

@@ -315,3 +315,92 @@ def test_fit_overflow_is_reported_and_grown(orc, fit_orc):
     ref, _ = fit_orc.loss_and_grads(start, {k: getattr(start, k) for k in names}, cams, targets)
     F0 = [orc.render(fit_orc.view_scene(start, {k: getattr(start, k) for k in names}, c)).image for c in cams]
     assert abs(loss - ref) <= sum(_loss_bound(f, t) for f, t in zip(F0, targets))
+
+
+def test_listing1_camera_conversion_and_gradient(orc):
+    """The 8-vector camera of Listing 1 (axis-angle rotation): the library's
+    conversion against the oracle's Rodrigues formula, its gradient against
+    the oracle's Jacobian (central differences in float64) applied to the
+    renderer's camera gradient, and a Renderer call with either camera form."""
+    import torch
+    from oracle import scene_utils
+    from paper_2004_07484_gb300 import _lib, Renderer
+    rng = np.random.default_rng(17)
+    cams8 = np.concatenate([rng.normal(size=(5, 3)), rng.normal(size=(5, 3)) * 1.2,
+                            rng.uniform(0.5, 2.0, (5, 1)), rng.uniform(1.0, 3.0, (5, 1))], axis=1)
+    cams8[0, 3:6] = 0.0
+    cams8[1, 3:6] = [1e-5, -2e-5, 0.0]
+    cams8 = cams8.astype(np.float32)
+    d8 = torch.from_numpy(cams8).cuda()
+    d11 = torch.empty((5, 11), device="cuda")
+    _lib.camera_from_axis_angle(d8.data_ptr(), d11.data_ptr(), 5, _stream())
+    g11 = rng.normal(size=(5, 11)).astype(np.float32)
+    dg8 = torch.empty((5, 8), device="cuda")
+    _lib.camera_axis_angle_backward(d8.data_ptr(), torch.from_numpy(g11).cuda().data_ptr(), dg8.data_ptr(), 5,
+                                    _stream())
+    torch.cuda.synchronize()
+    for k in range(5):
+        c8 = cams8[k].astype(np.float64)
+        np.testing.assert_allclose(d11[k].cpu().numpy(), scene_utils.cam11_from_cam8(c8), rtol=0, atol=2e-7)
+        J = np.zeros((11, 8))
+        for j in range(8):
+            h = 1e-6
+            cp, cm = c8.copy(), c8.copy()
+            cp[j] += h
+            cm[j] -= h
+            J[:, j] = (scene_utils.cam11_from_cam8(cp) - scene_utils.cam11_from_cam8(cm)) / (2 * h)
+        want = J.T @ g11[k].astype(np.float64)
+        np.testing.assert_allclose(dg8[k].cpu().numpy(), want, rtol=0, atol=2e-6 * max(1.0, np.abs(want).max()))
+    # a Renderer call with the 8-vector equals one with the converted 11-vector
+    sc = S.config_scene(0)
+    r = Renderer(sc.width, sc.height, sc.n_spheres, n_channels=3, n_track=5, gamma=0.1)
+    pos = torch.from_numpy(sc.pos).cuda()
+    feat = torch.from_numpy(sc.feat).cuda()
+    rad = torch.from_numpy(sc.rad).cuda()
+    c8 = torch.tensor([0.02, -0.01, 0.05, 0.03, -0.02, 0.01, 1.0, 2.0], device="cuda", requires_grad=True)
+    img8 = r(pos, feat, rad, c8)
+    (img8 * 1.0).sum().backward()
+    c11 = torch.from_numpy(scene_utils.cam11_from_cam8(c8.detach().cpu().numpy().astype(np.float64))
+                           .astype(np.float32)).cuda().requires_grad_(True)
+    img11 = r(pos, feat, rad, c11)
+    img11.sum().backward()
+    assert (img8 - img11).abs().max().item() <= 1e-5
+    J = np.zeros((11, 8))
+    base = c8.detach().cpu().numpy().astype(np.float64)
+    for j in range(8):
+        cp, cm = base.copy(), base.copy()
+        cp[j] += 1e-6
+        cm[j] -= 1e-6
+        J[:, j] = (scene_utils.cam11_from_cam8(cp) - scene_utils.cam11_from_cam8(cm)) / 2e-6
+    want = J.T @ c11.grad.cpu().numpy().astype(np.float64)
+    got = c8.grad.cpu().numpy()
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-3 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("n", [0, 1, 2047, 2049, 100_003])
+def test_prune_and_subdivide_match_oracle(n):
+    """Pruning (kept set bit-exact: the same float32 decision on both sides,
+    order preserved) and subdivision (children within float rounding) against
+    the oracle, for sizes around the 2048-sphere tiles of the compaction."""
+    import torch
+    from oracle import scene_utils
+    from paper_2004_07484_gb300.fit import prune_spheres, subdivide_spheres
+    rng = np.random.default_rng(n + 1)
+    pos = rng.normal(size=(n, 3)).astype(np.float32)
+    rad = rng.uniform(0.01, 0.2, n).astype(np.float32)
+    opa = rng.uniform(0, 1, n).astype(np.float32)
+    feat = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    bg = np.float32([0.5, 0.4, 0.6])
+    act = np.where(rng.uniform(0, 1, n) < 0.2, 0.0, rng.uniform(0, 1, n)).astype(np.float32)
+    d = [torch.from_numpy(x).cuda() for x in (pos, rad, opa, feat, bg, act)]
+    for activity, tol in ((None, -1.0), (d[5], -1.0), (d[5], 0.35), (None, 0.5)):
+        got = prune_spheres(*d[:5], activity=activity, color_tol=tol)
+        keep = scene_utils.prune_keep(feat, bg, None if activity is None else act, tol)
+        for g, want in zip(got, (pos, rad, opa, feat)):
+            np.testing.assert_array_equal(g.cpu().numpy(), want[keep])
+    cp, cr, co, cf = subdivide_spheres(*d[:4], offset_scale=0.7, radius_scale=0.3)
+    wp, wr, wo, wf = scene_utils.subdivide(pos, rad, opa, feat, 0.7, 0.3)
+    np.testing.assert_allclose(cp.cpu().numpy(), wp, rtol=0, atol=4e-7 * max(1.0, np.abs(wp).max() if n else 1.0))
+    np.testing.assert_allclose(cr.cpu().numpy(), wr, rtol=1e-7)
+    np.testing.assert_array_equal(co.cpu().numpy(), wo.astype(np.float32))
+    np.testing.assert_array_equal(cf.cpu().numpy(), wf.astype(np.float32))
