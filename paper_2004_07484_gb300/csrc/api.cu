@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "pulsar_internal.cuh"
 
@@ -10,6 +11,40 @@ namespace pulsar {
 namespace {
 
 constexpr size_t kAlign = 256;
+
+// A second stream per device for launches that may overlap the main
+// sequence, with its fork and join events; created on first use.  The mutex
+// makes each fork - launch - join sequence atomic among host threads (a
+// stream wait binds to the event's latest record when it is issued).
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::mutex g_side_mutex;
+SideStream g_side[64];
+
+cudaError_t side_stream(SideStream*& out) {   // call with g_side_mutex held
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  SideStream& sd = g_side[dev];
+  if (!sd.s) {
+    SideStream made;
+    e = cudaStreamCreateWithFlags(&made.s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&made.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&made.join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      if (made.join) cudaEventDestroy(made.join);
+      if (made.fork) cudaEventDestroy(made.fork);
+      if (made.s) cudaStreamDestroy(made.s);
+      return e;
+    }
+    sd = made;
+  }
+  out = &sd;
+  return cudaSuccess;
+}
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -318,8 +353,18 @@ pulsar_status fwd_n(int n, const pulsar_params* params, const pulsar_scene* scen
   for (int k = 0; k < n; ++k) tests = tests || out[k].n_tests != nullptr;
   cudaError_t e = launch_setup(v, d, -n, s);
   if (e == cudaSuccess && tests) e = launch_count_tests(v, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  // the pixels of empty tiles (background pass) are written on the side
+  // stream while the render pass draws the others
+  std::lock_guard<std::mutex> lock(g_side_mutex);
+  SideStream* side = nullptr;
+  e = side_stream(side);
+  if (e == cudaSuccess) e = cudaEventRecord(side->fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(side->s, side->fork, 0);
+  if (e == cudaSuccess) e = launch_background(v, false, 0u, side->s);
+  if (e == cudaSuccess) e = cudaEventRecord(side->join, side->s);
   if (e == cudaSuccess) e = launch_render_fwd(v, s);
-  if (e == cudaSuccess) e = launch_background(v, false, 0u, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, side->join, 0);
   return cuda_status(e);
 }
 
@@ -358,13 +403,27 @@ pulsar_status bwd_n(int n, const pulsar_params* params, const pulsar_scene* scen
     d[k].g_bg = q.g_bg;
   }
   cudaError_t e = launch_setup(v, d, -n, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  // the background-gradient partials of empty tiles are summed on the side
+  // stream while the render pass runs; the camera reduction joins them
+  std::lock_guard<std::mutex> lock(g_side_mutex);
+  SideStream* side = nullptr;
+  const bool bg = (grad_mask & PULSAR_GRAD_BG) != 0;
+  if (bg) {
+    e = side_stream(side);
+    if (e == cudaSuccess) e = cudaEventRecord(side->fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side->s, side->fork, 0);
+    if (e == cudaSuccess) e = launch_background(v, true, grad_mask, side->s);
+    if (e == cudaSuccess) e = cudaEventRecord(side->join, side->s);
+  }
   if (e == cudaSuccess) e = launch_zero_grads(v, grad_mask, s);
   const bool geo_or_values = (grad_mask & ~(uint32_t)PULSAR_GRAD_BG) != 0;
   if (e == cudaSuccess && geo_or_values && !(params[0].flags & PULSAR_FLAG_STORE_HITS))
     e = launch_track_pass(v, s);
   if (e == cudaSuccess) e = launch_render_bwd(v, grad_mask, s);
-  if (e == cudaSuccess && (grad_mask & PULSAR_GRAD_BG)) e = launch_background(v, true, grad_mask, s);
   if (e == cudaSuccess) e = launch_finalize(v, grad_mask, s);
+  if (e == cudaSuccess && bg) e = cudaStreamWaitEvent(s, side->join, 0);
+  if (e == cudaSuccess) e = launch_camera_reduce(v, grad_mask, s);
   return cuda_status(e);
 }
 

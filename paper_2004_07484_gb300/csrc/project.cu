@@ -464,6 +464,10 @@ cudaError_t launch_finalize(const WsView& v, uint32_t mask, cudaStream_t st) {
                             (v.paper ? (PULSAR_GRAD_OPA | PULSAR_GRAD_FEAT) : 0u);
   if (v.fin_blocks > 0 && (mask & fin_mask))
     finalize_kernel<<<v.fin_blocks, kFinalizeThreads, 0, st>>>(v, mask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_camera_reduce(const WsView& v, uint32_t mask, cudaStream_t st) {
   if (mask & (PULSAR_GRAD_CAM | PULSAR_GRAD_BG)) {
     camera_partials_kernel<<<dim3(v.n_scenes, kRedParts), 256, 0, st>>>(v, mask);
     camera_reduce_kernel<<<v.n_scenes, 64, 0, st>>>(v, mask);

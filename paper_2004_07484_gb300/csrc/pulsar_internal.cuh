@@ -462,6 +462,7 @@ cudaError_t launch_render_fwd(const WsView& v, cudaStream_t st);
 cudaError_t launch_track_pass(const WsView& v, cudaStream_t st);
 cudaError_t launch_render_bwd(const WsView& v, uint32_t grad_mask, cudaStream_t st);
 cudaError_t launch_finalize(const WsView& v, uint32_t grad_mask, cudaStream_t st);
+cudaError_t launch_camera_reduce(const WsView& v, uint32_t grad_mask, cudaStream_t st);
 cudaError_t launch_zero_grads(const WsView& v, uint32_t grad_mask, cudaStream_t st);
 
 }  // namespace pulsar
