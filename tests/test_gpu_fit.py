@@ -404,3 +404,35 @@ def test_prune_and_subdivide_match_oracle(n):
     np.testing.assert_allclose(cr.cpu().numpy(), wr, rtol=1e-7)
     np.testing.assert_array_equal(co.cpu().numpy(), wo.astype(np.float32))
     np.testing.assert_array_equal(cf.cpu().numpy(), wf.astype(np.float32))
+
+
+def test_fit_with_l1_loss_matches_oracle(orc, fit_orc):
+    """The l1 loss of Sec. 3.4 through the whole loop: two steps against the
+    oracle's loop (loss within the 1e-4-per-value image tolerance summed over
+    the values, parameters within the bound the gradient tolerance gives)."""
+    from paper_2004_07484_gb300.fit import AdamSettings, ViewFit
+    import torch
+    hidden, start, cams, targets = _fit_problem(orc, fit_orc, n=800, res=56)
+    steps, lr = 2, 1e-3
+    dev = {k: torch.from_numpy(np.ascontiguousarray(getattr(start, k))).cuda()
+           for k in ("pos", "rad", "opa", "feat", "bg")}
+    vf = ViewFit(settings_of(start), [torch.from_numpy(c).cuda() for c in cams],
+                 torch.from_numpy(np.stack(targets)).cuda(), dev["pos"], dev["rad"], dev["opa"], dev["feat"],
+                 dev["bg"], max(16 * start.n_spheres, 1 << 14), AdamSettings(lr=lr, loss="l1"))
+    losses = [float(vf.step().item()) for _ in range(steps)]
+    names = fit_orc.PARAM_NAMES
+    hist = []
+    ref_losses, ref_p, _ = fit_orc.fit(start, {k: getattr(start, k) for k in names}, cams, targets, steps, lr=lr,
+                                       kind="l1", bounds={"rad": (1e-4, np.inf), "opa": (0.0, 1.0)}, history=hist)
+    n_values = sum(t.size for t in targets)
+    assert abs(losses[0] - ref_losses[0]) <= 1e-4 * n_values
+    final = float(vf.evaluate().item())
+    assert final < losses[0]
+    # dL/dF = sign(F - T) is decided by float rounding wherever one sphere dominates a pixel in
+    # both the start and the target (F - T of order 1e-6): whole pixel contributions flip sign
+    # between float32 and float64, so the parameters are held only to Adam's step size (each
+    # step moves a parameter by at most about lr)
+    for k in names:
+        got = vf.params[k].cpu().numpy().astype(np.float64)
+        diff = np.abs(got - ref_p[k].astype(np.float64)).ravel()
+        assert diff.max() <= 2 * steps * lr + 1e-6, k
