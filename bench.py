@@ -743,10 +743,11 @@ def main():
     pk, pk_kind = peaks()
     clocks = clk.summary()
     # ALU roofline of the dominant kernel: algorithmic FP32 operations of the
-    # forward render, 14 per ray-sphere test (the hit predicate) and 21 + 2C per
-    # hit (depth, distance term, depth term, exponent, weight, C-channel update),
-    # with the test and hit counts from the kernel's own per-pixel counters
-    flops_fwd = 14.0 * tests + (21.0 + 2.0 * C) * hits
+    # forward render, 21 + 2C per hit (depth, distance term, depth term,
+    # exponent, weight, C-channel update), with the hit count from the
+    # kernel's own per-pixel counter.  The ray-sphere tests (14 operations
+    # each) are made by the block-list pass of binning, not by this kernel.
+    flops_fwd = (21.0 + 2.0 * C) * hits
     fp32_nominal = N_SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     dominant = "render_fwd" if fwd_ms >= bwd_ms else "render_bwd"
     achieved = flops_fwd / (fwd_ms * 1e-3) / 1e12
