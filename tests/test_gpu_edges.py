@@ -316,3 +316,34 @@ def test_orthographic_batch_with_paper_gradients(orc):
         want = orc.render_backward(sc, G, paper_grad=True)
         got = {n: t.cpu().numpy().astype(np.float64) for n, t in zip(("pos", "rad", "opa", "feat", "cam", "bg"), g)}
         assert_grads_close(got, want, scene=sc)
+
+
+@pytest.mark.parametrize("ortho", [False, True])
+def test_test_rectangles_miss_no_hit(orc, ortho):
+    """The block lists test only the tangent bounds of each sphere's
+    projection widened by 1/8 pixel: every pixel's hit count must still equal
+    the oracle's brute-force count over all spheres, for spheres from 0.2 to
+    20 pixels in radius, centred anywhere including beyond the image borders,
+    under a rotated wide-angle camera."""
+    g = np.random.default_rng(31 + ortho)
+    W, H, n = 96, 80, 3000
+    rows = S.random_rotation(g).T
+    t = np.array([0.1, -0.2, 0.3])
+    cam = S.make_cam(t=t, rot6=S.rot6_from_matrix(rows), focal=0.8, sensor_width=(6.0 if ortho else 2.4))
+    zc = g.uniform(1.5, 15.0, n)
+    k = (6.0 / W) if ortho else (2.4 / (W * 0.8))
+    span = np.stack([W, H]) * 0.6 * k
+    xy = g.uniform(-1, 1, (n, 2)) * (span if ortho else span[None] * zc[:, None])
+    pc = np.concatenate([xy, zc[:, None]], axis=1)
+    pos = (rows.T @ pc.T).T + t
+    pix = k if ortho else k * zc
+    rad = pix * np.exp(g.uniform(np.log(0.2), np.log(20.0), n))
+    sc = S.Scene(pos.astype(np.float32), rad.astype(np.float32), g.uniform(0.3, 1, n).astype(np.float32),
+                 g.uniform(0, 1, (n, 3)).astype(np.float32), cam, np.zeros(3, np.float32), W, H, 0.05, 8,
+                 zfar=20.0, ortho=ortho)
+    ref = orc.render(sc)
+    gpu = gpu_forward(sc, capacity=1 << 20)
+    assert ref.n_hits.sum() > 10000
+    np.testing.assert_array_equal(gpu["n_hits"].cpu().numpy(), ref.n_hits)
+    np.testing.assert_array_equal(gpu["tracked"].cpu().numpy(), ref.tracked)
+    assert np.abs(gpu["image"].cpu().numpy() - ref.image).max() <= 1e-4
