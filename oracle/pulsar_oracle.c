@@ -33,7 +33,7 @@
  *               image; the focal length does not enter).  Everything below
  *               then holds for the shifted centre c' = c - (rho_x, rho_y, 0)
  *               and the ray (0, 0, 1); the minimum size is R = max(r, 0.75 k)
- *               and the rectangle is the centre -+ R in pixels.
+ *               and the rectangle is the centre -+ R in pixels (+- 1/8).
  *   min size    every sphere is drawn with at least one pixel (App. B,
  *               Step 0): R = max(r, 0.75 |c| k).
  *   depth       z = (zfar - t_h) / (zfar - znear) in [0, 1], 0 = max depth
@@ -111,9 +111,12 @@ static float kappa_f32(const float* cam, int width, int ortho) {
 
 /* One axis of the enclosing rectangle.  In the (axis, z) plane the sphere is a
  * disk of radius R about (cx, cz); the tangent lines through the eye have the
- * slopes m = (cx cz -+ R sqrt(cx^2 + cz^2 - R^2)) / (cz^2 - R^2).  The pixel
- * range between them, widened by one pixel on each side, contains every pixel
- * whose ray meets the sphere. */
+ * slopes m = (cx cz -+ R sqrt(cx^2 + cz^2 - R^2)) / (cz^2 - R^2).  The pixels
+ * whose centres lie between them, with the bounds widened by 1/8 pixel on
+ * each side against rounding (App. B, Step 0: the bounds are made robust to
+ * numerical inaccuracy; the float32 hit predicate's boundary lies within
+ * ~1e-4 pixel of the exact one), contain every pixel whose ray meets the
+ * sphere. */
 static void axis_range_f32(float cx, float cz, float R, float R2, float kappa, int n,
                            int* lo, int* hi) {
   float den = fmaf(cz, cz, -R2);
@@ -128,20 +131,20 @@ static void axis_range_f32(float cx, float cz, float R, float R2, float kappa, i
   float fhi = mhi / kappa + half;
   flo = fmaxf(fminf(flo, (float)n + 2.0f), -4.0f);
   fhi = fmaxf(fminf(fhi, (float)n + 2.0f), -4.0f);
-  *lo = (int)ceilf(flo) - 1;
-  *hi = (int)floorf(fhi) + 1;
+  *lo = (int)ceilf(flo - 0.125f);
+  *hi = (int)floorf(fhi + 0.125f);
 }
 
 /* One axis of the rectangle of the orthographic camera: the centre -+ R in
- * pixels, widened by one pixel on each side. */
+ * pixels, widened by 1/8 pixel on each side. */
 static void axis_range_ortho_f32(float cx, float R, float kappa, int n, int* lo, int* hi) {
   float half = (float)(n - 1) * 0.5f;
   float flo = (cx - R) / kappa + half;
   float fhi = (cx + R) / kappa + half;
   flo = fmaxf(fminf(flo, (float)n + 2.0f), -4.0f);
   fhi = fmaxf(fminf(fhi, (float)n + 2.0f), -4.0f);
-  *lo = (int)ceilf(flo) - 1;
-  *hi = (int)floorf(fhi) + 1;
+  *lo = (int)ceilf(flo - 0.125f);
+  *hi = (int)floorf(fhi + 0.125f);
 }
 
 static void project_f32(const orc_params* P, const float* cam, const float B[9],
