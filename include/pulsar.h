@@ -166,8 +166,7 @@ pulsar_status pulsar_bin(const pulsar_params* params, void* workspace, size_t wo
  *              backward pass)
  *   n_hits     optional (may be NULL) H x W int32: hits blended
  *   n_tests    optional (may be NULL) H x W int32: ray-sphere tests made
- *              (spheres whose test rectangle contains the pixel: the tangent
- *              bounds of the sphere's projection widened by 1/8 pixel)
+ *              (spheres whose rectangle contains the pixel)
  *   tracked    optional (may be NULL) H x W x n_track int32: indices of the
  *              tracked hits, closest first (by depth, then index), -1 padded
  * Requires pulsar_bin on the same workspace. */

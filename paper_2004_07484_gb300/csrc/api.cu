@@ -51,7 +51,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
   size_t hdr, scenes, rec0, rec1, rec2, key0, key1, val0, val1, hist, block_sums, pkey0, pkey1, pval0,
       pval1, radix_tot, ranges, item_begin, item_desc, item_order, unit_list, unit_count, unit_cost, unit_order, unit_tests, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
-      gacc, rect_t, pg_cnt, pg_opa, pg_feat, fin_part, red_part, total;
+      gacc, pg_cnt, pg_opa, pg_feat, fin_part, red_part, total;
   int64_t n_spheres, n_tiles, n_pixels, capacity, max_items;
   int32_t sort_blocks, fin_blocks, tile_bits, segment, part_fields;
 };
@@ -150,7 +150,6 @@ Layout make_layout(const pulsar_params* ps, int n) {
   L.pix_aux = take(16 * (size_t)P);
   L.fres = take(4 * (size_t)P * C);
   L.gacc = take(16 * (size_t)M);
-  L.rect_t = take(8 * (size_t)M);
   // paper gradients: per sphere its tracked pixels and the opacity and feature sums
   const bool paper = (ps[0].flags & PULSAR_FLAG_PAPER_GRADIENTS) != 0;
   L.pg_cnt = take(paper ? 4 * (size_t)M : 0);
@@ -213,7 +212,6 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.pix_aux = reinterpret_cast<float4*>(b + L.pix_aux);
   v.fres = reinterpret_cast<float*>(b + L.fres);
   v.gacc = reinterpret_cast<float4*>(b + L.gacc);
-  v.rect_t = reinterpret_cast<uint2*>(b + L.rect_t);
   v.pg_cnt = reinterpret_cast<int32_t*>(b + L.pg_cnt);
   v.pg_opa = reinterpret_cast<float*>(b + L.pg_opa);
   v.pg_feat = reinterpret_cast<float*>(b + L.pg_feat);

@@ -42,8 +42,8 @@ __device__ __forceinline__ void block_batch(BlockListWarp& W, int cnt, const WsV
   int ntest = 0;
   if (lane < cnt) {
     id = __ldg(list + W.pos[lane]);
-    const uint2 rt = __ldg(v.rect_t + id);   // the test rectangle
-    const uint32_t bx = rt.x, by = rt.y;
+    const float4 b = __ldg(v.rec1 + id);
+    const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
     const int x0 = max((int)(bx & 0xffffu), wr.x0), x1 = min((int)(bx >> 16), wr.x1);
     const int y0 = max((int)(by & 0xffffu), wr.y0), y1 = min((int)(by >> 16), wr.y1);
     const int w = max(x1 - x0 + 1, 1);
@@ -181,10 +181,11 @@ __global__ void __launch_bounds__(256) count_tests_kernel(const WsView v, const 
     const int i = base + lane;
     uint32_t rm = 0u;
     if (i < it.b1) {
-      const uint2 rt = __ldg(v.rect_t + __ldg(list + i));   // the test rectangle
-      const int x0 = max((int)(rt.x & 0xffffu), wr.x0), x1 = min((int)(rt.x >> 16), wr.x1);
-      const int y0 = max((int)(rt.y & 0xffffu), wr.y0), y1 = min((int)(rt.y >> 16), wr.y1);
-      if (x0 <= x1 && y0 <= y1) {
+      const float4 b = __ldg(v.rec1 + __ldg(list + i));
+      if (rect_overlaps(b, wr)) {
+        const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
+        const int x0 = max((int)(bx & 0xffffu), wr.x0), x1 = min((int)(bx >> 16), wr.x1);
+        const int y0 = max((int)(by & 0xffffu), wr.y0), y1 = min((int)(by >> 16), wr.y1);
         const uint32_t row = ((2u << (x1 - wr.x0)) - (1u << (x0 - wr.x0)));
         for (int y = y0; y <= y1; ++y) rm |= row << ((y - wr.y0) * 8);
       }

@@ -95,16 +95,6 @@ __global__ void __launch_bounds__(kThreads) project_kernel(WsView v) {
                             __uint_as_float(pack_range(pr.y0, pr.y1)));
     v.key[0][i] = __float_as_uint(pr.key);
     v.val[0][i] = (uint32_t)i;
-    // the test rectangle of the block lists: the tangent bounds widened by an
-    // eighth of a pixel instead of a whole one (the hit predicate's float32
-    // boundary lies within ~1e-4 pixel of the exact one), inside the rectangle
-    if (pr.visible) {
-      constexpr float kTestMargin = 0.125f;
-      int tx0 = max((int)ceilf(pr.fx0 - kTestMargin), pr.x0), tx1 = min((int)floorf(pr.fx1 + kTestMargin), pr.x1);
-      int ty0 = max((int)ceilf(pr.fy0 - kTestMargin), pr.y0), ty1 = min((int)floorf(pr.fy1 + kTestMargin), pr.y1);
-      if (tx0 > tx1 || ty0 > ty1) tx0 = 1, tx1 = 0, ty0 = 1, ty1 = 0;   // no pixel centre to test
-      v.rect_t[i] = make_uint2(pack_range(tx0, tx1), pack_range(ty0, ty1));
-    }
     // value path: the centre to about 2^-46 relative (float-float), kept as
     // the float32 decision centre plus a float correction; the radius as
     // used by the value path

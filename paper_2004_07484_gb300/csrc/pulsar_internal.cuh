@@ -148,7 +148,6 @@ struct WsView {
   float4* pix_aux;           // per pixel: (t_K, id_K bits, reference sphere bits, 0)
   float* fres;               // per pixel x C: F - f_ref, the image relative to its reference feature
   float4* gacc;              // per sphere: dL/dc (3), dL/dR
-  uint2* rect_t;             // per sphere: the test rectangle (packed like the rectangle record)
   int32_t* pg_cnt;           // paper gradients: per sphere, pixels that track it
   float* pg_opa;             // paper gradients: per sphere, dL/do before averaging
   float* pg_feat;            // paper gradients: per sphere x C, dL/df before averaging
@@ -183,14 +182,16 @@ __device__ __forceinline__ float pixel_pitch(const float* cam, int width, bool o
 struct Projected {
   float cx, cy, cz, R, R2, key;
   bool visible;
-  int x0, x1, y0, y1;         // the rectangle: the tangent bounds widened by one pixel
-  float fx0, fx1, fy0, fy1;   // the tangent bounds in pixel units (before widening)
+  int x0, x1, y0, y1;
 };
 
 // One axis of the enclosing rectangle: the tangent slopes of the (axis, z)
-// disk seen from the eye, converted to pixel indices and widened by one pixel.
+// disk seen from the eye, converted to pixel units; the pixels whose centres
+// lie within the bounds widened by 1/8 pixel (the float32 hit predicate's
+// boundary lies within ~1e-4 pixel of the exact one).  The block lists test
+// exactly these pixels.
 __device__ __forceinline__ void axis_range(float cx, float cz, float R, float R2, float kappa,
-                                           int n, int& lo, int& hi, float& flo_out, float& fhi_out) {
+                                           int n, int& lo, int& hi) {
   float den = __fmaf_rn(cz, cz, -R2);
   float disc = __fmaf_rn(cx, cx, den);
   float root = __fsqrt_rn(disc);
@@ -203,25 +204,20 @@ __device__ __forceinline__ void axis_range(float cx, float cz, float R, float R2
   float fhi = __fadd_rn(__fdiv_rn(mhi, kappa), half);
   flo = fmaxf(fminf(flo, (float)n + 2.0f), -4.0f);
   fhi = fmaxf(fminf(fhi, (float)n + 2.0f), -4.0f);
-  lo = (int)ceilf(flo) - 1;
-  hi = (int)floorf(fhi) + 1;
-  flo_out = flo;
-  fhi_out = fhi;
+  lo = (int)ceilf(__fsub_rn(flo, 0.125f));
+  hi = (int)floorf(__fadd_rn(fhi, 0.125f));
 }
 
 // One axis of the rectangle of the orthographic camera: the centre -+ R in
-// pixels, widened by one pixel.
-__device__ __forceinline__ void axis_range_ortho(float cx, float R, float kappa, int n, int& lo, int& hi,
-                                                 float& flo_out, float& fhi_out) {
+// pixels, widened by 1/8 pixel.
+__device__ __forceinline__ void axis_range_ortho(float cx, float R, float kappa, int n, int& lo, int& hi) {
   float half = __fmul_rn((float)(n - 1), 0.5f);
   float flo = __fadd_rn(__fdiv_rn(__fsub_rn(cx, R), kappa), half);
   float fhi = __fadd_rn(__fdiv_rn(__fadd_rn(cx, R), kappa), half);
   flo = fmaxf(fminf(flo, (float)n + 2.0f), -4.0f);
   fhi = fmaxf(fminf(fhi, (float)n + 2.0f), -4.0f);
-  lo = (int)ceilf(flo) - 1;
-  hi = (int)floorf(fhi) + 1;
-  flo_out = flo;
-  fhi_out = fhi;
+  lo = (int)ceilf(__fsub_rn(flo, 0.125f));
+  hi = (int)floorf(__fadd_rn(fhi, 0.125f));
 }
 
 // Step 0 for one sphere: camera-space centre, effective radius (one-pixel
@@ -251,16 +247,15 @@ __device__ __forceinline__ Projected project_sphere(const float* B, const float*
   o.key = __int_as_float(0x7f800000);
   o.visible = false;
   o.x0 = o.x1 = o.y0 = o.y1 = -1;
-  o.fx0 = o.fx1 = o.fy0 = o.fy1 = 0.0f;
   float key = __fsub_rn(o.cz, R);
   if (!(R > 0.0f) || !(key > znear) || !(key < zfar)) return o;
   int x0, x1, y0, y1;
   if (ortho) {
-    axis_range_ortho(o.cx, R, kappa, width, x0, x1, o.fx0, o.fx1);
-    axis_range_ortho(o.cy, R, kappa, height, y0, y1, o.fy0, o.fy1);
+    axis_range_ortho(o.cx, R, kappa, width, x0, x1);
+    axis_range_ortho(o.cy, R, kappa, height, y0, y1);
   } else {
-    axis_range(o.cx, o.cz, R, o.R2, kappa, width, x0, x1, o.fx0, o.fx1);
-    axis_range(o.cy, o.cz, R, o.R2, kappa, height, y0, y1, o.fy0, o.fy1);
+    axis_range(o.cx, o.cz, R, o.R2, kappa, width, x0, x1);
+    axis_range(o.cy, o.cz, R, o.R2, kappa, height, y0, y1);
   }
   if (x1 < 0 || x0 > width - 1 || y1 < 0 || y0 > height - 1) return o;
   o.x0 = max(x0, 0);

@@ -232,19 +232,15 @@ __global__ void __launch_bounds__(kThreads) emit_pairs(WsView v) {
     int tx0 = (int)(bx & 0xffffu) / kTile, tx1 = (int)(bx >> 16) / kTile;
     int ty0 = (int)(by & 0xffffu) / kTile, ty1 = (int)(by >> 16) / kTile;
     uint32_t tb = (uint32_t)S.tile_begin;
-    // block sets from the (tighter) test rectangle; the tiles from the rectangle
-    const uint2 rt = v.rect_t[i];
-    const int x0 = (int)(rt.x & 0xffffu), x1 = (int)(rt.x >> 16);
-    const int y0 = (int)(rt.y & 0xffffu), y1 = (int)(rt.y >> 16);
+    const int x0 = (int)(bx & 0xffffu), x1 = (int)(bx >> 16);
+    const int y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
     for (int ty = ty0; ty <= ty1; ++ty) {
-      // rows of 8 x 4 pixel blocks the test rectangle meets in this tile row
+      // rows of 8 x 4 pixel blocks the rectangle meets in this tile row
       const int r0 = (max(y0 - ty * kTile, 0)) >> 2, r1 = (min(y1 - ty * kTile, kTile - 1)) >> 2;
-      const bool row_hit = y0 <= y1 && y0 <= ty * kTile + kTile - 1 && y1 >= ty * kTile;
-      const uint32_t rows = row_hit ? ((1u << (2 * r1 + 2)) - (1u << (2 * r0))) / 3u : 0u;   // sum of 4^r
+      const uint32_t rows = ((1u << (2 * r1 + 2)) - (1u << (2 * r0))) / 3u;   // sum of 4^r, r0..r1
       for (int tx = tx0; tx <= tx1; ++tx) {
         const int c0 = (max(x0 - tx * kTile, 0)) >> 3, c1 = (min(x1 - tx * kTile, kTile - 1)) >> 3;
-        const bool col_hit = x0 <= x1 && x0 <= tx * kTile + kTile - 1 && x1 >= tx * kTile;
-        const uint32_t blocks = col_hit ? ((2u << c1) - (1u << c0)) * rows : 0u;   // bit 2 r + c: block (c, r)
+        const uint32_t blocks = ((2u << c1) - (1u << c0)) * rows;   // bit 2 r + c: block (c, r)
         v.pkey[0][off] = (tb + (uint32_t)(ty * S.tiles_x + tx)) | (blocks << kTileKeyBits);
         v.pval[0][off] = i;
         ++off;
