@@ -46,7 +46,7 @@ N_SMS = 152
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only
 # for the kernel sources with this digest, reported as null otherwise.
 FWD_KERNEL_SOURCES = ("render_fwd.cu", "render_common.cuh", "pulsar_internal.cuh")
-FWD_TRAFFIC = {"sha256": "76401448ce386b4497572f2c3123c1ad2ac62b0836f2930e14d19905ebb7f5a0", "bytes": 220190208 + 11448064}
+FWD_TRAFFIC = {"sha256": "073c75eb82cbaaa16ba40719fbb602e056de7d8c2ae02c7c55d9ceebd8f5ae6a", "bytes": 211991040 + 10141952}
 
 
 def fwd_kernel_digest() -> str:
