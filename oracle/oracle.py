@@ -29,7 +29,7 @@ class OrcParams(ctypes.Structure):
         ("n_spheres", ctypes.c_int32), ("n_channels", ctypes.c_int32),
         ("n_track", ctypes.c_int32), ("tile", ctypes.c_int32),
         ("min_size", ctypes.c_int32), ("dist_literal", ctypes.c_int32), ("paper_grad", ctypes.c_int32),
-        ("ortho", ctypes.c_int32),
+        ("ortho", ctypes.c_int32), ("paper_stop", ctypes.c_int32),
         ("gamma", ctypes.c_double), ("eps", ctypes.c_double),
         ("znear", ctypes.c_double), ("zfar", ctypes.c_double),
     ]
@@ -63,6 +63,8 @@ def lib():
         L.orc_render_bwd.argtypes = [P(OrcParams), P(d), P(d), P(d), P(d), P(d), P(d), P(d),
                                      P(d), P(d), P(d), P(d), P(d), P(d)]
         L.orc_render_bwd.restype = None
+        L.orc_paper_stop_margin.argtypes = [P(OrcParams), P(d), P(d), P(d), P(d), P(d)]
+        L.orc_paper_stop_margin.restype = None
         L.orc_rows.argtypes = [P(d), P(d)]
         L.orc_rows.restype = None
         L.orc_hit_f32.argtypes = [P(OrcParams), P(d), d, P(d), ctypes.c_int, ctypes.c_int,
@@ -87,13 +89,15 @@ def _d(a) -> np.ndarray:
 
 def params(scene, tile: int = 16, min_size: bool = True, dist_literal: bool = False,
            n_track: int | None = None, paper_grad: bool = False, ortho: bool | None = None) -> OrcParams:
-    """ortho=None takes the scene's own ``ortho`` attribute (False when absent)."""
+    """ortho=None takes the scene's own ``ortho`` attribute (False when absent);
+    the scene's ``paper_stop`` attribute selects the paper's early termination."""
     if ortho is None:
         ortho = bool(getattr(scene, "ortho", False))
+    paper_stop = bool(getattr(scene, "paper_stop", False))
     return OrcParams(int(scene.width), int(scene.height), int(scene.pos.shape[0]),
                      int(scene.feat.shape[1]), int(n_track if n_track is not None else scene.n_track),
                      int(tile), int(bool(min_size)), int(bool(dist_literal)), int(bool(paper_grad)),
-                     int(bool(ortho)),
+                     int(bool(ortho)), int(paper_stop),
                      float(np.float32(scene.gamma)), float(np.float32(scene.eps)),
                      float(np.float32(scene.znear)), float(np.float32(scene.zfar)))
 
@@ -181,6 +185,18 @@ def render(scene, n_track: int | None = None, min_size: bool = True, dist_litera
                          _ptr(nh, ctypes.c_int32), _ptr(tr, ctypes.c_int32), _ptr(tt, ctypes.c_float),
                          _ptr(ws, D))
     return Forward(img, ld, nh, tr, tt, ws)
+
+
+def paper_stop_margin(scene, **kw) -> np.ndarray:
+    """(H, W) float64: per pixel the smallest |ln(a / 0.01)| over the early-
+    termination tests the pixel takes (scene.paper_stop set), a the largest
+    possible weight tested; +inf where no test is taken."""
+    p = params(scene, **kw)
+    out = np.zeros((p.height, p.width), np.float64)
+    D = ctypes.c_double
+    lib().orc_paper_stop_margin(ctypes.byref(p), _ptr(_d(scene.pos), D), _ptr(_d(scene.rad), D),
+                                _ptr(_d(scene.opa), D), _ptr(_d(scene.cam), D), _ptr(out, D))
+    return out
 
 
 @dataclass

@@ -56,6 +56,14 @@
  *               sphere's area, taken as n_i pixels, times 1e-3 -- that is,
  *               1e-3 times the plain camera gradient.  The background
  *               gradient is unchanged.
+ *   paper stop  optional early termination of App. B, Step 2 (the paper's
+ *               default, an approximation): a pixel takes its hits in the tile
+ *               list's order (sort key c_z - R, then index) and stops before
+ *               the first whose largest possible weight e^{o_max z_b / g} /
+ *               (D + e^{o_max z_b / g}) is below 1 %, z_b the depth term of its
+ *               key, o_max the largest opacity of the scene's visible spheres
+ *               and D the denominator of the hits taken so far; blending and
+ *               tracking see only the hits taken.
  */
 #include <math.h>
 #include <stdint.h>
@@ -72,6 +80,7 @@ typedef struct {
   int32_t dist_literal;  /* 1: d = min(1, dist/R) instead of 1 - min(1, dist/R) */
   int32_t paper_grad;    /* 1: the paper's gradient normalisations (header) */
   int32_t ortho;         /* 1: orthographic camera (header) */
+  int32_t paper_stop;    /* 1: the paper's 1 % early termination (header) */
   double gamma, eps, znear, zfar;
 } orc_params;
 
@@ -264,6 +273,7 @@ static void rows_c(const double complex a[6], double complex B[9]) {
 typedef struct {
   int id;
   float t32;
+  float key;      /* the sphere's sort key (tile-list order) */
 } hit_rec;
 
 static int hit_cmp(const void* a, const void* b) {
@@ -289,6 +299,7 @@ typedef struct {
   float camf[11];
   float Bf[9];
   float kappaf;
+  double omax;      /* largest |opacity| of the visible spheres (float32 values) */
   proj32* pj;
   sph64* sv;
 } ctx_t;
@@ -322,6 +333,10 @@ static void ctx_init(const orc_params* P, const double* pos, const double* rad,
     double cn = sqrt(s->c[0] * s->c[0] + s->c[1] * s->c[1] + s->c[2] * s->c[2]);
     s->R = s->clamped ? (P->ortho ? 0.75 * C->kappa : 0.75 * cn * C->kappa) : rad[i];
   }
+  C->omax = 0.0;
+  if (C->opa)
+    for (int i = 0; i < M; ++i)
+      if (C->pj[i].visible && fabs((double)(float)C->opa[i]) > C->omax) C->omax = fabs((double)(float)C->opa[i]);
 }
 
 static void ctx_free(ctx_t* C) {
@@ -365,8 +380,55 @@ static void ray_values(const orc_params* P, const sph64* s, double rx, double ry
   o->d = P->dist_literal ? o->dq : 1.0 - o->dq;
 }
 
+/* Order of the tile lists: sort key, then index. */
+static int hit_key_cmp(const void* a, const void* b) {
+  const hit_rec* x = (const hit_rec*)a;
+  const hit_rec* y = (const hit_rec*)b;
+  float kx = x->key, ky = y->key;
+  if (kx < ky) return -1;
+  if (kx > ky) return 1;
+  return (x->id > y->id) - (x->id < y->id);
+}
+
+static void ray_values(const orc_params* P, const sph64* s, double rx, double ry, rayq* o);
+
+/* The paper's early termination: keeps the hits (in tile-list order) before
+ * the first whose largest possible weight is below 1 % (header).  The hits
+ * come in and go out ordered by (key, index).  With margin != NULL, *margin
+ * receives the smallest |ln(a / tau)| over the tests taken, a the tested
+ * largest possible weight: how far the pixel's decisions are from the
+ * threshold (a renderer that accumulates D in another precision can decide
+ * otherwise only where this is small). */
+static int paper_stop_filter(const orc_params* P, const ctx_t* C, int u, int v, hit_rec* hits, int n,
+                             double* margin) {
+  const double tau = 0.01, g = P->gamma, zr = P->zfar - P->znear;
+  double rx = (double)(2 * u + 1 - P->width) * 0.5 * C->kappa;
+  double ry = (double)(2 * v + 1 - P->height) * 0.5 * C->kappa;
+  double m = P->eps / g, den = 1.0;   /* the background term alone, shifted by its own exponent */
+  for (int j = 0; j < n; ++j) {
+    int i = hits[j].id;
+    double zb = (P->zfar - (double)C->pj[i].key) / zr;
+    double amax = exp(C->omax * zb / g - m);
+    double a = amax / (den + amax);
+    if (margin) {
+      double mg = fabs(log(a / tau));
+      if (mg < *margin) *margin = mg;
+    }
+    if (a < tau) return j;
+    rayq q;
+    ray_values(P, &C->sv[i], rx, ry, &q);
+    double s = C->opa[i] * q.z / g;
+    if (s > m) {
+      den *= exp(m - s);
+      m = s;
+    }
+    den += C->opa[i] * q.d * exp(s - m);
+  }
+  return n;
+}
+
 /* Collect and order the hits of one pixel.  Returns the hit count. */
-static int pixel_hits(const orc_params* P, const ctx_t* C, int u, int v, hit_rec* hits) {
+static int pixel_hits_m(const orc_params* P, const ctx_t* C, int u, int v, hit_rec* hits, double* margin) {
   int M = P->n_spheres, n = 0;
   float rx = ray_coord_f32(u, P->width, C->kappaf);
   float ry = ray_coord_f32(v, P->height, C->kappaf);
@@ -376,11 +438,20 @@ static int pixel_hits(const orc_params* P, const ctx_t* C, int u, int v, hit_rec
     if (hit_px(P, &C->pj[i], rx, ry, (float)P->zfar, &t)) {
       hits[n].id = i;
       hits[n].t32 = t;
+      hits[n].key = C->pj[i].key;
       ++n;
     }
   }
+  if (P->paper_stop && n > 0) {
+    qsort(hits, (size_t)n, sizeof(hit_rec), hit_key_cmp);
+    n = paper_stop_filter(P, C, u, v, hits, n, margin);
+  }
   qsort(hits, (size_t)n, sizeof(hit_rec), hit_cmp);
   return n;
+}
+
+static int pixel_hits(const orc_params* P, const ctx_t* C, int u, int v, hit_rec* hits) {
+  return pixel_hits_m(P, C, u, v, hits, NULL);
 }
 
 /* Blend one pixel by Eq. 1.  Writes F (C values) and returns log D, where
@@ -512,6 +583,32 @@ void orc_render_fwd(const orc_params* P, const double* pos, const double* rad,
           if (tracked) tracked[px * K + k] = k < n ? hits[k].id : -1;
           if (tracked_t) tracked_t[px * K + k] = k < n ? hits[k].t32 : INFINITY;
         }
+      }
+    free(hits);
+  }
+  ctx_free(&C);
+}
+
+/* The decision margin of the early termination (paper_stop set): per pixel
+ * the smallest |ln(a / 0.01)| over the tests the pixel takes, a the largest
+ * possible weight tested (see paper_stop_filter); +inf where no test is
+ * taken.  margin: H x W. */
+void orc_paper_stop_margin(const orc_params* P, const double* pos, const double* rad,
+                           const double* opa, const double* cam, double* margin) {
+  ctx_t C;
+  memset(&C, 0, sizeof(C));
+  C.pos = pos; C.rad = rad; C.opa = opa; C.cam = cam;
+  ctx_init(P, pos, rad, cam, NULL, NULL, NULL, &C);
+  int W = P->width, H = P->height, M = P->n_spheres;
+#pragma omp parallel
+  {
+    hit_rec* hits = (hit_rec*)malloc(sizeof(hit_rec) * (size_t)(M + 1));
+#pragma omp for schedule(dynamic, 1)
+    for (int v = 0; v < H; ++v)
+      for (int u = 0; u < W; ++u) {
+        double mg = INFINITY;
+        pixel_hits_m(P, &C, u, v, hits, &mg);
+        margin[(size_t)v * W + u] = mg;
       }
     free(hits);
   }

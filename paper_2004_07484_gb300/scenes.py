@@ -46,6 +46,7 @@ class Scene:
     name: str = ""
     meta: dict = field(default_factory=dict)
     ortho: bool = False      # orthographic camera (rays along +z from the sensor plane)
+    paper_stop: bool = False # the paper's 1 % early termination (an approximation)
 
     @property
     def n_spheres(self) -> int:

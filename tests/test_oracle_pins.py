@@ -554,3 +554,65 @@ def test_orthographic_gradients_match_central_differences(orc, rotated):
     # larger step against round-off
     _check_fd(orc, sc, G, grads, "cam", [0, 1, 2, 3, 4, 5, 6, 7, 8, 10], K, hscales=(0.05, 1.0, 5.0))
     _check_fd(orc, sc, G, grads, "bg", [0, 1, 2], K)
+
+
+# ---------------------------------------------------------------- the paper's 1 % early termination
+
+def _stop_column(t4):
+    """Four unit spheres centred on the optical axis whose front surfaces lie
+    at depths 3, 3.5, 4 and t4 (znear 1, zfar 11: depth terms 0.8, 0.75, 0.7
+    and (11 - t4) / 10), all opaque, gamma 0.1: at the centre pixel the
+    exponents are 8, 7.5, 7 and 10 (11 - t4) with d = 1."""
+    sc = scene_of([[0, 0, 4.0], [0, 0, 4.5], [0, 0, 5.0], [0, 0, t4 + 1.0]], [1.0] * 4, [1.0] * 4,
+                  [[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]], 65, 65, 0.1, n_track=8, eps=1e-4,
+                  znear=1.0, zfar=11.0, bg=[0.25, 0.5, 0.75])
+    sc.paper_stop = True
+    return sc
+
+
+@pytest.mark.parametrize("t4, taken", [(7.0, 3), (6.8, 4)])
+def test_paper_stop_on_a_column_of_spheres(orc, t4, taken):
+    """By hand: the fourth sphere's largest possible weight is e^{4} / (e^{8} +
+    e^{7.5} + e^{7} + e^{4} + e^{0.001}) = 0.0092 < 1 % at t4 = 7 (the pixel
+    stops after three hits) and e^{4.2} / (...) = 0.0112 at t4 = 6.8 (it takes
+    all four); the second and third spheres pass by far (0.38, 0.19)."""
+    sc = _stop_column(t4)
+    out = orc.render(sc)
+    c = 32
+    assert out.n_hits[c, c] == taken
+    assert list(out.tracked[c, c, :taken]) == list(range(taken))
+    # the image blends the taken hits only (Eq. 1 over three or four spheres)
+    e = [(11.0 - f32(k)) / 10.0 / f32(0.1) for k in (3.0, 3.5, 4.0, f32(t4 + 1.0) - 1.0)]
+    B = math.exp(f32(1e-4) / f32(0.1))
+    feat = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]], np.float64)
+    num = B * np.array([0.25, 0.5, 0.75]) + sum(math.exp(e[k]) * feat[k] for k in range(taken))
+    den = B + sum(math.exp(e[k]) for k in range(taken))
+    np.testing.assert_allclose(out.image[c, c], num / den, rtol=1e-12)
+    # the smallest distance to the threshold is the fourth test's
+    a4 = math.exp(e[3]) / (B + sum(math.exp(x) for x in e))
+    margin = orc.paper_stop_margin(sc)
+    assert margin[c, c] == pytest.approx(abs(math.log(a4 / 0.01)), rel=1e-9)
+    # without the option every pixel takes every hit
+    sc.paper_stop = False
+    assert orc.render(sc).n_hits[c, c] == 4
+
+
+def test_paper_stop_error_is_bounded_by_the_remaining_hits(orc):
+    """Each hit a pixel leaves out has weight numerator o d e^{o z / g} at most
+    A = e^{o_max z_b / g} of the first left out (o, d <= 1, z <= z_b, keys in
+    increasing order), and A / (D + A) < 1 %; with n hits left out, the
+    exact colour differs from the truncated one by at most 2 f_max n A / (D + n A)
+    <= 2 f_max n t / (1 + n t), t = 0.01 / 0.99."""
+    sc = config_scene(0, n=20000, res=48)
+    assert sc.opa.max() <= 1.0 and sc.opa.min() >= 0.0
+    exact = orc.render(sc)
+    sc.paper_stop = True
+    stop = orc.render(sc)
+    left = exact.n_hits - stop.n_hits
+    assert left.min() >= 0 and (left > 0).mean() > 0.01 and stop.n_hits.sum() > 0
+    fmax = max(float(np.abs(sc.feat).max()), float(np.abs(sc.bg).max()))
+    t = 0.01 / 0.99
+    bound = 2.0 * fmax * left * t / (1.0 + left * t)
+    err = np.abs(exact.image - stop.image).max(axis=2)
+    assert np.all(err <= bound + 1e-12)
+    assert np.all(err[left == 0] <= 1e-12)
