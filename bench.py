@@ -575,10 +575,10 @@ def main():
     pairs_needed = autotune.pairs_per_scene([base], inputs)[0]
     capacity = tuned.capacities[0]
 
-    def settings(store: bool):
+    def settings(store: bool, paper_stop: bool = False):
         return RenderSettings(sc.width, sc.height, sc.n_channels, sc.n_track, sc.gamma, sc.eps,
                               sc.znear, sc.zfar, store_hits=store, segment=tuned.segment,
-                              persistent=tuned.persistent)
+                              persistent=tuned.persistent, paper_stop=paper_stop)
 
     # counters for the algorithmic work of the render kernels
     H, W, C = sc.height, sc.width, sc.n_channels
@@ -594,21 +594,21 @@ def main():
 
     fwd_ev, bwd_ev = [], []
 
-    def step(store: bool, timed_kernels: bool):
-        s = settings(store)
+    def step(store: bool, timed_kernels: bool, paper_stop: bool = False):
+        s = settings(store, paper_stop)
         fr, image, log_norm = forward_frame(s, t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"],
                                             capacity, check_overflow=False)
         grads = backward_frame(fr, t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"], image,
                                log_norm, G)
         return fr, image, grads
 
-    def timed_steps(store: bool, k: int):
+    def timed_steps(store: bool, k: int, paper_stop: bool = False):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
         for i in range(k):
             flush.fill_(i & 0xff)
             starts[i].record(stream)
-            fr, image, grads = step(store, True)
+            fr, image, grads = step(store, True, paper_stop)
             ends[i].record(stream)
         torch.cuda.synchronize()
         return [s.elapsed_time(e) for s, e in zip(starts, ends)], fr
@@ -616,6 +616,7 @@ def main():
     for _ in range(max(args.warmup, 3)):
         step(True, False)
         step(False, False)
+        step(True, False, True)
     torch.cuda.synchronize()
     if args.profile_step and args.profile_batch > 0:
         if rank == 0:
@@ -638,6 +639,8 @@ def main():
         t_wall = time.perf_counter()
         ms_store, fr_last = timed_steps(not args.recompute, args.steps)
         ms_rec, _ = timed_steps(args.recompute, max(3, args.steps // 2))
+        # the paper's default early termination (an approximation), for comparison
+        ms_ps, _ = timed_steps(True, max(3, args.steps // 2), True)
         t_wall = time.perf_counter() - t_wall
     gc.enable()
     st, _ = _lib.read_status(fr_last.ws.data_ptr(), fr_last.ws_bytes, stream.cuda_stream)
@@ -645,6 +648,7 @@ def main():
     if world > 1:
         dist.barrier()
     total_ms = max_over_ranks(sum(ms_store), world, dev)
+    ps_total_ms = max_over_ranks(sum(ms_ps), world, dev)
     ms_per_step = total_ms / args.steps
     ms_sorted = sorted(ms_store)
     value = job_throughput(world, args.steps, total_ms)
@@ -789,14 +793,19 @@ def main():
                        "l2": "flushed between steps (256 MB write, untimed)",
                        "hit_lists": "recompute" if args.recompute else "store"},
             "recompute_ms_per_step" if not args.recompute else "store_ms_per_step": statistics.mean(ms_rec),
+            "paper_stop": {"value": job_throughput(world, len(ms_ps), ps_total_ms),
+                           "unit": UNIT, "ms_per_step": statistics.mean(ms_ps),
+                           "what": "the paper's 1% early termination on top of the exact one "
+                                   "(approximate; whole tile lists per work item), stored hits"},
             "e2e": {"value": job_throughput(world, 1, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "how": "pinned host buffers; per step the inputs (positions, features, radii, opacities, "
                            "camera, background, dL/dF) are copied in and the image and all six gradients "
                            "copied out, pipelined over two buffer slots on separate copy streams"},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-            "gpu_launches": (launches_store * args.steps + launches_rec * len(ms_rec)) if not args.recompute
-            else (launches_rec * args.steps + launches_store * len(ms_rec)),
+            "gpu_launches": ((launches_store * args.steps + launches_rec * len(ms_rec)) if not args.recompute
+                             else (launches_rec * args.steps + launches_store * len(ms_rec)))
+            + launches_store * len(ms_ps),
             "wall_s_timed": t_wall, "batched": batched, "batched_headline": batched_headline,
             "autotune": {"segment": tuned.segment, "persistent": tuned.persistent,
                          "candidates_ms": {f"{a}/{'persistent' if b else 'per-unit'}": v

@@ -92,7 +92,19 @@ enum {
    * pixel (u, v) sees along +z from (rho_x, rho_y, 0) in camera space, rho =
    * ((u + 1/2 - W/2) k, (v + 1/2 - H/2) k) with k = sensor_width / W; the
    * focal length does not enter.  The minimum size is R = max(r, 0.75 k). */
-  PULSAR_FLAG_ORTHOGRAPHIC = 1u << 6
+  PULSAR_FLAG_ORTHOGRAPHIC = 1u << 6,
+  /* The paper's early termination (App. B, Step 2; an approximation, the
+   * paper's default), on top of the exact one: a pixel takes its hits in list
+   * order (sort key, then index) and stops before the first hit whose largest
+   * possible weight e^{o_max z_k / g} / (D + e^{o_max z_k / g}) is below 1 %,
+   * z_k the depth term of the sphere's sort key, o_max the largest |o| of
+   * the scene's visible spheres and D the denominator of Eq. 1 over the hits
+   * taken; blending and tracking see only the hits taken.  The decision is
+   * taken in float32.  Each tile's list is then one work item (`segment` is
+   * ignored), and the backward pass needs PULSAR_FLAG_STORE_HITS (without it
+   * PULSAR_ERR_UNSUPPORTED): the forward pass records where each pixel
+   * stopped.  Forward and backward calls take the same flags. */
+  PULSAR_FLAG_PAPER_STOP = 1u << 7
 };
 
 /* grad_mask bits of pulsar_render_bwd: gradients are computed only where

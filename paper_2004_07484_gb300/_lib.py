@@ -21,6 +21,7 @@ FLAG_PERSISTENT = 1 << 3
 FLAG_ACCUMULATE = 1 << 4
 FLAG_PAPER_GRADIENTS = 1 << 5
 FLAG_ORTHOGRAPHIC = 1 << 6
+FLAG_PAPER_STOP = 1 << 7
 
 GRAD_POS, GRAD_RAD, GRAD_OPA, GRAD_FEAT, GRAD_CAM, GRAD_BG = (1 << k for k in range(6))
 GRAD_ALL = 63

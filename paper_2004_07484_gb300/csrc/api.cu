@@ -75,7 +75,7 @@ pulsar_status validate(const pulsar_params* p) {
   if (!(p->eps >= 0.0f) || !(p->znear > 0.0f) || !(p->zfar > p->znear)) return PULSAR_ERR_INVALID_ARG;
   if (p->flags & ~(uint32_t)(PULSAR_FLAG_STORE_HITS | PULSAR_FLAG_DIST_LITERAL | PULSAR_FLAG_NO_MIN_SIZE |
                              PULSAR_FLAG_PERSISTENT | PULSAR_FLAG_ACCUMULATE | PULSAR_FLAG_PAPER_GRADIENTS |
-                             PULSAR_FLAG_ORTHOGRAPHIC))
+                             PULSAR_FLAG_ORTHOGRAPHIC | PULSAR_FLAG_PAPER_STOP))
     return PULSAR_ERR_INVALID_ARG;
   if (p->segment != 0 && (p->segment < 32 || p->segment > 65536 || p->segment % 32 != 0))
     return PULSAR_ERR_INVALID_ARG;
@@ -107,7 +107,11 @@ Layout make_layout(const pulsar_params* ps, int n) {
   int bits = 1;
   while (bits < 32 && ((int64_t)1 << bits) < NT) ++bits;
   L.tile_bits = bits;
-  L.segment = ps[0].segment > 0 ? ps[0].segment : kDefaultSegment;
+  // the paper's early termination follows a pixel's denominator along the
+  // whole list: one segment per tile
+  L.segment = (ps[0].flags & PULSAR_FLAG_PAPER_STOP) ? kWholeList
+              : ps[0].segment > 0                     ? ps[0].segment
+                                                      : kDefaultSegment;
   L.max_items = NT + (cap + L.segment - 1) / L.segment;
   L.part_fields = 6 + C + 2 * K;
   size_t off = 0;
@@ -375,6 +379,10 @@ pulsar_status bwd_n(int n, const pulsar_params* params, const pulsar_scene* scen
   if (st != PULSAR_OK) return st;
   if (!scenes_ok(n, params, scenes) || !io) return PULSAR_ERR_INVALID_ARG;
   if (grad_mask & ~(uint32_t)PULSAR_GRAD_ALL) return PULSAR_ERR_INVALID_ARG;
+  // where the paper's early termination stopped a pixel is known from the
+  // forward pass only
+  if ((params[0].flags & PULSAR_FLAG_PAPER_STOP) && !(params[0].flags & PULSAR_FLAG_STORE_HITS))
+    return PULSAR_ERR_UNSUPPORTED;
   for (int k = 0; k < n; ++k) {
     const pulsar_bwd_io& q = io[k];
     if (!q.image || !q.log_norm || !q.grad_image) return PULSAR_ERR_INVALID_ARG;

@@ -9,7 +9,8 @@
 // pass, each batch of staged spheres is first hit-tested by every lane, then
 // each lane walks its own tracked hits and adds their gradients with (vector)
 // atomics, so lanes never wait on one another's hits.  A pixel stops at the
-// first key beyond its threshold.
+// first key beyond its threshold, or (PULSAR_FLAG_PAPER_STOP) at the list
+// position where the forward pass's early termination stopped it.
 //
 // Derivatives (Eq. 1 with a = o d e^{o z / gamma}, D its denominator, G = dL/dF):
 //   dL/df_i = w_i G,   dL/da_i = G.(f_i - F) / D,
@@ -94,6 +95,7 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
   float logD = 0.0f, GFres = 0.0f, Gref = 0.0f;
   float thr_t = __int_as_float(0x7f800000);
   int thr_i = 0x7fffffff, dom = -1;
+  int stop_pos = 0x7fffffff;   // list position where the paper's early termination stopped
 #pragma unroll
   for (int c = 0; c < CMAX; ++c) G[c] = 0.0f;
   if (pc.inside) {
@@ -123,6 +125,7 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
     thr_t = aux.x;
     thr_i = __float_as_int(aux.y);
     dom = __float_as_int(aux.z);
+    if (S.flags & PULSAR_FLAG_PAPER_STOP) stop_pos = __float_as_int(aux.w);
     const float* fref = dom < 0 ? S.bg : S.feat + (int64_t)(dom - S.sphere_begin) * C;
 #pragma unroll
     for (int c = 0; c < CMAX; ++c)
@@ -158,7 +161,7 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
       hits &= hits - 1u;
       const float4 a = sb.rec0[cur][j];
       const float4 b = sb.rec1[cur][j];
-      if (b.x >= kstop) {
+      if (b.x >= kstop || ws.base + j >= stop_pos) {
         done = true;
         break;
       }

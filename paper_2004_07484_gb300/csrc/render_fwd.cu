@@ -41,6 +41,15 @@
 //        pixel's).
 // Both tests only use the segment's own state, so they stay exact when the
 // segments are merged.
+//
+// With PULSAR_FLAG_PAPER_STOP a pixel also stops, as the paper's renderer
+// does (App. B, Step 2), before the first hit whose largest possible weight
+// A = e^{o_max z_b / g} is below 1 % of D + A; that is, with D = e^{m} den,
+// beyond the key
+//   k3 = zfar - (zfar - znear) (g / o_max) (m + ln den + ln(0.01 / 0.99)),
+// which only falls as hits are blended.  The pixel's list position where it
+// stopped goes to the backward pass with the tracked set.  Tiles then have a
+// single segment, as the rule needs the pixel's whole denominator.
 #include "render_common.cuh"
 
 namespace pulsar {
@@ -130,6 +139,12 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   int nhit = 0, ntest = 0;
   bool done = !pc.inside;
   float kstop1 = __int_as_float(0x7f800000);   // tracked-set bound (i)
+  // the paper's early termination: its key bound and where the pixel stopped
+  const bool pstop = BLEND && (S.flags & PULSAR_FLAG_PAPER_STOP) != 0 && omax > 0.0f;
+  const float pscale = range * gamma / omax;
+  auto paper_bound = [&]() { return zfar - pscale * ((bs.m + __logf(bs.den)) + kLogStopRatio); };
+  float kstop3 = pstop ? paper_bound() : __int_as_float(0x7f800000);
+  int stop_pos = 0x7fffffff;
 
   if (S.n_tests) ntest = v.unit_tests[(size_t)it.slot * 32 + lane];
   for (; ws.base < ws.n; ws.advance()) {
@@ -154,6 +169,11 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
       const float4 b = sb.rec1[cur][j];
       if (b.x >= fmaxf(kstop1, kstop2)) {
         done = true;
+        break;
+      }
+      if (b.x > kstop3) {
+        done = true;
+        stop_pos = ws.base + j;
         break;
       }
       // The float32 hit depth orders the queue and makes the far-plane cut.
@@ -181,6 +201,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
         if (od != 0.0f) {   // a zero weight adds nothing and must not move the shift
           const float z = (((zfar - a.z) - c2.z) + vg.off) * inv_range;
           blend_hit<CMAX>(bs, b.y * z * inv_gamma, od, &sb.feat[cur][j * StageBuf<CMAX>::FS], id);
+          if (pstop) kstop3 = paper_bound();
         }
       }
       if (may_queue) {
@@ -193,7 +214,15 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
     }
     // a pixel that stopped at no hit still stops once the batch's last key
     // passes its bound (keys rise along the list)
-    if (!done && sb.rec1[cur][ws.count() - 1].x >= fmaxf(kstop1, kstop2)) done = true;
+    if (!done) {
+      const float last = sb.rec1[cur][ws.count() - 1].x;
+      if (last >= fmaxf(kstop1, kstop2)) {
+        done = true;
+      } else if (last > kstop3) {
+        done = true;
+        stop_pos = ws.base + ws.count();
+      }
+    }
   }
   ws.drain();
 
@@ -321,7 +350,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
         }
     }
     v.pix_aux[gpix] = make_float4(key_depth(q[KMAX - 1]), __int_as_float(key_index(q[KMAX - 1])),
-                                  __int_as_float(bs.dom), 0.0f);
+                                  __int_as_float(bs.dom), __int_as_float(stop_pos));
   } else {
     if (!pc.inside) return;
     reinterpret_cast<float2*>(v.pix_aux)[2 * gpix] =

@@ -275,24 +275,24 @@ __global__ void __launch_bounds__(1024) make_items(WsView v) {
   const int64_t per = (nt + 1023) / 1024;
   const int64_t t0 = (int64_t)threadIdx.x * per;
   const int64_t t1 = t0 + per < nt ? t0 + per : nt;
-  const int seg_len = v.segment;
+  const int64_t seg_len = v.segment;
   uint32_t s = 0;
   for (int64_t t = t0; t < t1; ++t) {
     const int2 rg = v.ranges[t];
-    s += (uint32_t)((rg.y - rg.x + seg_len - 1) / seg_len);
+    s += (uint32_t)(((int64_t)rg.y - rg.x + seg_len - 1) / seg_len);
   }
   uint32_t tot;
   uint32_t base = block_exclusive_scan<1024>(s, warp_tot, tot);
   for (int64_t t = t0; t < t1; ++t) {
     const int2 rg = v.ranges[t];
-    const int ns = (rg.y - rg.x + seg_len - 1) / seg_len;
+    const int ns = (int)(((int64_t)rg.y - rg.x + seg_len - 1) / seg_len);
     v.item_begin[t] = (int32_t)base;
     const int scene = ns > 0 ? scene_of_tile(v.scenes, v.n_scenes, t) : 0;
     for (int k = 0; k < ns; ++k) {
       ItemDesc d;
       d.tile = (int32_t)t;
-      d.b0 = rg.x + k * seg_len;
-      d.b1 = min(rg.x + (k + 1) * seg_len, rg.y);
+      d.b0 = (int32_t)(rg.x + k * seg_len);
+      d.b1 = (int32_t)min(rg.x + (k + 1) * seg_len, (int64_t)rg.y);
       d.seg = k;
       d.nseg = ns;
       d.first = (int32_t)base;
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(1024) make_items(WsView v) {
   auto cls = [&](uint32_t i) {
     const ItemDesc& d = v.item_desc[i];
     const int len = d.b1 - d.b0;
-    return (int)(((int64_t)(seg_len - len) * (kOrderBuckets - 1)) / seg_len);
+    return (int)(((seg_len - len) * (kOrderBuckets - 1)) / seg_len);
   };
   for (uint32_t i = threadIdx.x; i < tot; i += 1024) atomicAdd(&bucket[cls(i)], 1u);
   __syncthreads();

@@ -38,6 +38,7 @@ class RenderSettings:
     accumulate: bool = False         # backward adds into the gradient buffers (views sharing them)
     paper_gradients: bool = False    # the paper's gradient normalisations (App. B, Sec. 6)
     orthographic: bool = False       # orthographic camera: pitch = sensor width / W (Sec. 1)
+    paper_stop: bool = False         # the paper's 1 % early termination (App. B, Step 2; approximate)
 
     def flags(self) -> int:
         f = 0
@@ -55,6 +56,8 @@ class RenderSettings:
             f |= _lib.FLAG_PAPER_GRADIENTS
         if self.orthographic:
             f |= _lib.FLAG_ORTHOGRAPHIC
+        if self.paper_stop:
+            f |= _lib.FLAG_PAPER_STOP
         return f
 
     def params(self, n_spheres: int, capacity: int) -> _lib.Params:

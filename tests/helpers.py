@@ -23,7 +23,8 @@ def settings_of(scene: Scene, store=True, dist_literal=False, min_size=True, n_t
                           n_track or scene.n_track, float(scene.gamma), float(scene.eps),
                           float(scene.znear), float(scene.zfar), store, dist_literal, min_size,
                           segment=segment, persistent=persistent, paper_gradients=paper,
-                          orthographic=bool(getattr(scene, "ortho", False)))
+                          orthographic=bool(getattr(scene, "ortho", False)),
+                          paper_stop=bool(getattr(scene, "paper_stop", False)))
 
 
 def gpu_forward(scene: Scene, store=True, dist_literal=False, min_size=True, capacity=None,

@@ -55,7 +55,7 @@ def test_workspace_size_validates_settings(lib):
     assert lib.lib().pulsar_workspace_size(ctypes.byref(_params(lib))) > 0
     bad = [dict(width=0), dict(height=70000), dict(n_channels=0), dict(n_track=0), dict(gamma=2.0),
            dict(gamma=1e-7), dict(znear=0.0), dict(zfar=0.5), dict(list_capacity=-1),
-           dict(flags=1 << 7), dict(n_spheres=-1)]
+           dict(flags=1 << 8), dict(n_spheres=-1)]
     for b in bad:
         assert lib.lib().pulsar_workspace_size(ctypes.byref(_params(lib, **b))) == 0, b
     unsupported = [dict(n_channels=33), dict(n_track=33), dict(tile=8)]
@@ -159,4 +159,7 @@ def test_fit_entry_points_reject_bad_arguments_on_the_host(lib):
     assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=lib.FLAG_PAPER_GRADIENTS))) > \
         L.pulsar_workspace_size(ctypes.byref(_params(lib)))   # per-sphere sums of the paper mode
     assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=lib.FLAG_ORTHOGRAPHIC))) > 0
-    assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=1 << 7))) == 0
+    # the paper's early termination keeps every tile's list whole: fewer work items
+    assert 0 < L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=lib.FLAG_PAPER_STOP))) <= \
+        L.pulsar_workspace_size(ctypes.byref(_params(lib)))
+    assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=1 << 8))) == 0

@@ -347,3 +347,71 @@ def test_test_rectangles_miss_no_hit(orc, ortho):
     np.testing.assert_array_equal(gpu["n_hits"].cpu().numpy(), ref.n_hits)
     np.testing.assert_array_equal(gpu["tracked"].cpu().numpy(), ref.tracked)
     assert np.abs(gpu["image"].cpu().numpy() - ref.image).max() <= 1e-4
+
+
+def _deep_cloud(seed, n, W, H, rad):
+    """Spheres from depth 2 to 18 at gamma 0.05: far hits behind near ones
+    fall below the 1 % of the paper's early termination at a few per cent of
+    the pixels."""
+    sc = S.uniform_cloud(seed, n, W, H, gamma=0.05, n_track=5, rad=rad, z=(2.0, 18.0))
+    sc.paper_stop = True
+    return sc
+
+
+def _truncation_bound(exact, stop, sc):
+    """Largest colour change from leaving out n hits (each with a weight
+    numerator at most A, A / (D + A) < 1 %): 2 f_max n t / (1 + n t)."""
+    left = exact.n_hits - stop.n_hits
+    t = 0.01 / 0.99
+    fmax = max(float(np.abs(sc.feat).max()), float(np.abs(sc.bg).max()))
+    return 2.0 * fmax * left * t / (1.0 + left * t)
+
+
+@pytest.mark.parametrize("persistent", [False, True], ids=["items", "persistent"])
+def test_paper_stop_forward_matches_oracle(orc, persistent):
+    """The paper's early termination (App. B, Step 2): on every pixel whose
+    decisions lie clear of the 1 % threshold (|ln(a / 0.01)| >= 1e-3 for every
+    test the oracle takes; a float32 denominator can only decide otherwise
+    nearer) the image is at oracle parity and the tracked hits are equal; every
+    pixel stays within the truncation bound of the exact image."""
+    sc = _deep_cloud(85, 2000, 64, 48, (0.05, 0.4))
+    ref = orc.render(sc)
+    margin = orc.paper_stop_margin(sc)
+    sc_exact = S.Scene(**{**sc.__dict__, "paper_stop": False})
+    exact = orc.render(sc_exact)
+    assert (exact.n_hits > ref.n_hits).mean() > 0.01          # the option does cut lists here
+    gpu = gpu_forward(sc, persistent=persistent)
+    img = gpu["image"].cpu().numpy()
+    clear = margin >= 1e-3
+    assert clear.mean() >= 0.99
+    err = np.abs(img - ref.image).max(axis=2)
+    assert err[clear].max() <= 1e-4
+    np.testing.assert_array_equal(gpu["tracked"].cpu().numpy()[clear], ref.tracked[clear])
+    bound = _truncation_bound(exact, ref, sc)
+    assert np.all(np.abs(img - exact.image).max(axis=2) <= bound + 1e-4)
+    # the exact renderer differs from it by the truncation
+    plain = gpu_forward(sc_exact)
+    assert np.abs(plain["image"].cpu().numpy() - exact.image).max() <= 1e-4
+
+
+def test_paper_stop_gradients_match_oracle(orc):
+    """Gradients through the hits the early termination kept (the forward
+    pass records where each pixel stopped); every decision of this scene lies
+    at least 2e-3 from the threshold.  Without stored hits the backward pass
+    reports an unsupported setting."""
+    sc = _deep_cloud(86, 600, 48, 40, (0.1, 0.5))
+    assert orc.paper_stop_margin(sc).min() >= 2e-3
+    ref = orc.render(sc)
+    gpu = gpu_forward(sc)
+    assert np.abs(gpu["image"].cpu().numpy() - ref.image).max() <= 1e-4
+    np.testing.assert_array_equal(gpu["tracked"].cpu().numpy(), ref.tracked)
+    G = S.grad_image(12, sc.height, sc.width, sc.n_channels)
+    want = orc.render_backward(sc, G)
+    assert_grads_close(gpu_backward(gpu, G), want, scene=sc)
+    # the gradients differ from the exact renderer's (hits were left out)
+    sc_exact = S.Scene(**{**sc.__dict__, "paper_stop": False})
+    full = orc.render_backward(sc_exact, G)
+    assert np.abs(full.opa - want.opa).max() > 1e-5 * np.abs(full.opa).max()
+    rec = gpu_forward(sc, store=False)
+    with pytest.raises(Exception, match="unsupported"):
+        gpu_backward(rec, G)
