@@ -96,7 +96,8 @@ enum {
   /* The paper's early termination (App. B, Step 2; an approximation, the
    * paper's default), on top of the exact one: a pixel takes its hits in list
    * order (sort key, then index) and stops before the first hit whose largest
-   * possible weight e^{o_max z_k / g} / (D + e^{o_max z_k / g}) is below 1 %,
+   * possible weight e^{o_max z_k / g} / (D + e^{o_max z_k / g}) is below
+   * min_contrib (the paper's "n percent" as a fraction, 1 % by default),
    * z_k the depth term of the sphere's sort key, o_max the largest |o| of
    * the scene's visible spheres and D the denominator of Eq. 1 over the hits
    * taken; blending and tracking see only the hits taken.  The decision is
@@ -137,6 +138,9 @@ typedef struct {
                               render passes (a tile's list is split into segments
                               rendered in parallel and merged); 0 = 1024, else a
                               multiple of 32 in [32, 65536] */
+  float min_contrib;       /* PULSAR_FLAG_PAPER_STOP: the fraction of the blend below
+                              which a hit stops a pixel, in [0, 1); 0 = 0.01, the
+                              paper's default.  Ignored without the flag. */
 } pulsar_params;
 
 /* Scene inputs: device pointers, float32, contiguous. */

@@ -32,6 +32,7 @@ class OrcParams(ctypes.Structure):
         ("ortho", ctypes.c_int32), ("paper_stop", ctypes.c_int32),
         ("gamma", ctypes.c_double), ("eps", ctypes.c_double),
         ("znear", ctypes.c_double), ("zfar", ctypes.c_double),
+        ("min_contrib", ctypes.c_double),
     ]
 
 
@@ -90,7 +91,8 @@ def _d(a) -> np.ndarray:
 def params(scene, tile: int = 16, min_size: bool = True, dist_literal: bool = False,
            n_track: int | None = None, paper_grad: bool = False, ortho: bool | None = None) -> OrcParams:
     """ortho=None takes the scene's own ``ortho`` attribute (False when absent);
-    the scene's ``paper_stop`` attribute selects the paper's early termination."""
+    the scene's ``paper_stop`` attribute selects the paper's early termination,
+    with the threshold ``min_contrib`` (float32 value; 0.01 when absent)."""
     if ortho is None:
         ortho = bool(getattr(scene, "ortho", False))
     paper_stop = bool(getattr(scene, "paper_stop", False))
@@ -99,7 +101,8 @@ def params(scene, tile: int = 16, min_size: bool = True, dist_literal: bool = Fa
                      int(tile), int(bool(min_size)), int(bool(dist_literal)), int(bool(paper_grad)),
                      int(bool(ortho)), int(paper_stop),
                      float(np.float32(scene.gamma)), float(np.float32(scene.eps)),
-                     float(np.float32(scene.znear)), float(np.float32(scene.zfar)))
+                     float(np.float32(scene.znear)), float(np.float32(scene.zfar)),
+                     float(np.float32(getattr(scene, "min_contrib", 0.01))))
 
 
 @dataclass
@@ -188,7 +191,7 @@ def render(scene, n_track: int | None = None, min_size: bool = True, dist_litera
 
 
 def paper_stop_margin(scene, **kw) -> np.ndarray:
-    """(H, W) float64: per pixel the smallest |ln(a / 0.01)| over the early-
+    """(H, W) float64: per pixel the smallest |ln(a / min_contrib)| over the early-
     termination tests the pixel takes (scene.paper_stop set), a the largest
     possible weight tested; +inf where no test is taken."""
     p = params(scene, **kw)

@@ -60,9 +60,10 @@
  *               default, an approximation): a pixel takes its hits in the tile
  *               list's order (sort key c_z - R, then index) and stops before
  *               the first whose largest possible weight e^{o_max z_b / g} /
- *               (D + e^{o_max z_b / g}) is below 1 %, z_b the depth term of its
- *               key, o_max the largest opacity of the scene's visible spheres
- *               and D the denominator of the hits taken so far; blending and
+ *               (D + e^{o_max z_b / g}) is below min_contrib (the paper's
+ *               "n percent", 1 % by default), z_b the depth term of its key,
+ *               o_max the largest opacity of the scene's visible spheres and D
+ *               the denominator of the hits taken so far; blending and
  *               tracking see only the hits taken.
  */
 #include <math.h>
@@ -80,8 +81,9 @@ typedef struct {
   int32_t dist_literal;  /* 1: d = min(1, dist/R) instead of 1 - min(1, dist/R) */
   int32_t paper_grad;    /* 1: the paper's gradient normalisations (header) */
   int32_t ortho;         /* 1: orthographic camera (header) */
-  int32_t paper_stop;    /* 1: the paper's 1 % early termination (header) */
+  int32_t paper_stop;    /* 1: the paper's early termination (header) */
   double gamma, eps, znear, zfar;
+  double min_contrib;    /* its threshold as a fraction (the paper's n percent; 0.01 by default) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -401,7 +403,7 @@ static void ray_values(const orc_params* P, const sph64* s, double rx, double ry
  * otherwise only where this is small). */
 static int paper_stop_filter(const orc_params* P, const ctx_t* C, int u, int v, hit_rec* hits, int n,
                              double* margin) {
-  const double tau = 0.01, g = P->gamma, zr = P->zfar - P->znear;
+  const double tau = P->min_contrib, g = P->gamma, zr = P->zfar - P->znear;
   double rx = (double)(2 * u + 1 - P->width) * 0.5 * C->kappa;
   double ry = (double)(2 * v + 1 - P->height) * 0.5 * C->kappa;
   double m = P->eps / g, den = 1.0;   /* the background term alone, shifted by its own exponent */
@@ -590,7 +592,7 @@ void orc_render_fwd(const orc_params* P, const double* pos, const double* rad,
 }
 
 /* The decision margin of the early termination (paper_stop set): per pixel
- * the smallest |ln(a / 0.01)| over the tests the pixel takes, a the largest
+ * the smallest |ln(a / min_contrib)| over the tests the pixel takes, a the largest
  * possible weight tested (see paper_stop_filter); +inf where no test is
  * taken.  margin: H x W. */
 void orc_paper_stop_margin(const orc_params* P, const double* pos, const double* rad,

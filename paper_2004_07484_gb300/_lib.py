@@ -50,6 +50,7 @@ class Params(ctypes.Structure):
         ("gamma", ctypes.c_float), ("eps", ctypes.c_float),
         ("znear", ctypes.c_float), ("zfar", ctypes.c_float),
         ("flags", ctypes.c_uint32), ("segment", ctypes.c_int32),
+        ("min_contrib", ctypes.c_float),
     ]
 
 

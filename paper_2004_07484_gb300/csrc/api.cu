@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "pulsar_internal.cuh"
@@ -79,6 +80,7 @@ pulsar_status validate(const pulsar_params* p) {
     return PULSAR_ERR_INVALID_ARG;
   if (p->segment != 0 && (p->segment < 32 || p->segment > 65536 || p->segment % 32 != 0))
     return PULSAR_ERR_INVALID_ARG;
+  if (!(p->min_contrib >= 0.0f && p->min_contrib < 1.0f)) return PULSAR_ERR_INVALID_ARG;
   return PULSAR_OK;
 }
 
@@ -247,6 +249,11 @@ void fill_scenes(const pulsar_params* ps, const pulsar_scene* sc, int n, SceneDe
     d.n_channels = p.n_channels;
     d.n_track = p.n_track;
     d.flags = p.flags;
+    {
+      // ln(tau / (1 - tau)) of the paper's early termination
+      const double tau = p.min_contrib > 0.0f ? (double)p.min_contrib : 0.01;
+      d.stop_log_ratio = (float)std::log(tau / (1.0 - tau));
+    }
     tiles_of(p, d.tiles_x, d.tiles_y);
     d.sphere_begin = sb;
     d.tile_begin = tb;

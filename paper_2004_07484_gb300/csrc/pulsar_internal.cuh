@@ -29,8 +29,6 @@ constexpr int kFinalizeThreads = 256;
 constexpr int kCamPartials = 16;     // floats per finalize-block camera partial (13 used)
 constexpr int kDefaultSegment = 1024;  // list entries one CTA processes per work item
 constexpr int kWholeList = 1 << 30;    // segment length that keeps every tile's list whole
-// ln(0.01 / 0.99): the paper's early termination drops hits below 1 % of the blend
-constexpr float kLogStopRatio = -4.59511985013459f;
 constexpr int kTileKeyBits = 24;        // pair keys: tile index bits (the block set above them)
 constexpr uint32_t kTileKeyMask = (1u << kTileKeyBits) - 1u;
 
@@ -79,6 +77,7 @@ struct SceneDev {
   float kappa;               // pixel pitch on the unit image plane, s / (W f), float32 decisions
   float kappa_hi, kappa_lo;  // kappa64 split into two floats (value path)
   uint32_t omax_bits;        // max |o| over visible spheres, float bits
+  float stop_log_ratio;      // ln(tau / (1 - tau)), tau the early-termination threshold
   uint32_t pad_;             // unused
 };
 

@@ -44,9 +44,9 @@
 //
 // With PULSAR_FLAG_PAPER_STOP a pixel also stops, as the paper's renderer
 // does (App. B, Step 2), before the first hit whose largest possible weight
-// A = e^{o_max z_b / g} is below 1 % of D + A; that is, with D = e^{m} den,
-// beyond the key
-//   k3 = zfar - (zfar - znear) (g / o_max) (m + ln den + ln(0.01 / 0.99)),
+// A = e^{o_max z_b / g} is below tau (1 % by default) of D + A; that is, with
+// D = e^{m} den, beyond the key
+//   k3 = zfar - (zfar - znear) (g / o_max) (m + ln den + ln(tau / (1 - tau))),
 // which only falls as hits are blended.  The pixel's list position where it
 // stopped goes to the backward pass with the tracked set.  Tiles then have a
 // single segment, as the rule needs the pixel's whole denominator.
@@ -142,7 +142,8 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   // the paper's early termination: its key bound and where the pixel stopped
   const bool pstop = BLEND && (S.flags & PULSAR_FLAG_PAPER_STOP) != 0 && omax > 0.0f;
   const float pscale = range * gamma / omax;
-  auto paper_bound = [&]() { return zfar - pscale * ((bs.m + __logf(bs.den)) + kLogStopRatio); };
+  const float log_ratio = S.stop_log_ratio;
+  auto paper_bound = [&]() { return zfar - pscale * ((bs.m + __logf(bs.den)) + log_ratio); };
   float kstop3 = pstop ? paper_bound() : __int_as_float(0x7f800000);
   int stop_pos = 0x7fffffff;
 

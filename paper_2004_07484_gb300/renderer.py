@@ -38,7 +38,8 @@ class RenderSettings:
     accumulate: bool = False         # backward adds into the gradient buffers (views sharing them)
     paper_gradients: bool = False    # the paper's gradient normalisations (App. B, Sec. 6)
     orthographic: bool = False       # orthographic camera: pitch = sensor width / W (Sec. 1)
-    paper_stop: bool = False         # the paper's 1 % early termination (App. B, Step 2; approximate)
+    paper_stop: bool = False         # the paper's early termination (App. B, Step 2; approximate)
+    min_contrib: float = 0.0         # its threshold as a fraction of the blend; 0 = 0.01 (the paper's)
 
     def flags(self) -> int:
         f = 0
@@ -64,7 +65,7 @@ class RenderSettings:
         return _lib.Params(int(self.width), int(self.height), int(n_spheres), int(self.n_channels),
                            int(self.n_track), int(self.tile), int(capacity), float(self.gamma),
                            float(self.eps), float(self.znear), float(self.zfar), int(self.flags()),
-                           int(self.segment))
+                           int(self.segment), float(self.min_contrib))
 
 
 def _dev_f32(name: str, t: torch.Tensor, shape) -> torch.Tensor:

@@ -46,7 +46,8 @@ class Scene:
     name: str = ""
     meta: dict = field(default_factory=dict)
     ortho: bool = False      # orthographic camera (rays along +z from the sensor plane)
-    paper_stop: bool = False # the paper's 1 % early termination (an approximation)
+    paper_stop: bool = False # the paper's early termination (an approximation)
+    min_contrib: float = 0.01  # its threshold (the paper's "n percent" as a fraction)
 
     @property
     def n_spheres(self) -> int:

@@ -24,7 +24,8 @@ def settings_of(scene: Scene, store=True, dist_literal=False, min_size=True, n_t
                           float(scene.znear), float(scene.zfar), store, dist_literal, min_size,
                           segment=segment, persistent=persistent, paper_gradients=paper,
                           orthographic=bool(getattr(scene, "ortho", False)),
-                          paper_stop=bool(getattr(scene, "paper_stop", False)))
+                          paper_stop=bool(getattr(scene, "paper_stop", False)),
+                          min_contrib=float(getattr(scene, "min_contrib", 0.01)))
 
 
 def gpu_forward(scene: Scene, store=True, dist_literal=False, min_size=True, capacity=None,

@@ -55,7 +55,8 @@ def test_workspace_size_validates_settings(lib):
     assert lib.lib().pulsar_workspace_size(ctypes.byref(_params(lib))) > 0
     bad = [dict(width=0), dict(height=70000), dict(n_channels=0), dict(n_track=0), dict(gamma=2.0),
            dict(gamma=1e-7), dict(znear=0.0), dict(zfar=0.5), dict(list_capacity=-1),
-           dict(flags=1 << 8), dict(n_spheres=-1)]
+           dict(flags=1 << 8), dict(n_spheres=-1), dict(min_contrib=-0.01), dict(min_contrib=1.0),
+           dict(min_contrib=float("nan"))]
     for b in bad:
         assert lib.lib().pulsar_workspace_size(ctypes.byref(_params(lib, **b))) == 0, b
     unsupported = [dict(n_channels=33), dict(n_track=33), dict(tile=8)]

@@ -360,21 +360,24 @@ def _deep_cloud(seed, n, W, H, rad):
 
 def _truncation_bound(exact, stop, sc):
     """Largest colour change from leaving out n hits (each with a weight
-    numerator at most A, A / (D + A) < 1 %): 2 f_max n t / (1 + n t)."""
+    numerator at most A, A / (D + A) < tau): 2 f_max n t / (1 + n t)."""
     left = exact.n_hits - stop.n_hits
-    t = 0.01 / 0.99
+    tau = float(np.float32(sc.min_contrib))
+    t = tau / (1.0 - tau)
     fmax = max(float(np.abs(sc.feat).max()), float(np.abs(sc.bg).max()))
     return 2.0 * fmax * left * t / (1.0 + left * t)
 
 
-@pytest.mark.parametrize("persistent", [False, True], ids=["items", "persistent"])
-def test_paper_stop_forward_matches_oracle(orc, persistent):
+@pytest.mark.parametrize("persistent,tau", [(False, 0.01), (True, 0.01), (False, 0.05)],
+                         ids=["items", "persistent", "5-percent"])
+def test_paper_stop_forward_matches_oracle(orc, persistent, tau):
     """The paper's early termination (App. B, Step 2): on every pixel whose
-    decisions lie clear of the 1 % threshold (|ln(a / 0.01)| >= 1e-3 for every
+    decisions lie clear of the threshold (|ln(a / tau)| >= 1e-3 for every
     test the oracle takes; a float32 denominator can only decide otherwise
     nearer) the image is at oracle parity and the tracked hits are equal; every
     pixel stays within the truncation bound of the exact image."""
     sc = _deep_cloud(85, 2000, 64, 48, (0.05, 0.4))
+    sc.min_contrib = tau
     ref = orc.render(sc)
     margin = orc.paper_stop_margin(sc)
     sc_exact = S.Scene(**{**sc.__dict__, "paper_stop": False})

@@ -570,13 +570,17 @@ def _stop_column(t4):
     return sc
 
 
-@pytest.mark.parametrize("t4, taken", [(7.0, 3), (6.8, 4)])
-def test_paper_stop_on_a_column_of_spheres(orc, t4, taken):
+@pytest.mark.parametrize("t4, tau, taken", [(7.0, 0.01, 3), (6.8, 0.01, 4), (6.8, 0.02, 3),
+                                             (7.0, 0.005, 4)])
+def test_paper_stop_on_a_column_of_spheres(orc, t4, tau, taken):
     """By hand: the fourth sphere's largest possible weight is e^{4} / (e^{8} +
-    e^{7.5} + e^{7} + e^{4} + e^{0.001}) = 0.0092 < 1 % at t4 = 7 (the pixel
-    stops after three hits) and e^{4.2} / (...) = 0.0112 at t4 = 6.8 (it takes
-    all four); the second and third spheres pass by far (0.38, 0.19)."""
+    e^{7.5} + e^{7} + e^{4} + e^{0.001}) = 0.0092 at t4 = 7 and e^{4.2} / (...)
+    = 0.0112 at t4 = 6.8, so the pixel stops after three hits where that is
+    below the threshold (1 % at t4 = 7, 2 % at t4 = 6.8) and takes all four
+    otherwise (1 % at t4 = 6.8, 0.5 % at t4 = 7); the second and third spheres
+    pass by far (0.38, 0.19)."""
     sc = _stop_column(t4)
+    sc.min_contrib = tau
     out = orc.render(sc)
     c = 32
     assert out.n_hits[c, c] == taken
@@ -591,7 +595,7 @@ def test_paper_stop_on_a_column_of_spheres(orc, t4, taken):
     # the smallest distance to the threshold is the fourth test's
     a4 = math.exp(e[3]) / (B + sum(math.exp(x) for x in e))
     margin = orc.paper_stop_margin(sc)
-    assert margin[c, c] == pytest.approx(abs(math.log(a4 / 0.01)), rel=1e-9)
+    assert margin[c, c] == pytest.approx(abs(math.log(a4 / f32(tau))), rel=1e-9)
     # without the option every pixel takes every hit
     sc.paper_stop = False
     assert orc.render(sc).n_hits[c, c] == 4
