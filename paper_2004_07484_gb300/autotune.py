@@ -3,9 +3,9 @@
 The paper renders one scene per call with a fixed launch shape.  For a batch
 of uneven scenes, two scheduling choices of this library change only the
 speed, never the result: the segment length (list entries per work item; a
-tile's list is split into segments rendered in parallel and merged) and
-the kernel form (one CTA per work unit, or persistent CTAs taking units from
-a counter).  ``tune`` sizes every scene's pair-list capacity from one binning
+tile's list is split into segments rendered in parallel and merged; with the
+paper's early termination lists stay whole) and the kernel form (one CTA per
+work unit, or persistent CTAs taking units from a counter).  ``tune`` sizes every scene's pair-list capacity from one binning
 pass of the batch itself, then times the batch's forward + backward for each
 candidate and keeps the fastest.  Results are cached per batch signature
 (scene count, image sizes, sphere counts rounded to powers of two, channels,
@@ -41,7 +41,8 @@ def signature(settings: list[RenderSettings], n_spheres: list[int]) -> tuple:
     s0 = settings[0]
     sizes = tuple(sorted((s.width, s.height, max(0, int(math.log2(max(m, 1))))) for s, m in
                          zip(settings, n_spheres)))
-    return (len(settings), sizes, s0.n_channels, s0.n_track, s0.store_hits, s0.dist_literal, s0.min_size)
+    return (len(settings), sizes, s0.n_channels, s0.n_track, s0.store_hits, s0.dist_literal, s0.min_size,
+            s0.paper_stop, s0.orthographic, s0.paper_gradients)
 
 
 def pairs_per_scene(settings: list[RenderSettings], inputs) -> list[int]:
@@ -89,7 +90,8 @@ def tune(settings: list[RenderSettings], inputs, grads, reps: int = 3, use_cache
     pairs = pairs_per_scene(settings, inputs)
     caps = [int(p * CAPACITY_MARGIN) + 1024 for p in pairs]
     ms = {}
-    for seg in SEGMENTS:
+    # the paper's early termination keeps every tile's list whole: only the form is chosen
+    for seg in ((0,) if settings[0].paper_stop else SEGMENTS):
         for pers in FORMS:
             cand = [replace(s, segment=seg, persistent=pers) for s in settings]
             ms[(seg, pers)] = time_step(cand, inputs, grads, caps, reps)
