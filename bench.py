@@ -576,14 +576,15 @@ def main():
     pairs_needed = autotune.pairs_per_scene([base], inputs)[0]
     capacity = tuned.capacities[0]
 
-    # the paper's early termination keeps lists whole; its kernel form is tuned on its own
+    # the paper's early termination walks a tile's segments in order; its
+    # scheduling is tuned on its own
     tuned_ps = autotune.tune([replace(base, paper_stop=True)], inputs, [G])
 
     def settings(store: bool, paper_stop: bool = False):
         if paper_stop:
             return RenderSettings(sc.width, sc.height, sc.n_channels, sc.n_track, sc.gamma, sc.eps,
-                                  sc.znear, sc.zfar, store_hits=store, persistent=tuned_ps.persistent,
-                                  paper_stop=True)
+                                  sc.znear, sc.zfar, store_hits=store, segment=tuned_ps.segment,
+                                  persistent=tuned_ps.persistent, paper_stop=True)
         return RenderSettings(sc.width, sc.height, sc.n_channels, sc.n_track, sc.gamma, sc.eps,
                               sc.znear, sc.zfar, store_hits=store, segment=tuned.segment,
                               persistent=tuned.persistent)
@@ -804,8 +805,9 @@ def main():
             "paper_stop": {"value": job_throughput(world, len(ms_ps), ps_total_ms),
                            "unit": UNIT, "ms_per_step": statistics.mean(ms_ps),
                            "what": "the paper's 1% early termination on top of the exact one "
-                                   "(approximate; whole tile lists per work item), stored hits",
-                           "persistent": tuned_ps.persistent},
+                                   "(approximate; one render unit walks a tile's segments in order), "
+                                   "stored hits",
+                           "segment": tuned_ps.segment, "persistent": tuned_ps.persistent},
             "e2e": {"value": job_throughput(world, 1, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "how": "pinned host buffers; per step the inputs (positions, features, radii, opacities, "

@@ -101,10 +101,10 @@ enum {
    * z_k the depth term of the sphere's sort key, o_max the largest |o| of
    * the scene's visible spheres and D the denominator of Eq. 1 over the hits
    * taken; blending and tracking see only the hits taken.  The decision is
-   * taken in float32.  Each tile's list is then one work item (`segment` is
-   * ignored), and the backward pass needs PULSAR_FLAG_STORE_HITS (without it
-   * PULSAR_ERR_UNSUPPORTED): the forward pass records where each pixel
-   * stopped.  Forward and backward calls take the same flags. */
+   * taken in float32.  A render unit then walks every segment of its tile's
+   * list in order, and the backward pass needs PULSAR_FLAG_STORE_HITS
+   * (without it PULSAR_ERR_UNSUPPORTED): the forward pass records where each
+   * pixel stopped.  Forward and backward calls take the same flags. */
   PULSAR_FLAG_PAPER_STOP = 1u << 7
 };
 

@@ -4,8 +4,9 @@ The paper renders one scene per call with a fixed launch shape.  For a batch
 of uneven scenes, two scheduling choices of this library change only the
 speed, never the result: the segment length (list entries per work item; a
 tile's list is split into segments rendered in parallel and merged; with the
-paper's early termination lists stay whole) and the kernel form (one CTA per
-work unit, or persistent CTAs taking units from a counter).  ``tune`` sizes every scene's pair-list capacity from one binning
+paper's early termination one unit walks a tile's segments in order) and the
+kernel form (one CTA per work unit, or persistent CTAs taking units from a
+counter).  ``tune`` sizes every scene's pair-list capacity from one binning
 pass of the batch itself, then times the batch's forward + backward for each
 candidate and keeps the fastest.  Results are cached per batch signature
 (scene count, image sizes, sphere counts rounded to powers of two, channels,
@@ -90,8 +91,7 @@ def tune(settings: list[RenderSettings], inputs, grads, reps: int = 3, use_cache
     pairs = pairs_per_scene(settings, inputs)
     caps = [int(p * CAPACITY_MARGIN) + 1024 for p in pairs]
     ms = {}
-    # the paper's early termination keeps every tile's list whole: only the form is chosen
-    for seg in ((0,) if settings[0].paper_stop else SEGMENTS):
+    for seg in SEGMENTS:
         for pers in FORMS:
             cand = [replace(s, segment=seg, persistent=pers) for s in settings]
             ms[(seg, pers)] = time_step(cand, inputs, grads, caps, reps)

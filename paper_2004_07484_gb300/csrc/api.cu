@@ -109,11 +109,7 @@ Layout make_layout(const pulsar_params* ps, int n) {
   int bits = 1;
   while (bits < 32 && ((int64_t)1 << bits) < NT) ++bits;
   L.tile_bits = bits;
-  // the paper's early termination follows a pixel's denominator along the
-  // whole list: one segment per tile
-  L.segment = (ps[0].flags & PULSAR_FLAG_PAPER_STOP) ? kWholeList
-              : ps[0].segment > 0                     ? ps[0].segment
-                                                      : kDefaultSegment;
+  L.segment = ps[0].segment > 0 ? ps[0].segment : kDefaultSegment;
   L.max_items = NT + (cap + L.segment - 1) / L.segment;
   L.part_fields = 6 + C + 2 * K;
   size_t off = 0;
@@ -188,6 +184,9 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.part_fields = L.part_fields;
   v.persistent = (ps[0].flags & PULSAR_FLAG_PERSISTENT) ? 1 : 0;
   v.paper = (ps[0].flags & PULSAR_FLAG_PAPER_GRADIENTS) ? 1 : 0;
+  // the paper's early termination follows a pixel's denominator along its
+  // whole list: one render unit walks every segment of its tile in order
+  v.chain = (ps[0].flags & PULSAR_FLAG_PAPER_STOP) ? 1 : 0;
   v.rec0 = reinterpret_cast<float4*>(b + L.rec0);
   v.rec1 = reinterpret_cast<float4*>(b + L.rec1);
   v.rec2 = reinterpret_cast<float4*>(b + L.rec2);

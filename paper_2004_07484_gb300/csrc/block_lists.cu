@@ -145,12 +145,23 @@ __device__ __forceinline__ int cost_class(uint32_t c) {
   return max(kCostClasses - 1 - cls, 0);
 }
 
+// Cost of unit u as the render passes see it: with a chained walk the first
+// segment's unit renders all segments of its tile and the others none.
+__device__ __forceinline__ uint32_t walk_cost(const WsView& v, uint32_t u) {
+  if (!v.chain) return v.unit_cost[u];
+  const ItemDesc d = v.item_desc[u / kBlocksPerTile];
+  if (d.seg != 0) return 0u;
+  uint32_t c = 0;
+  for (int k = d.first; k < d.first + d.nseg; ++k) c += v.unit_cost[k * kBlocksPerTile + u % kBlocksPerTile];
+  return c;
+}
+
 __global__ void __launch_bounds__(1024) order_units_kernel(const WsView v) {
   __shared__ uint32_t bucket[kCostClasses];
   const uint32_t n = (uint32_t)v.hdr->n_items * kBlocksPerTile;
   if (threadIdx.x < kCostClasses) bucket[threadIdx.x] = 0u;
   __syncthreads();
-  for (uint32_t u = threadIdx.x; u < n; u += 1024) atomicAdd(&bucket[cost_class(v.unit_cost[u])], 1u);
+  for (uint32_t u = threadIdx.x; u < n; u += 1024) atomicAdd(&bucket[cost_class(walk_cost(v, u))], 1u);
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t run = 0;
@@ -162,7 +173,7 @@ __global__ void __launch_bounds__(1024) order_units_kernel(const WsView v) {
   }
   __syncthreads();
   for (uint32_t u = threadIdx.x; u < n; u += 1024)
-    v.unit_order[atomicAdd(&bucket[cost_class(v.unit_cost[u])], 1u)] = (int32_t)u;
+    v.unit_order[atomicAdd(&bucket[cost_class(walk_cost(v, u))], 1u)] = (int32_t)u;
 }
 
 // The n_tests diagnostic: per work unit and pixel, the spheres of the

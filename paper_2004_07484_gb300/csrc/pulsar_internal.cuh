@@ -28,7 +28,6 @@ constexpr int kMaxScenes = 64;
 constexpr int kFinalizeThreads = 256;
 constexpr int kCamPartials = 16;     // floats per finalize-block camera partial (13 used)
 constexpr int kDefaultSegment = 1024;  // list entries one CTA processes per work item
-constexpr int kWholeList = 1 << 30;    // segment length that keeps every tile's list whole
 constexpr int kTileKeyBits = 24;        // pair keys: tile index bits (the block set above them)
 constexpr uint32_t kTileKeyMask = (1u << kTileKeyBits) - 1u;
 
@@ -124,6 +123,7 @@ struct WsView {
   int32_t part_fields;       // floats per pixel of a partial forward state
   int32_t persistent;        // render passes run as persistent kernels
   int32_t paper;             // the paper's gradient normalisations
+  int32_t chain;             // render units walk a tile's segments in order (early termination)
   float4* rec0;              // per sphere: c.x, c.y, c.z, R^2
   float4* rec1;              // per sphere: key, o, x-range (x0 | x1 << 16), y-range
   float4* rec2;              // per sphere: c - c.xyz (low-order part of the double centre), R

@@ -64,10 +64,16 @@ __device__ __forceinline__ void add_hit_grads(int id_global, int64_t id_local, f
 
 // Back-propagates through work unit w (a pixel block of one work item) with
 // one warp.
-template <int CMAX>
+template <int CMAX, bool CHAIN>
 __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, StageBuf<CMAX, kBwdBuffers>& sb) {
   ItemCtx it;
   if (!item_ctx(v, w, it)) return;
+  const bool cam = (mask & PULSAR_GRAD_CAM) != 0;
+  // a chained walk handles the tile's later segments from its first
+  if (CHAIN && it.seg != 0) {
+    if (cam && threadIdx.x == 0) v.item_kappa[it.slot] = 0.0f;
+    return;
+  }
   const SceneDev& S = v.scenes[it.scene];
   const PixelCtx pc = pixel_ctx(S, it.tile, it.block);
   const int C = S.n_channels;
@@ -79,13 +85,12 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
   const bool geo = (mask & (PULSAR_GRAD_POS | PULSAR_GRAD_RAD | PULSAR_GRAD_CAM)) != 0;
   const bool opa = (mask & PULSAR_GRAD_OPA) != 0;
   const bool feat = (mask & PULSAR_GRAD_FEAT) != 0;
-  const bool cam = (mask & PULSAR_GRAD_CAM) != 0;
   const bool bgw = (mask & PULSAR_GRAD_BG) != 0;
   const bool per_hit = geo || opa || feat;
   const int lane = threadIdx.x & 31;
 
   // the first batches of the block list stage while the pixel data loads
-  UnitStream<CMAX, kBwdBuffers> ws;
+  UnitStream<CMAX, kBwdBuffers, CHAIN> ws;
   if (per_hit) ws.start(sb, v, S, it, true);
 
   // per-pixel upstream data
@@ -262,19 +267,19 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
 
 // One CTA per work unit, or (persistent) one resident CTA per slot taking
 // units from the workspace counter.
-template <int CMAX>
+template <int CMAX, bool CHAIN>
 __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v, uint32_t mask) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageBuf<CMAX, kBwdBuffers>& sb = *reinterpret_cast<StageBuf<CMAX, kBwdBuffers>*>(smem_raw);
   if (!v.persistent) {
-    bwd_unit<CMAX>(v, mask, blockIdx.x, sb);
+    bwd_unit<CMAX, CHAIN>(v, mask, blockIdx.x, sb);
     return;
   }
   const int n_units = v.hdr->n_items * kBlocksPerTile;
   for (;;) {
     const int w = next_unit(v);
     if (w >= n_units) break;
-    bwd_unit<CMAX>(v, mask, w, sb);
+    bwd_unit<CMAX, CHAIN>(v, mask, w, sb);
     __syncwarp();
   }
 }
@@ -282,7 +287,8 @@ __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v, uint
 template <int CMAX>
 cudaError_t launch_bwd_t(const WsView& v, uint32_t mask, cudaStream_t st) {
   const size_t smem = sizeof(StageBuf<CMAX, kBwdBuffers>);
-  auto kern = render_bwd_kernel<CMAX>;
+  // the paper's early termination walks a tile's segments in order
+  auto kern = v.chain ? render_bwd_kernel<CMAX, true> : render_bwd_kernel<CMAX, false>;
   unsigned grid = (unsigned)v.max_items * kBlocksPerTile;
   if (v.persistent) {
     const unsigned slots = resident_slots(kern, 32, smem);

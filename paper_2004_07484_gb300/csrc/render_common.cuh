@@ -201,18 +201,46 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <int CMAX, int NB = 2>
+template <int CMAX, int NB = 2, bool CHAIN = false>
 struct UnitStream {
   static_assert(NB >= 2, "at least double buffering");
-  const uint2* __restrict__ src;   // the unit's block list
+  const uint2* __restrict__ src;   // the unit's block list (of its pixel block, all segments)
   int n;                           // its length
   int base;                        // first entry of the current batch
   int buf;                         // buffer holding the current batch
   uint2 e_next;                    // this lane's entry of the next batch to stage
+  // Chained walk (the paper's early termination, which needs a pixel's whole
+  // list): the unit's list is the concatenation of the block lists of every
+  // segment of its tile, in segment order.  c_item is the segment holding
+  // entry c_cum onwards; loads come at rising positions.
+  const ItemDesc* __restrict__ items;
+  const int32_t* __restrict__ counts;
+  int block, c_item, c_cum, c_cnt, c_b0;   // c_cnt entries of segment c_item start at c_b0
 
-  __device__ __forceinline__ uint2 load(int at) const {
+  __device__ __forceinline__ uint2 load(int at) {
     const int i = at + (int)(threadIdx.x & 31);
-    return i < n ? src[i] : make_uint2(0u, 0u);
+    if (i >= n) return make_uint2(0u, 0u);
+    if constexpr (!CHAIN) {
+      return src[i];
+    } else {
+      // the segment holding `at` (warp-uniform; it moves only at segment ends)
+      while (at >= c_cum + c_cnt) {
+        c_cum += c_cnt;
+        ++c_item;
+        c_cnt = counts[c_item * kBlocksPerTile + block];
+        c_b0 = items[c_item].b0;
+      }
+      if (i < c_cum + c_cnt) return src[c_b0 + (i - c_cum)];
+      // this lane's entry lies in a later segment
+      int k = c_item + 1, cum = c_cum + c_cnt;
+      int cnt = counts[k * kBlocksPerTile + block];
+      while (i >= cum + cnt) {
+        cum += cnt;
+        ++k;
+        cnt = counts[k * kBlocksPerTile + block];
+      }
+      return src[items[k].b0 + (i - cum)];
+    }
   }
 
   // One commit group: records (and, with need_values, value records and
@@ -253,8 +281,22 @@ struct UnitStream {
     if (need_values && S.n_channels < CMAX)
       for (int e = lane; e < NB * 32 * StageBuf<CMAX, NB>::FS; e += 32) (&sb.feat[0][0])[e] = 0.0f;
     __syncwarp();
-    src = v.unit_list + (size_t)it.block * v.capacity + it.b0;
-    n = v.unit_count[it.slot];
+    if constexpr (CHAIN) {
+      // every segment of the tile, from its first
+      src = v.unit_list + (size_t)it.block * v.capacity;
+      items = v.item_desc;
+      counts = v.unit_count;
+      block = it.block;
+      c_item = it.first;
+      c_cum = 0;
+      c_cnt = counts[it.first * kBlocksPerTile + block];
+      c_b0 = items[it.first].b0;
+      n = 0;
+      for (int k = it.first; k < it.first + it.nseg; ++k) n += counts[k * kBlocksPerTile + block];
+    } else {
+      src = v.unit_list + (size_t)it.block * v.capacity + it.b0;
+      n = v.unit_count[it.slot];
+    }
     base = 0;
     buf = 0;
 #pragma unroll

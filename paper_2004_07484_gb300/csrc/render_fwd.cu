@@ -49,7 +49,9 @@
 //   k3 = zfar - (zfar - znear) (g / o_max) (m + ln den + ln(tau / (1 - tau))),
 // which only falls as hits are blended.  The pixel's list position where it
 // stopped goes to the backward pass with the tracked set.  Tiles then have a
-// single segment, as the rule needs the pixel's whole denominator.
+// chained walk: one render unit takes every segment of its tile's list in
+// order (the block lists are still built per segment), as the rule needs the
+// pixel's whole denominator.
 #include "render_common.cuh"
 
 namespace pulsar {
@@ -100,10 +102,12 @@ __device__ __forceinline__ const float* ref_feature(const SceneDev& S, int dom) 
 }
 
 // Renders work unit w (a pixel block of one work item) with one warp.
-template <int KMAX, int CMAX, bool BLEND>
+template <int KMAX, int CMAX, bool BLEND, bool CHAIN>
 __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<CMAX>& sb) {
   ItemCtx it;
   if (!item_ctx(v, w, it)) return;
+  // a chained walk renders the tile's later segments from its first
+  if (CHAIN && it.seg != 0) return;
   const SceneDev& S = v.scenes[it.scene];
   const PixelCtx pc = pixel_ctx(S, it.tile, it.block);
   const WarpRect wr = warp_rect(pc, it.block);
@@ -118,7 +122,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   const int lane = threadIdx.x;
 
   // the first batches of the block list stage while the state is set up
-  UnitStream<CMAX> ws;
+  UnitStream<CMAX, 2, CHAIN> ws;
   ws.start(sb, v, S, it, BLEND);
 
   // the background term e^{eps/g - m} belongs to the first segment only
@@ -147,7 +151,12 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   float kstop3 = pstop ? paper_bound() : __int_as_float(0x7f800000);
   int stop_pos = 0x7fffffff;
 
-  if (S.n_tests) ntest = v.unit_tests[(size_t)it.slot * 32 + lane];
+  if (S.n_tests) {
+    ntest = v.unit_tests[(size_t)it.slot * 32 + lane];
+    if (CHAIN)
+      for (int k = it.first + 1; k < it.first + it.nseg; ++k)
+        ntest += v.unit_tests[((size_t)k * kBlocksPerTile + it.block) * 32 + lane];
+  }
   for (; ws.base < ws.n; ws.advance()) {
     if (__all_sync(0xffffffffu, done)) break;
     // remaining-mass bound (ii), from the state at the start of this batch;
@@ -227,7 +236,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   }
   ws.drain();
 
-  if (it.nseg > 1) {
+  if (it.nseg > 1 && !CHAIN) {
     // leave this block's segment state, then let the block's last segment merge
     const int F = v.part_fields;
     const int q0 = kPRes + C;
@@ -361,28 +370,28 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
 
 // One CTA per work unit, or (persistent) one resident CTA per slot taking
 // units from the workspace counter.
-template <int KMAX, int CMAX, bool BLEND>
+template <int KMAX, int CMAX, bool BLEND, bool CHAIN>
 __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v, int persistent) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageBuf<CMAX>& sb = *reinterpret_cast<StageBuf<CMAX>*>(smem_raw);
   if (!persistent) {
-    traverse_unit<KMAX, CMAX, BLEND>(v, blockIdx.x, sb);
+    traverse_unit<KMAX, CMAX, BLEND, CHAIN>(v, blockIdx.x, sb);
     return;
   }
   const int n_units = v.hdr->n_items * kBlocksPerTile;
   for (;;) {
     const int w = next_unit(v);
     if (w >= n_units) break;
-    traverse_unit<KMAX, CMAX, BLEND>(v, w, sb);
+    traverse_unit<KMAX, CMAX, BLEND, CHAIN>(v, w, sb);
     __syncwarp();
   }
 }
 
-template <int KMAX, int CMAX, bool BLEND>
+template <int KMAX, int CMAX, bool BLEND, bool CHAIN = false>
 cudaError_t launch_t(const WsView& v, cudaStream_t st) {
   // staging buffers, then (blending) every lane's reference feature
   const size_t smem = sizeof(StageBuf<CMAX>) + (BLEND ? sizeof(float) * 32 * StageBuf<CMAX>::FS : 0);
-  auto kern = traverse_kernel<KMAX, CMAX, BLEND>;
+  auto kern = traverse_kernel<KMAX, CMAX, BLEND, CHAIN>;
   unsigned grid = (unsigned)v.max_items * kBlocksPerTile;
   if (v.persistent) {
     const unsigned slots = resident_slots(kern, 32, smem);
@@ -401,6 +410,13 @@ cudaError_t launch_k(const WsView& v, cudaStream_t st) {
   if constexpr (!BLEND) {
     return launch_t<KMAX, 4, false>(v, st);
   } else {
+    // the paper's early termination walks a tile's segments in order
+    if (v.chain) {
+      if (C <= 4) return launch_t<KMAX, 4, true, true>(v, st);
+      if (C <= 8) return launch_t<KMAX, 8, true, true>(v, st);
+      if (C <= 16) return launch_t<KMAX, 16, true, true>(v, st);
+      return launch_t<KMAX, 32, true, true>(v, st);
+    }
     if (C <= 4) return launch_t<KMAX, 4, true>(v, st);
     if (C <= 8) return launch_t<KMAX, 8, true>(v, st);
     if (C <= 16) return launch_t<KMAX, 16, true>(v, st);

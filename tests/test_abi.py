@@ -160,7 +160,7 @@ def test_fit_entry_points_reject_bad_arguments_on_the_host(lib):
     assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=lib.FLAG_PAPER_GRADIENTS))) > \
         L.pulsar_workspace_size(ctypes.byref(_params(lib)))   # per-sphere sums of the paper mode
     assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=lib.FLAG_ORTHOGRAPHIC))) > 0
-    # the paper's early termination keeps every tile's list whole: fewer work items
-    assert 0 < L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=lib.FLAG_PAPER_STOP))) <= \
+    # the paper's early termination keeps the workspace layout
+    assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=lib.FLAG_PAPER_STOP))) == \
         L.pulsar_workspace_size(ctypes.byref(_params(lib)))
     assert L.pulsar_workspace_size(ctypes.byref(_params(lib, flags=1 << 8))) == 0

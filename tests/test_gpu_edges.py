@@ -368,9 +368,10 @@ def _truncation_bound(exact, stop, sc):
     return 2.0 * fmax * left * t / (1.0 + left * t)
 
 
-@pytest.mark.parametrize("persistent,tau", [(False, 0.01), (True, 0.01), (False, 0.05)],
-                         ids=["items", "persistent", "5-percent"])
-def test_paper_stop_forward_matches_oracle(orc, persistent, tau):
+@pytest.mark.parametrize("persistent,tau,segment", [(False, 0.01, 0), (True, 0.01, 0), (False, 0.05, 0),
+                                                    (False, 0.01, 32), (True, 0.01, 64)],
+                         ids=["items", "persistent", "5-percent", "chain-32", "chain-64-persistent"])
+def test_paper_stop_forward_matches_oracle(orc, persistent, tau, segment):
     """The paper's early termination (App. B, Step 2): on every pixel whose
     decisions lie clear of the threshold (|ln(a / tau)| >= 1e-3 for every
     test the oracle takes; a float32 denominator can only decide otherwise
@@ -383,7 +384,7 @@ def test_paper_stop_forward_matches_oracle(orc, persistent, tau):
     sc_exact = S.Scene(**{**sc.__dict__, "paper_stop": False})
     exact = orc.render(sc_exact)
     assert (exact.n_hits > ref.n_hits).mean() > 0.01          # the option does cut lists here
-    gpu = gpu_forward(sc, persistent=persistent)
+    gpu = gpu_forward(sc, persistent=persistent, segment=segment)
     img = gpu["image"].cpu().numpy()
     clear = margin >= 1e-3
     assert clear.mean() >= 0.99
@@ -400,16 +401,22 @@ def test_paper_stop_forward_matches_oracle(orc, persistent, tau):
 def test_paper_stop_gradients_match_oracle(orc):
     """Gradients through the hits the early termination kept (the forward
     pass records where each pixel stopped); every decision of this scene lies
-    at least 2e-3 from the threshold.  Without stored hits the backward pass
+    at least 2e-3 from the threshold.  Tile lists split into 32-entry segments
+    walked in order give the same.  Without stored hits the backward pass
     reports an unsupported setting."""
     sc = _deep_cloud(86, 600, 48, 40, (0.1, 0.5))
     assert orc.paper_stop_margin(sc).min() >= 2e-3
     ref = orc.render(sc)
+    G = S.grad_image(12, sc.height, sc.width, sc.n_channels)
+    want = orc.render_backward(sc, G)
+    for segment in (32, 64):
+        gpu = gpu_forward(sc, segment=segment, persistent=segment == 64)
+        np.testing.assert_array_equal(gpu["tracked"].cpu().numpy(), ref.tracked)
+        assert np.abs(gpu["image"].cpu().numpy() - ref.image).max() <= 1e-4
+        assert_grads_close(gpu_backward(gpu, G), want, scene=sc)
     gpu = gpu_forward(sc)
     assert np.abs(gpu["image"].cpu().numpy() - ref.image).max() <= 1e-4
     np.testing.assert_array_equal(gpu["tracked"].cpu().numpy(), ref.tracked)
-    G = S.grad_image(12, sc.height, sc.width, sc.n_channels)
-    want = orc.render_backward(sc, G)
     assert_grads_close(gpu_backward(gpu, G), want, scene=sc)
     # the gradients differ from the exact renderer's (hits were left out)
     sc_exact = S.Scene(**{**sc.__dict__, "paper_stop": False})
