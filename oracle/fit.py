@@ -54,7 +54,9 @@ def view_scene(base, params: dict, cam):
     return SimpleNamespace(pos=params["pos"], rad=params["rad"], opa=params["opa"], feat=params["feat"],
                            cam=np.asarray(cam, np.float32), bg=base.bg, width=base.width, height=base.height,
                            gamma=base.gamma, n_track=base.n_track, eps=base.eps, znear=base.znear,
-                           zfar=base.zfar)
+                           zfar=base.zfar, ortho=getattr(base, "ortho", False),
+                           paper_stop=getattr(base, "paper_stop", False),
+                           min_contrib=getattr(base, "min_contrib", 0.01))
 
 
 def loss_and_grads(base, params: dict, cams, targets, kind: str = "l2", scale: float = 1.0):

@@ -243,8 +243,14 @@ def _adam_step_bound(history, name, lr, steps):
     return b
 
 
-def test_fit_steps_match_oracle_loop(orc, fit_orc):
+@pytest.mark.parametrize("paper_stop", [False, True], ids=["exact", "paper-stop"])
+def test_fit_steps_match_oracle_loop(orc, fit_orc, paper_stop):
+    """Three Adam steps of the fit against the oracle's loop; also with the
+    paper's 1 % early termination, whose decisions in these views all lie at
+    least 1.5e-2 from the threshold (it cuts the lists of 1 to 2 % of the
+    pixels)."""
     hidden, start, cams, targets = _fit_problem(orc, fit_orc)
+    start.paper_stop = paper_stop
     steps, lr = 3, 1e-3
     vf = _view_fit(start, cams, targets, lr)
     losses = []
