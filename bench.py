@@ -764,7 +764,7 @@ def main():
     fp32_nominal = N_SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     dominant = "render_fwd" if fwd_ms >= bwd_ms else "render_bwd"
     achieved = flops_fwd / (fwd_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "pulsar_render_fwd (traverse_kernel<16, 16, 1>)", "achieved": achieved,
+    roofline = {"bound": "alu", "kernel": "pulsar_render_fwd (traverse_kernel<16, 16, 1, 0>)", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "traffic": FWD_TRAFFIC["bytes"] if fwd_kernel_digest() == FWD_TRAFFIC["sha256"] else None,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
