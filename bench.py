@@ -158,6 +158,78 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def stage_work(L: int, tests: int, hits: int, tracked: int, M: int, P: int, C: int) -> dict:
+    """Algorithmic bytes and FP32 operations of every stage of one fwd + bwd
+    render, counted from the run's own pair count L, pixel tests, hits and
+    tracked hits:
+      project      read position, radius, opacity (20 B), write the draw records (48 B) per sphere;
+      depth sort   one read and one write of (key, index), 8 B each way per sphere;
+      binning      emit and sort (tile, sphere) pairs, 16 B per pair; ~30 operations per pixel test
+                   of the intersection search (block lists);
+      forward      list entries and draw records 36 B + the features 4C B per pair, the image 4C B
+                   and log D + hit count 8 B per pixel; 16 + 2C operations per blended hit;
+      backward     dL/dF and F 8C B and the per-pixel tracked threshold 16 B per pixel, draw records
+                   32 B, features 4C B and gradient writes 20 + 4C B per sphere, camera chain 28 B per
+                   sphere; 60 + 4C operations per tracked hit."""
+    return {
+        "project": (20.0 * M + 48.0 * M, 0.0),
+        "depth sort": (16.0 * M, 0.0),
+        "binning": (16.0 * L, 30.0 * tests),
+        "forward render": (36.0 * L + 4.0 * C * L + 4.0 * C * P + 8.0 * P, (16.0 + 2.0 * C) * hits),
+        "backward": (8.0 * C * P + 16.0 * P + (32.0 + 4.0 * C + 20.0 + 4.0 * C + 28.0) * M,
+                     (60.0 + 4.0 * C) * tracked),
+    }
+
+
+def step_roofline(L, tests, hits, tracked, M, P, C, K, stage_mean, ms_per_step, pk, pk_kind, fp32_tflops):
+    """The composite roofline of one render: per stage the larger of its HBM
+    time (algorithmic bytes / measured copy bandwidth) and its FP32 time
+    (operations / measured FMA rate), summed, against the measured step; and
+    the forward render (the dominant kernel) against HBM."""
+    bw = pk["hbm_gbs"] * 1e9
+    fp = fp32_tflops * 1e12
+    work = stage_work(L, tests, hits, tracked, M, P, C)
+    stages, t_roof = [], 0.0
+    for name, (b, f) in work.items():
+        tb, tf = b / bw, f / fp
+        t_roof += max(tb, tf)
+        stages.append({"stage": name, "bytes": b, "flops": f, "t_hbm_us": tb * 1e6, "t_fp32_us": tf * 1e6,
+                       "bound": "hbm" if tb >= tf else "fp32"})
+    # measured per C-ABI call (CUDA events on the launch stream, mean over the timed steps)
+    calls = {"pulsar_project": ("project",), "pulsar_bin": ("depth sort", "binning"),
+             "pulsar_render_fwd": ("forward render",), "pulsar_render_bwd": ("backward",)}
+    call_ms = {"pulsar_project": stage_mean["project"], "pulsar_bin": stage_mean["bin"],
+               "pulsar_render_fwd": stage_mean["render_fwd"], "pulsar_render_bwd": stage_mean["render_bwd"]}
+    per_call = {}
+    for call, names in calls.items():
+        b = sum(work[n][0] for n in names)
+        f = sum(work[n][1] for n in names)
+        tr = sum(max(work[n][0] / bw, work[n][1] / fp) for n in names)
+        ms = call_ms[call]
+        per_call[call] = {"ms": ms, "t_roof_us": tr * 1e6, "frac": tr / (ms * 1e-3),
+                          "hbm_frac": b / (ms * 1e-3) / bw, "fp32_frac": f / (ms * 1e-3) / fp}
+    fb, ff = work["forward render"]
+    fwd_s = stage_mean["render_fwd"] * 1e-3
+    achieved = fb / fwd_s / 1e9
+    traffic = FWD_TRAFFIC["bytes"] if fwd_kernel_digest() == FWD_TRAFFIC["sha256"] else None
+    return {"bound": "hbm", "kernel": "pulsar_render_fwd (forward render: set-up and render kernel; the "
+                                      "background pass overlaps on a side stream)",
+            "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+            "peak_kind": f"{pk_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if pk_kind == "measured"
+                         else "fallback copy bandwidth",
+            "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write), null when the "
+                                                "kernel changed since the capture",
+            "algorithmic_bytes_per_launch": fb, "fp32": {"achieved_tflops": ff / fwd_s / 1e12,
+                                                         "peak_tflops": fp32_tflops,
+                                                         "frac": ff / fwd_s / fp,
+                                                         "peak_kind": "measured in this run (FMA probe)"},
+            "step": {"t_roof_us": t_roof * 1e6, "ms_per_step": ms_per_step,
+                     "frac": t_roof / (ms_per_step * 1e-3)},
+            "per_call": per_call, "stages": stages,
+            "counts": {"pairs": L, "pixel_tests": tests, "hits": hits, "tracked_hits": tracked, "spheres": M,
+                       "pixels": P, "channels": C, "n_track": K}}
+
+
 def make_scene(rank: int, n: int | None = None, res: int | None = None, config: int = 2):
     from paper_2004_07484_gb300 import scenes
     if config != 2:
@@ -168,21 +240,41 @@ def make_scene(rank: int, n: int | None = None, res: int | None = None, config: 
                                      n_channels=16, gamma=1e-2, n_track=16)
 
 
-def cpu_oracle_sample(sc, n_side: int):
-    """Oracle fwd + bwd on an n_side x n_side pixel window of the workload.
-    Returns (seconds, fraction of one render the window covers)."""
+# pixels on a side of the oracle's timed window, the same in both arms
+CPU_WINDOW = 128
+
+
+def _oracle_window_s(sc, n_side: int) -> float:
+    """Seconds of one oracle fwd + bwd on the n_side x n_side window at the
+    image centre: the forward at the window's pixels, the backward with dL/dF
+    given on the window only (n_side = 0: the calls' fixed set-up alone)."""
     from oracle import oracle
     from paper_2004_07484_gb300 import scenes
-    oracle.build()
-    n_side = min(n_side, sc.width, sc.height)
     v0, u0 = (sc.height - n_side) // 2, (sc.width - n_side) // 2
-    pix = [(u, v) for v in range(v0, v0 + n_side) for u in range(u0, u0 + n_side)]
-    G = np.zeros((sc.height, sc.width, sc.n_channels))
-    G[v0:v0 + n_side, u0:u0 + n_side] = scenes.grad_image(5, n_side, n_side, sc.n_channels)
+    pix = np.array([(u, v) for v in range(v0, v0 + n_side) for u in range(u0, u0 + n_side)],
+                   np.int32).reshape(-1, 2)
+    G = scenes.grad_image(5, n_side, n_side, sc.n_channels) if n_side else np.zeros((0, 0, sc.n_channels))
     t0 = time.perf_counter()
     oracle.render_pixels(sc, pix)
-    oracle.render_backward(sc, G)
-    dt = time.perf_counter() - t0
+    oracle.render_backward_window(sc, G, u0, v0)
+    return time.perf_counter() - t0
+
+
+def oracle_setup_s(sc) -> float:
+    """The oracle calls' set-up that does not grow with the window (projection
+    of every sphere, float64 copies of the inputs and gradient arrays): the
+    fastest of three empty-window runs."""
+    from oracle import oracle
+    oracle.build()
+    return min(_oracle_window_s(sc, 0) for _ in range(3))
+
+
+def cpu_oracle_sample(sc, n_side: int, setup_s: float):
+    """Oracle fwd + bwd on an n_side x n_side pixel window of the workload,
+    with the fixed set-up (setup_s) subtracted.  Returns (seconds of windowed
+    work, fraction of one render the window covers)."""
+    n_side = min(n_side, sc.width, sc.height)
+    dt = max(_oracle_window_s(sc, n_side) - setup_s, 1e-9)
     return dt, (n_side * n_side) / float(sc.width * sc.height)
 
 
@@ -198,15 +290,18 @@ def run_reference(args):
     if rank != 0:
         return
     sc = make_scene(0)
-    n_side = 8
+    n_side = CPU_WINDOW
+    setup = oracle_setup_s(sc)
     tot, frac = 0.0, 0.0
     for _ in range(args.warmup):
-        cpu_oracle_sample(sc, n_side)
+        cpu_oracle_sample(sc, n_side, setup)
     for _ in range(args.steps):
-        dt, f = cpu_oracle_sample(sc, n_side)
+        dt, f = cpu_oracle_sample(sc, n_side, setup)
         tot += dt
         frac += f
     value = frac / tot
+    sample = (f"{n_side}x{n_side}-pixel window at the image centre per step, fwd + bwd, FP64 brute force over "
+              f"all {sc.n_spheres} spheres; the calls' fixed set-up ({setup:.3f} s, an empty window) subtracted")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -214,7 +309,7 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "renders_per_step": 1,
                        "parallelism": "replicas x1 (independent renders)", "hit_lists": "store"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-                             "sample": f"{n_side}x{n_side}-pixel window per step, fwd + bwd, FP64 brute force"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -244,10 +339,14 @@ def bench_batched(dev, steps: int, warmup: int, flush):
     t_tune = time.perf_counter() - t_tune
     tuned = autotune.apply(sets, choice)
     caps = choice.capacities
+    # the plain arm: every scene with its own autotuned scheduling and capacity
+    own = [autotune.tune([s], [x], [G]) for s, x, G in zip(sets, inputs, grads)]
+    plain_sets = [autotune.apply([s], c)[0] for s, c in zip(sets, own)]
+    plain_caps = [c.capacities[0] for c in own]
     stream = torch.cuda.current_stream(dev)
 
     def plain_step():
-        for s, x, G, c in zip(sets, inputs, grads, caps):
+        for s, x, G, c in zip(plain_sets, inputs, grads, plain_caps):
             fr, image, log_norm = forward_frame(s, *x, c, check_overflow=False)
             backward_frame(fr, *x, image, log_norm, G)
 
@@ -293,7 +392,11 @@ def bench_batched(dev, steps: int, warmup: int, flush):
             "autotune": {"segment": choice.segment, "persistent": choice.persistent,
                          "candidates_ms": {f"{a}/{'persistent' if b else 'per-unit'}": v
                                            for (a, b), v in choice.ms.items()},
-                         "seconds": t_tune},
+                         "seconds": t_tune,
+                         "plain": "each scene's calls with its own autotuned segment, kernel form and "
+                                  "capacity (tuned as a batch of one)",
+                         "plain_choices": sorted({f"{c.segment}/{'persistent' if c.persistent else 'per-unit'}"
+                                                  for c in own})},
             "launches_per_step": {"plain": 32 * n, "batched": 32, "graph": 1},
             "steps": k, "l2": "flushed between steps (256 MB write, untimed)"}
 
@@ -486,10 +589,12 @@ def bench_fit(args):
     if not args.no_cpu_baseline:
         sc_view = scenes.Scene(start.pos, start.rad, start.opa, start.feat, cams[0], start.bg, W, H, start.gamma,
                                start.n_track)
-        dt, frac = cpu_oracle_sample(sc_view, 16)
+        setup = oracle_setup_s(sc_view)
+        dt, frac = cpu_oracle_sample(sc_view, 48, setup)
         cpu = {"value": frac / dt / V, "unit": "steps/s", "cores": host_cores(), "kind": "oracle",
-               "sample": f"16x16-pixel window of one view, fwd + bwd, FP64 brute force over all "
-                         f"{start.n_spheres} spheres, scaled to 4 whole views per step (Adam not timed)"}
+               "sample": f"48x48-pixel window of one view, fwd + bwd, FP64 brute force over all "
+                         f"{start.n_spheres} spheres, the calls' fixed set-up ({setup:.3f} s) subtracted, "
+                         f"scaled to 4 whole views per step (Adam not timed)"}
     n_val = V * H * W * C
     line = {"metric": FIT_METRIC, "value": world * args.steps / (fit_ms * 1e-3), "unit": "steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": fit_ms / args.steps,
@@ -598,34 +703,54 @@ def main():
     torch.cuda.synchronize()
     hits = int(n_hits.sum().item())
     tests = int(n_tests.sum().item())
+    tracked_hits = int(n_hits.clamp(max=sc.n_track).sum().item())   # min(hits, n_track) per pixel
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB of L2
 
-    fwd_ev, bwd_ev = [], []
+    from paper_2004_07484_gb300.renderer import Frame, scene_args
 
-    def step(store: bool, timed_kernels: bool, paper_stop: bool = False):
+    def step(store: bool, marks=None, paper_stop: bool = False):
+        """One pass of the hot path through the C ABI; marks (three events), when
+        given, are recorded after project, bin and the forward render."""
         s = settings(store, paper_stop)
-        fr, image, log_norm = forward_frame(s, t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"],
-                                            capacity, check_overflow=False)
+        fr = Frame(s, sc.n_spheres, capacity, dev)
+        sa = scene_args(t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"])
+        _lib.project(fr.params, sa, fr.ws.data_ptr(), fr.ws_bytes, stream.cuda_stream)
+        if marks:
+            marks[0].record(stream)
+        _lib.bin(fr.params, fr.ws.data_ptr(), fr.ws_bytes, stream.cuda_stream)
+        if marks:
+            marks[1].record(stream)
+        image = torch.empty((H, W, C), dtype=torch.float32, device=dev)
+        log_norm = torch.empty((H, W), dtype=torch.float32, device=dev)
+        _lib.render_fwd(fr.params, sa, fr.ws.data_ptr(), fr.ws_bytes, image.data_ptr(), log_norm.data_ptr(),
+                        None, None, None, stream.cuda_stream)
+        if marks:
+            marks[2].record(stream)
         grads = backward_frame(fr, t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"], image,
                                log_norm, G)
         return fr, image, grads
 
-    def timed_steps(store: bool, k: int, paper_stop: bool = False):
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+    stage_ms = {"project": [], "bin": [], "render_fwd": [], "render_bwd": []}
+
+    def timed_steps(store: bool, k: int, paper_stop: bool = False, record_stages: bool = False):
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(k)]
         for i in range(k):
             flush.fill_(i & 0xff)
-            starts[i].record(stream)
-            fr, image, grads = step(store, True, paper_stop)
-            ends[i].record(stream)
+            ev[i][0].record(stream)
+            fr, image, grads = step(store, ev[i][1:4], paper_stop)
+            ev[i][4].record(stream)
         torch.cuda.synchronize()
-        return [s.elapsed_time(e) for s, e in zip(starts, ends)], fr
+        if record_stages:
+            for e in ev:
+                for name, a, b in (("project", 0, 1), ("bin", 1, 2), ("render_fwd", 2, 3), ("render_bwd", 3, 4)):
+                    stage_ms[name].append(e[a].elapsed_time(e[b]))
+        return [e[0].elapsed_time(e[4]) for e in ev], fr
 
     for _ in range(max(args.warmup, 3)):
-        step(True, False)
-        step(False, False)
-        step(True, False, True)
+        step(True)
+        step(False)
+        step(True, None, True)
     torch.cuda.synchronize()
     if args.profile_step and args.profile_batch > 0:
         if rank == 0:
@@ -633,7 +758,7 @@ def main():
         return
     if args.profile_step:
         torch.cuda.nvtx.range_push("pulsar_step")
-        step(not args.recompute, True)
+        step(not args.recompute)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if rank == 0:
@@ -646,7 +771,7 @@ def main():
     gc.disable()   # no collector pauses between the timed launches
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
-        ms_store, fr_last = timed_steps(not args.recompute, args.steps)
+        ms_store, fr_last = timed_steps(not args.recompute, args.steps, record_stages=True)
         ms_rec, _ = timed_steps(args.recompute, max(3, args.steps // 2))
         # the paper's default early termination (an approximation), for comparison
         ms_ps, _ = timed_steps(True, max(3, args.steps // 2), True)
@@ -662,33 +787,7 @@ def main():
     ms_sorted = sorted(ms_store)
     value = job_throughput(world, args.steps, total_ms)
 
-    # per-kernel timing of the dominant kernels (events on the launch stream)
-    def kernel_ms(store: bool, reps: int = 5):
-        s = settings(store)
-        fwd, bwd = [], []
-        for i in range(reps):
-            fr = None
-            flush.fill_(i & 0xff)
-            from paper_2004_07484_gb300.renderer import Frame, scene_args
-            fr = Frame(s, sc.n_spheres, capacity, dev)
-            sa = scene_args(t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"])
-            _lib.project(fr.params, sa, fr.ws.data_ptr(), fr.ws_bytes, stream.cuda_stream)
-            _lib.bin(fr.params, fr.ws.data_ptr(), fr.ws_bytes, stream.cuda_stream)
-            image = torch.empty((H, W, C), dtype=torch.float32, device=dev)
-            log_norm = torch.empty((H, W), dtype=torch.float32, device=dev)
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record(stream)
-            _lib.render_fwd(fr.params, sa, fr.ws.data_ptr(), fr.ws_bytes, image.data_ptr(),
-                            log_norm.data_ptr(), None, None, None, stream.cuda_stream)
-            e1.record(stream)
-            backward_frame(fr, t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"], image, log_norm, G)
-            e2.record(stream)
-            torch.cuda.synchronize()
-            fwd.append(e0.elapsed_time(e1))
-            bwd.append(e1.elapsed_time(e2))
-        return statistics.median(fwd), statistics.median(bwd)
-
-    fwd_ms, bwd_ms = kernel_ms(not args.recompute)
+    stage_mean = {k: statistics.mean(v) for k, v in stage_ms.items()}
     sink = torch.zeros(1, device=dev)
     fp32_peak = _lib.probe_fma_throughput(sink.data_ptr(), 8192, stream.cuda_stream)[0] / 1e12
 
@@ -755,37 +854,24 @@ def main():
 
     pk, pk_kind = peaks()
     clocks = clk.summary()
-    # ALU roofline of the dominant kernel: algorithmic FP32 operations of the
-    # forward render, 21 + 2C per hit (depth, distance term, depth term,
-    # exponent, weight, C-channel update), with the hit count from the
-    # kernel's own per-pixel counter.  The ray-sphere tests (14 operations
-    # each) are made by the block-list pass of binning, not by this kernel.
-    flops_fwd = (21.0 + 2.0 * C) * hits
-    fp32_nominal = N_SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    dominant = "render_fwd" if fwd_ms >= bwd_ms else "render_bwd"
-    achieved = flops_fwd / (fwd_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "pulsar_render_fwd (traverse_kernel<16, 16, 1, 0>)", "achieved": achieved,
-                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "traffic": FWD_TRAFFIC["bytes"] if fwd_kernel_digest() == FWD_TRAFFIC["sha256"] else None,
-                "traffic_unit": "bytes per launch (ncu dram read + write)",
-                "algorithmic_flops_per_launch": flops_fwd,
-                "peak_kind": "measured in this run: FP32 FMA throughput probe (pulsar_probe_fma_throughput, "
-                             "8 independent chains per thread, 64 warps per SM)",
-                "peak_nominal": fp32_nominal,
-                "peak_nominal_kind": f"{N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x max SM clock "
-                                     f"({pk.get('sm_max_mhz', 2070.0)} MHz, {pk_kind})",
-                "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "dominant": dominant,
-                "ray_tests": tests, "hits": hits, "pairs": pairs_needed}
+    roofline = step_roofline(pairs_needed, tests, hits, tracked_hits, sc.n_spheres, H * W, C, sc.n_track,
+                             stage_mean, ms_per_step, pk, pk_kind, fp32_peak)
     batched = None if args.no_batched else bench_batched(dev, args.steps, args.warmup, flush)
     batched_headline = None
     if not args.no_batched and args.config == 2 and args.spheres is None and args.res is None:
         batched_headline = bench_batched_headline(dev, args.steps, args.warmup, flush)
+        # the headline comparison of the batched form: the same workload's plain single render
+        batched_headline["plain_renders_per_s"] = value
+        batched_headline["speedup_batched_vs_plain"] = batched_headline["batched_renders_per_s"] / value
+        batched_headline["speedup_graph_vs_plain"] = batched_headline["graph_renders_per_s"] / value
     cpu = None
     if not args.no_cpu_baseline:
-        dt, frac = cpu_oracle_sample(sc, 16)
+        setup = oracle_setup_s(sc)
+        dt, frac = cpu_oracle_sample(sc, CPU_WINDOW, setup)
         cpu = {"value": frac / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-               "sample": f"16x16-pixel window at the image centre, fwd + bwd, FP64 brute force over all "
-                         f"{sc.n_spheres} spheres"}
+               "sample": f"{CPU_WINDOW}x{CPU_WINDOW}-pixel window at the image centre, fwd + bwd, FP64 brute "
+                         f"force over all {sc.n_spheres} spheres; the calls' fixed set-up ({setup:.3f} s, "
+                         f"an empty window) subtracted"}
     # kernels per step: project 2 (setup, project); binning 24 (four 8-bit radix
     # passes of the 32-bit depth keys and two of the 12-bit tile keys, 3 kernels
     # each, then count, scan, emit, ranges, items, block lists); forward 3

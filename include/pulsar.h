@@ -243,18 +243,25 @@ pulsar_status pulsar_last_overflow(const pulsar_params* params, void* workspace,
  *   Runs pulsar_project, pulsar_bin and pulsar_render_fwd with a 64 MiB
  *   device array inside the library as the workspace.  Inputs and outputs
  *   are the caller's, as for pulsar_render_fwd.
- *   Returns PULSAR_ERR_CAPACITY, before enqueuing anything, when
+ *   Validates params exactly as pulsar_render_fwd does (same status codes),
+ *   then returns PULSAR_ERR_CAPACITY, before enqueuing anything, when
  *   pulsar_workspace_size(params) exceeds PULSAR_STATIC_WORKSPACE_BYTES.
  *   The array is shared by every call in the process and keeps the last
  *   call's contents; calls that overlap on the GPU (other streams, other
  *   threads) race on it and must be serialised by the caller.
  *   Its device address is looked up once per device, by the first call made
  *   with that device current; make that first call before any stream
- *   capture.  A list_capacity overflow cannot be read back through this
- *   entry point: choose list_capacity so it cannot overflow (n_spheres times
- *   the number of tiles is always enough). */
+ *   capture.  The address is stale after cudaDeviceReset of that device.
+ *   A list_capacity overflow (the image is then background only) is read
+ *   back with pulsar_static_read_status. */
 pulsar_status pulsar_render_fwd_static(const pulsar_params* params, const pulsar_scene* scene,
                                        float* image, float* log_norm, void* stream);
+
+/* Status of the last pulsar_render_fwd_static call on the current device, as
+ * pulsar_read_status reports it for a caller workspace: PULSAR_OK, or
+ * PULSAR_ERR_CAPACITY after a list_capacity overflow, with the pair count the
+ * call needed in *pairs_needed (may be NULL).  Synchronises the stream. */
+pulsar_status pulsar_static_read_status(int64_t* pairs_needed, void* stream);
 
 /* ------------------------------------------------------------------------
  * Batched rendering: several independent scenes (each with its own sphere

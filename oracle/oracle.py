@@ -64,6 +64,10 @@ def lib():
         L.orc_render_bwd.argtypes = [P(OrcParams), P(d), P(d), P(d), P(d), P(d), P(d), P(d),
                                      P(d), P(d), P(d), P(d), P(d), P(d)]
         L.orc_render_bwd.restype = None
+        L.orc_render_bwd_window.argtypes = [P(OrcParams), P(d), P(d), P(d), P(d), P(d), P(d), P(d),
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            P(d), P(d), P(d), P(d), P(d), P(d)]
+        L.orc_render_bwd_window.restype = None
         L.orc_paper_stop_margin.argtypes = [P(OrcParams), P(d), P(d), P(d), P(d), P(d)]
         L.orc_paper_stop_margin.restype = None
         L.orc_rows.argtypes = [P(d), P(d)]
@@ -228,6 +232,25 @@ def render_backward(scene, grad: np.ndarray, n_track: int | None = None, min_siz
     lib().orc_render_bwd(ctypes.byref(p), *[_ptr(a, D) for a in arrs], _ptr(G, D),
                          _ptr(out.pos, D), _ptr(out.rad, D), _ptr(out.opa, D), _ptr(out.feat, D),
                          _ptr(out.cam, D), _ptr(out.bg, D))
+    return out
+
+
+def render_backward_window(scene, grad: np.ndarray, u0: int, v0: int, n_track: int | None = None,
+                           min_size: bool = True, dist_literal: bool = False) -> Gradients:
+    """render_backward with dL/dF given on the window of grad's shape at
+    (u0, v0) and zero elsewhere (not with the paper's normalisations)."""
+    p = params(scene, n_track=n_track, min_size=min_size, dist_literal=dist_literal)
+    M, C = p.n_spheres, p.n_channels
+    G = _d(grad)
+    wh, ww = G.shape[0], G.shape[1]
+    assert G.shape[2] == C and 0 <= u0 and u0 + ww <= p.width and 0 <= v0 and v0 + wh <= p.height
+    arrs = _scene_arrays(scene)
+    out = Gradients(np.zeros((M, 3)), np.zeros(M), np.zeros(M), np.zeros((M, C)), np.zeros(11),
+                    np.zeros(C))
+    D = ctypes.c_double
+    lib().orc_render_bwd_window(ctypes.byref(p), *[_ptr(a, D) for a in arrs], _ptr(G, D), int(u0), int(v0),
+                                int(ww), int(wh), _ptr(out.pos, D), _ptr(out.rad, D), _ptr(out.opa, D),
+                                _ptr(out.feat, D), _ptr(out.cam, D), _ptr(out.bg, D))
     return out
 
 

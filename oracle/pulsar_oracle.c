@@ -531,26 +531,49 @@ int64_t orc_tile_lists(const orc_params* P, const float* key, const int32_t* rec
                        int64_t* offsets, int32_t* ids, int64_t capacity) {
   int T = P->tile, M = P->n_spheres;
   int ntx = (P->width + T - 1) / T, nty = (P->height + T - 1) / T;
+  int nt = ntx * nty;
   int* order = (int*)malloc(sizeof(int) * (size_t)(M > 0 ? M : 1));
   int nv = 0;
   for (int i = 0; i < M; ++i)
     if (rect[4 * i] >= 0) order[nv++] = i;
   g_sort_keys = key;
   qsort(order, (size_t)nv, sizeof(int), key_cmp);
+  /* tiles are independent: first every tile's length, then (after the
+   * prefix sum) every tile's entries, both by scanning the sorted spheres */
+  int64_t* len = (int64_t*)calloc((size_t)(nt > 0 ? nt : 1), sizeof(int64_t));
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int t = 0; t < nt; ++t) {
+    int tx = t % ntx, ty = t / ntx;
+    int ux0 = tx * T, ux1 = tx * T + T - 1, vy0 = ty * T, vy1 = ty * T + T - 1;
+    int64_t n = 0;
+    for (int k = 0; k < nv; ++k) {
+      const int32_t* q = rect + 4 * order[k];
+      if (q[1] < ux0 || q[0] > ux1 || q[3] < vy0 || q[2] > vy1) continue;
+      ++n;
+    }
+    len[t] = n;
+  }
   int64_t total = 0;
-  for (int ty = 0; ty < nty; ++ty)
-    for (int tx = 0; tx < ntx; ++tx) {
-      offsets[ty * ntx + tx] = total;
+  for (int t = 0; t < nt; ++t) {
+    offsets[t] = total;
+    total += len[t];
+  }
+  offsets[nt] = total;
+  if (total <= capacity) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int t = 0; t < nt; ++t) {
+      int tx = t % ntx, ty = t / ntx;
       int ux0 = tx * T, ux1 = tx * T + T - 1, vy0 = ty * T, vy1 = ty * T + T - 1;
+      int64_t o = offsets[t];
       for (int k = 0; k < nv; ++k) {
         int i = order[k];
         const int32_t* q = rect + 4 * i;
         if (q[1] < ux0 || q[0] > ux1 || q[3] < vy0 || q[2] > vy1) continue;
-        if (total < capacity) ids[total] = i;
-        ++total;
+        ids[o++] = i;
       }
     }
-  offsets[ntx * nty] = total;
+  }
+  free(len);
   free(order);
   return total > capacity ? -1 : total;
 }
@@ -621,10 +644,15 @@ void orc_paper_stop_margin(const orc_params* P, const double* pos, const double*
  * Gradients flow through each pixel's tracked hits only (App. B).
  * Outputs (all accumulated from zero here): g_pos M x 3, g_rad M, g_opa M,
  * g_feat M x C, g_cam 11 (same order as cam), g_bg C. */
-void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
-                    const double* opa, const double* feat, const double* cam, const double* bg,
-                    const double* grad, double* g_pos, double* g_rad, double* g_opa,
-                    double* g_feat, double* g_cam, double* g_bg) {
+/* The backward pass over the pixels of the window [u0, u0 + ww) x [v0, v0 + wh);
+ * grad holds dL/dF of the window's pixels (row-major, ww x wh x C), and dL/dF
+ * is zero everywhere else.  Without the paper's normalisations, pixels with
+ * zero dL/dF contribute nothing, so this equals the full-image pass with that
+ * dL/dF. */
+static void render_bwd_window(const orc_params* P, const double* pos, const double* rad,
+                              const double* opa, const double* feat, const double* cam, const double* bg,
+                              const double* grad, int u0, int v0, int ww, int wh, double* g_pos,
+                              double* g_rad, double* g_opa, double* g_feat, double* g_cam, double* g_bg) {
   ctx_t C;
   memset(&C, 0, sizeof(C));
   C.pos = pos; C.rad = rad; C.opa = opa; C.feat = feat; C.cam = cam; C.bg = bg;
@@ -649,9 +677,9 @@ void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
     double gk_local = 0.0;
     double* gbg_local = (double*)calloc((size_t)(Cn > 0 ? Cn : 1), sizeof(double));
 #pragma omp for schedule(dynamic, 1)
-    for (int v = 0; v < H; ++v)
-      for (int u = 0; u < W; ++u) {
-        size_t px = (size_t)v * W + u;
+    for (int v = v0; v < v0 + wh; ++v)
+      for (int u = u0; u < u0 + ww; ++u) {
+        size_t px = (size_t)(v - v0) * ww + (u - u0);
         const double* G = grad + px * Cn;
         int nz = 0;
         for (int c = 0; c < Cn; ++c) nz |= G[c] != 0.0;
@@ -803,6 +831,25 @@ void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
   free(gc);
   free(n_px);
   ctx_free(&C);
+}
+
+void orc_render_bwd(const orc_params* P, const double* pos, const double* rad,
+                    const double* opa, const double* feat, const double* cam, const double* bg,
+                    const double* grad, double* g_pos, double* g_rad, double* g_opa,
+                    double* g_feat, double* g_cam, double* g_bg) {
+  render_bwd_window(P, pos, rad, opa, feat, cam, bg, grad, 0, 0, P->width, P->height, g_pos, g_rad,
+                    g_opa, g_feat, g_cam, g_bg);
+}
+
+/* The backward pass with dL/dF given on a window only (zero elsewhere; not
+ * with the paper's normalisations, which count every pixel's tracked hits). */
+void orc_render_bwd_window(const orc_params* P, const double* pos, const double* rad,
+                           const double* opa, const double* feat, const double* cam, const double* bg,
+                           const double* grad, int u0, int v0, int ww, int wh, double* g_pos,
+                           double* g_rad, double* g_opa, double* g_feat, double* g_cam, double* g_bg) {
+  if (P->paper_grad) return;
+  render_bwd_window(P, pos, rad, opa, feat, cam, bg, grad, u0, v0, ww, wh, g_pos, g_rad, g_opa,
+                    g_feat, g_cam, g_bg);
 }
 
 /* Rotation rows in double (for tests of the camera model). */

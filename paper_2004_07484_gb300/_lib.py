@@ -28,7 +28,7 @@ GRAD_ALL = 63
 
 EXPORTED = ("pulsar_workspace_size", "pulsar_project", "pulsar_bin", "pulsar_render_fwd",
             "pulsar_render_bwd", "pulsar_read_tile_lists", "pulsar_read_status",
-            "pulsar_status_string", "pulsar_render_fwd_static", "pulsar_workspace_size_batched",
+            "pulsar_status_string", "pulsar_render_fwd_static", "pulsar_static_read_status", "pulsar_workspace_size_batched",
             "pulsar_project_batched", "pulsar_bin_batched", "pulsar_render_fwd_batched",
             "pulsar_render_bwd_batched", "pulsar_read_tile_lists_batched",
             "pulsar_probe_fma_throughput", "pulsar_last_overflow", "pulsar_render_batched",
@@ -116,6 +116,8 @@ def lib():
         L.pulsar_status_string.restype = ctypes.c_char_p
         L.pulsar_render_fwd_static.argtypes = [P, S, vp, vp, vp]
         L.pulsar_render_fwd_static.restype = ctypes.c_int
+        L.pulsar_static_read_status.argtypes = [ctypes.POINTER(ctypes.c_int64), vp]
+        L.pulsar_static_read_status.restype = ctypes.c_int
         i32 = ctypes.c_int
         L.pulsar_workspace_size_batched.argtypes = [i32, P]
         L.pulsar_workspace_size_batched.restype = sz
@@ -162,6 +164,13 @@ def render_fwd_static(p: Params, s: SceneArgs, image: int, log_norm: int, stream
     """Forward render using the library's fixed device array as workspace (no allocation)."""
     _check(lib().pulsar_render_fwd_static(ctypes.byref(p), ctypes.byref(s), image, log_norm, stream),
            "pulsar_render_fwd_static")
+
+
+def static_read_status(stream: int) -> tuple[int, int]:
+    """(status, pairs_needed) of the last render_fwd_static call; synchronises the stream."""
+    need = ctypes.c_int64(0)
+    st = lib().pulsar_static_read_status(ctypes.byref(need), stream)
+    return int(st), int(need.value)
 
 
 def status_string(status: int) -> str:

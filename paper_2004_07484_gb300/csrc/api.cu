@@ -457,6 +457,9 @@ pulsar_status read_lists_n(int n, const pulsar_params* params, void* ws, size_t 
 }
 
 }  // namespace
+
+pulsar_status validate_params(const pulsar_params* p) { return validate_batch(1, p); }
+
 }  // namespace pulsar
 
 using namespace pulsar;

@@ -457,6 +457,10 @@ __device__ __forceinline__ float warp_sum(float v) {
 // host-side launch helpers (defined in the .cu files)
 // ----------------------------------------------------------------------------
 
+// Host-side validation of one scene's parameters (the checks every
+// single-scene entry point makes first).
+pulsar_status validate_params(const pulsar_params* p);
+
 cudaError_t launch_setup(const WsView& v, const SceneDev* host_scenes, int n, cudaStream_t st);
 cudaError_t launch_project(const WsView& v, cudaStream_t st);
 cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st);

@@ -11,7 +11,9 @@
 // Set-up: the array's device address is looked up with cudaGetSymbolAddress
 // once per device, on the first call made while that device is current.  In
 // host code the array's name is only a host-side stand-in, so the kernels are
-// always given the looked-up address.
+// always given the looked-up address.  The address belongs to the device's
+// context: after cudaDeviceReset it is stale, so a process that resets a
+// device must not call these entry points on it again.
 #include <mutex>
 
 #include "pulsar_internal.cuh"
@@ -51,8 +53,10 @@ using namespace pulsar;
 extern "C" pulsar_status pulsar_render_fwd_static(const pulsar_params* params,
                                                   const pulsar_scene* scene, float* image,
                                                   float* log_norm, void* stream) {
+  // the same validation, in the same order, as pulsar_render_fwd
+  const pulsar_status valid = validate_params(params);
+  if (valid != PULSAR_OK) return valid;
   const size_t need = pulsar_workspace_size(params);
-  if (need == 0) return PULSAR_ERR_INVALID_ARG;
   if (need > (size_t)PULSAR_STATIC_WORKSPACE_BYTES) return PULSAR_ERR_CAPACITY;
   if (!scene || !image || !log_norm) return PULSAR_ERR_INVALID_ARG;
   void* ws = nullptr;
@@ -67,4 +71,10 @@ extern "C" pulsar_status pulsar_render_fwd_static(const pulsar_params* params,
     st = pulsar_render_fwd(params, scene, ws, PULSAR_STATIC_WORKSPACE_BYTES, image, log_norm,
                            nullptr, nullptr, nullptr, stream);
   return st;
+}
+
+extern "C" pulsar_status pulsar_static_read_status(int64_t* pairs_needed, void* stream) {
+  void* ws = nullptr;
+  if (static_ws_address(&ws) != cudaSuccess) return PULSAR_ERR_CUDA;
+  return pulsar_read_status(ws, PULSAR_STATIC_WORKSPACE_BYTES, pairs_needed, stream);
 }

@@ -183,6 +183,22 @@ def test_32_scene_batch_sampled(orc):
     scenes, and gradient sums over every scene."""
     scs = S.batch_scenes(1003)
     out = run_batch(scs, capacities=[max(6 * sc.n_spheres, 1 << 14) for sc in scs])
+    # every scene's tile lists bit-exact: the batch has tens of thousands of
+    # tiles, so the tile-key sort takes two digit passes
+    ranges, ids = batch_tile_lists(out["frame"])
+    assert len(ranges) > 256
+    t0 = m0 = 0
+    for sc in scs:
+        off, oids = orc.tile_lists(sc, tile=16)
+        nt = len(off) - 1
+        b, e = ranges[t0:t0 + nt, 0], ranges[t0:t0 + nt, 1]
+        assert np.array_equal(e - b, np.diff(off)), sc.name
+        nz = e > b
+        got = np.concatenate([ids[x:y] for x, y in zip(b[nz], e[nz])]) - m0 if nz.any() else ids[:0]
+        np.testing.assert_array_equal(got, oids, err_msg=sc.name)
+        t0 += nt
+        m0 += sc.n_spheres
+    assert t0 == len(ranges)
     g = np.random.default_rng(3)
     picks = sorted(g.choice(len(scs), 4, replace=False))
     for k in picks:

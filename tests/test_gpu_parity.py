@@ -112,6 +112,19 @@ def test_tile_lists_bit_exact(orc, cache, variant):
     assert_tile_lists_equal(ranges, ids, off, oids)
 
 
+@pytest.mark.parametrize("config", [1, 2], ids=["100k_spheres_512", "1M_spheres_1024"])
+def test_tile_lists_bit_exact_full_size(orc, config):
+    """Every tile's list of the full-size workloads (1,024 and 4,096 tiles, so
+    the tile-key sort takes more than one digit pass) equals the oracle's
+    by-definition lists (App. B, Step 1)."""
+    sc = S.config_scene(config)
+    gpu = gpu_forward(sc, capacity=16 << 20)
+    ranges, ids = gpu_tile_lists(gpu["frame"])
+    off, oids = orc.tile_lists(sc, tile=16)
+    assert len(oids) > 100_000
+    assert_tile_lists_equal(ranges, ids, off, oids)
+
+
 @pytest.mark.parametrize("variant", VARIANTS, ids=_id)
 def test_forward_matches_oracle(orc, cache, variant):
     sc, ref, gpu, okw = run_pair(orc, cache, *variant)

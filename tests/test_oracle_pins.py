@@ -620,3 +620,19 @@ def test_paper_stop_error_is_bounded_by_the_remaining_hits(orc):
     err = np.abs(exact.image - stop.image).max(axis=2)
     assert np.all(err <= bound + 1e-12)
     assert np.all(err[left == 0] <= 1e-12)
+
+
+def test_windowed_backward_equals_full_image_with_zero_outside(orc):
+    """The windowed backward (the CPU baseline's timed unit) is the full-image
+    backward whose dL/dF is zero outside the window."""
+    sc = config_scene(0)
+    g = np.random.default_rng(8)
+    u0, v0, ww, wh = 20, 26, 13, 9
+    Gw = g.standard_normal((wh, ww, sc.n_channels))
+    G = np.zeros((sc.height, sc.width, sc.n_channels))
+    G[v0:v0 + wh, u0:u0 + ww] = Gw
+    full = orc.render_backward(sc, G)
+    win = orc.render_backward_window(sc, Gw, u0, v0)
+    for k in ("pos", "rad", "opa", "feat", "cam", "bg"):
+        a, b = getattr(full, k), getattr(win, k)
+        assert np.abs(a - b).max() <= 1e-12 * max(1.0, np.abs(a).max()), k
