@@ -467,6 +467,84 @@ def bench_batched_headline(dev, steps: int, warmup: int, flush, n_renders: int =
             "l2": "flushed between steps (256 MB write, untimed)"}
 
 
+def shading_net(dev, channels: int, seed: int = 2):
+    """The 3-layer 3x3 conv shading net of the 1M-sphere workload (channels ->
+    32 -> 32 -> 3, ReLU between, FP32, seeded default initialisation), in
+    channels-last layout: the renderer's H x W x C image is its input as is."""
+    import torch
+    torch.manual_seed(seed)
+    net = torch.nn.Sequential(torch.nn.Conv2d(channels, 32, 3, padding=1), torch.nn.ReLU(),
+                              torch.nn.Conv2d(32, 32, 3, padding=1), torch.nn.ReLU(),
+                              torch.nn.Conv2d(32, 3, 3, padding=1))
+    return net.to(dev).to(memory_format=torch.channels_last)
+
+
+def bench_shading(dev, sc, t, tuned, capacity: int, steps: int, warmup: int, flush):
+    """The headline workload as its configuration states it: the render feeds
+    the conv shading net, the loss is the mean squared output against a zero
+    target, and loss.backward() runs through the renderer's autograd function;
+    store (the workspace kept for the backward pass) against recompute (the
+    workspace released, lists and hit lists rebuilt in the backward pass).
+    Strict FP32 convolutions (TF32 off)."""
+    import torch
+    from paper_2004_07484_gb300 import Renderer
+    prev_tf32 = torch.backends.cudnn.allow_tf32
+    torch.backends.cudnn.allow_tf32 = False
+    H, W, C = sc.height, sc.width, sc.n_channels
+    net = shading_net(dev, C)
+    params = {k: t[k].clone().requires_grad_(True) for k in ("pos", "feat", "rad", "opa", "cam", "bg")}
+    stream = torch.cuda.current_stream(dev)
+    k = max(3, min(steps, 10))
+
+    def timed(fn):
+        ms = []
+        for i in range(k):
+            flush.fill_(i & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    out = {"workload": "render -> conv 3x3 " + f"{C}->32->32->3 (ReLU, FP32, TF32 off) -> mean L2 to zero -> "
+                       "loss.backward() through the renderer's torch.autograd.Function",
+           "steps": k, "l2": "flushed between steps (256 MB write, untimed)"}
+    for mode, budget in (("store", None), ("recompute", 0)):
+        r = Renderer(W, H, sc.n_spheres, n_channels=C, n_track=sc.n_track, gamma=sc.gamma, eps=sc.eps,
+                     znear=sc.znear, zfar=sc.zfar, list_capacity=capacity, check_overflow=False,
+                     memory_budget=budget, segment=tuned.segment, persistent=tuned.persistent)
+
+        def step():
+            for p in params.values():
+                p.grad = None
+            img = r(params["pos"], params["feat"], params["rad"], params["cam"], opa=params["opa"],
+                    bg=params["bg"])
+            y = net(img.permute(2, 0, 1).unsqueeze(0))
+            (y * y).mean().backward()
+
+        for _ in range(max(warmup, 3)):
+            step()
+        torch.cuda.synchronize(dev)
+        ms = timed(step)
+        out[mode] = {"renders_per_s": 1e3 / ms, "ms_per_step": ms, "mode_taken": r.last_mode,
+                     "retained_workspace_bytes": r.last_workspace_bytes if r.last_mode == "store" else 0}
+    # the net alone (forward + backward on a fixed image), for the split
+    x = torch.randn((1, C, H, W), device=dev).to(memory_format=torch.channels_last).requires_grad_(True)
+
+    def net_step():
+        x.grad = None
+        y = net(x)
+        (y * y).mean().backward()
+
+    for _ in range(3):
+        net_step()
+    out["net_only_ms"] = timed(net_step)
+    torch.backends.cudnn.allow_tf32 = prev_tf32
+    return out
+
+
 FIT_METRIC = "scene-fit steps/sec (4 views fwd+bwd + Adam) at 5M spheres 1920x1080"
 FIT_WORKLOAD = ("scene fit: 5M spheres on 20 ellipsoid surfaces (hidden scene), 1920x1080, C=3 U[0,1], "
                 "gamma=1e-2, n_track=8, 4 views at random rotations about the centroid (distance 8), "
@@ -856,6 +934,9 @@ def main():
     clocks = clk.summary()
     roofline = step_roofline(pairs_needed, tests, hits, tracked_hits, sc.n_spheres, H * W, C, sc.n_track,
                              stage_mean, ms_per_step, pk, pk_kind, fp32_peak)
+    shading = None
+    if args.config == 2 and args.spheres is None and args.res is None:
+        shading = bench_shading(dev, sc, t, tuned, capacity, args.steps, args.warmup, flush)
     batched = None if args.no_batched else bench_batched(dev, args.steps, args.warmup, flush)
     batched_headline = None
     if not args.no_batched and args.config == 2 and args.spheres is None and args.res is None:
@@ -903,7 +984,7 @@ def main():
             "gpu_launches": ((launches_store * args.steps + launches_rec * len(ms_rec)) if not args.recompute
                              else (launches_rec * args.steps + launches_store * len(ms_rec)))
             + launches_store * len(ms_ps),
-            "wall_s_timed": t_wall, "batched": batched, "batched_headline": batched_headline,
+            "wall_s_timed": t_wall, "shading": shading, "batched": batched, "batched_headline": batched_headline,
             "autotune": {"segment": tuned.segment, "persistent": tuned.persistent,
                          "candidates_ms": {f"{a}/{'persistent' if b else 'per-unit'}": v
                                            for (a, b), v in tuned.ms.items()}}}

@@ -170,13 +170,20 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
         done = true;
         break;
       }
-      RayHit h;
-      if (!pixel_ray_hit(a, b.x, pc.rx, pc.ry, zfar, ortho, h)) continue;
       const int id = sb.id[cur][j];
-      if (hit_less(thr_t, thr_i, h.t, id)) continue;   // beyond the tracked set
+      const float4 c2 = sb.rec2[cur][j];
+      // Tracked: a hit (depth below zfar) with (t, id) at most the pixel's
+      // threshold.  A sphere whose far side lies in front of both the
+      // threshold depth and zfar is a tracked hit whatever its exact hit
+      // depth (every hit depth is at most c_z + R, up to rounding), so the
+      // hit depth is evaluated only for spheres near the threshold.
+      if (!(fmaf(1.0001f, a.z, 1.001f * c2.w) < fminf(thr_t, zfar))) {
+        RayHit h;
+        if (!pixel_ray_hit(a, b.x, pc.rx, pc.ry, zfar, ortho, h)) continue;
+        if (hit_less(thr_t, thr_i, h.t, id)) continue;   // beyond the tracked set
+      }
       float gc0 = 0.f, gc1 = 0.f, gc2 = 0.f, gR = 0.f, go = 0.f;
       float gf[CMAX];
-      const float4 c2 = sb.rec2[cur][j];
       const ValueGeom g = pixel_value_geom(a, c2, pc.vr, ortho);
       const float R = c2.w;
       const float inv_rr = vdiv(1.0f, g.rr);

@@ -12,7 +12,7 @@ be CUDA float32.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 
 import torch
 
@@ -247,13 +247,28 @@ def backward_batch(fr: BatchFrame, inputs, images, log_norms, grad_images,
 
 
 class _RenderFunction(torch.autograd.Function):
+    """The render as an autograd node.  Store: the forward's workspace (sphere
+    records, tile and block lists, each pixel's tracked-hit bound and blend
+    reference) stays alive until the backward pass.  Recompute (the
+    renderer's memory budget is smaller than that workspace): the workspace is
+    released after the forward pass, and the backward pass rebuilds it (the
+    lists and every pixel's n_track hit list) by rendering again before it
+    differentiates."""
+
     @staticmethod
     def forward(ctx, renderer, pos, feat, rad, opa, cam, bg):
         s = renderer.settings
         fr, image, log_norm = forward_frame(s, pos, feat, rad, opa, cam, bg, renderer.capacity,
                                             check_overflow=renderer.check_overflow)
         renderer.capacity = max(renderer.capacity, int(fr.params.list_capacity))
-        ctx.frame = fr
+        renderer.last_workspace_bytes = int(fr.ws_bytes)
+        keep = renderer.keeps_workspace(fr.ws_bytes)
+        renderer.last_mode = "store" if keep else "recompute"
+        ctx.frame = fr if keep else None
+        # what the backward pass re-renders with, should it recompute
+        ctx.settings = replace(s)
+        ctx.capacity = int(fr.params.list_capacity)
+        ctx.check_overflow = renderer.check_overflow
         ctx.save_for_backward(pos, feat, rad, opa, cam, bg, image, log_norm)
         ctx.mark_non_differentiable(log_norm)
         return image, log_norm
@@ -269,8 +284,12 @@ class _RenderFunction(torch.autograd.Function):
                 mask |= flag
         if mask == 0:
             return (None,) * 7
+        fr = ctx.frame
+        if fr is None:   # recompute: the lists and hit lists of the same render, rebuilt
+            fr, image, log_norm = forward_frame(ctx.settings, pos, feat, rad, opa, cam, bg, ctx.capacity,
+                                                check_overflow=ctx.check_overflow)
         g_pos, g_rad, g_opa, g_feat, g_cam, g_bg = backward_frame(
-            ctx.frame, pos, feat, rad, opa, cam, bg, image, log_norm, grad_image.contiguous(), mask)
+            fr, pos, feat, rad, opa, cam, bg, image, log_norm, grad_image.contiguous(), mask)
         ctx.frame = None
         return None, g_pos, g_feat, g_rad, g_opa, g_cam, g_bg
 
@@ -311,20 +330,38 @@ class Renderer(torch.nn.Module):
     feature image.  ``cam`` is the 11-vector [t, 6D rotation, focal, sensor
     width] or Listing 1's 8-vector [t, axis-angle rotation, focal, sensor
     width]; opacities default to 1 and the background to 0.
+
+    ``memory_budget`` (bytes, None = unlimited) is what a render may keep
+    alive between its forward and backward pass.  When the render's
+    workspace fits, it is kept (store); otherwise it is released after the
+    forward pass and the backward pass recomputes the tile lists and each
+    pixel's n_track hit list by rendering again (recompute).  ``last_mode``
+    and ``last_workspace_bytes`` report the choice of the latest forward.
+    ``segment`` and ``persistent`` are the scheduling options of
+    ``RenderSettings`` (the autotuner's choice can be passed here).
     """
 
     def __init__(self, width: int, height: int, max_n_spheres: int, n_channels: int = 3,
                  n_track: int = 5, gamma: float = 0.1, eps: float = 1e-5, znear: float = 1.0,
                  zfar: float = 20.0, store_hits: bool = True, dist_literal: bool = False,
                  min_size: bool = True, list_capacity: int | None = None,
-                 check_overflow: bool = True):
+                 check_overflow: bool = True, memory_budget: int | None = None, segment: int = 0,
+                 persistent: bool = False):
         super().__init__()
         self.settings = RenderSettings(width, height, n_channels, n_track, gamma, eps, znear, zfar,
-                                       store_hits, dist_literal, min_size)
+                                       store_hits, dist_literal, min_size, segment=segment,
+                                       persistent=persistent)
         self.max_n_spheres = int(max_n_spheres)
         self.capacity = int(list_capacity or _default_capacity(self.settings, self.max_n_spheres))
         self.check_overflow = check_overflow
+        self.memory_budget = memory_budget
         self.last_log_norm = None
+        self.last_mode = None
+        self.last_workspace_bytes = 0
+
+    def keeps_workspace(self, ws_bytes: int) -> bool:
+        """Whether a render whose workspace takes ws_bytes keeps it for the backward pass."""
+        return self.memory_budget is None or int(ws_bytes) <= int(self.memory_budget)
 
     def forward(self, pos, feat, rad, cam, opa=None, bg=None, gamma: float | None = None,
                 max_depth: float | None = None):
