@@ -127,9 +127,9 @@ Layout make_layout(const pulsar_params* ps, int n) {
   L.key1 = take(4 * (size_t)M);
   L.val0 = take(4 * (size_t)M);
   L.val1 = take(4 * (size_t)M);
-  L.hist = take(4 * (size_t)kRadix * L.sort_blocks);
+  L.hist = take(4 * (size_t)std::max(kRadix, kDepthRadix) * L.sort_blocks);
   L.block_sums = take(4 * (size_t)L.sort_blocks);
-  L.radix_tot = take(4 * (size_t)kRadix);
+  L.radix_tot = take(4 * (size_t)std::max(kRadix, kDepthRadix));
   L.pkey0 = take(4 * (size_t)cap);
   L.pkey1 = take(4 * (size_t)cap);
   L.pval0 = take(4 * (size_t)cap);
@@ -187,6 +187,26 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   // the paper's early termination follows a pixel's denominator along its
   // whole list: one render unit walks every segment of its tile in order
   v.chain = (ps[0].flags & PULSAR_FLAG_PAPER_STOP) ? 1 : 0;
+  // depth sort keys: visible keys lie strictly between a scene's planes, so
+  // their float bits minus those of the batch's smallest znear lie in
+  // (0, top - base), top the bits of the largest zfar; culled spheres take
+  // top - base, the passes cover the bits of that range
+  {
+    uint32_t lo = 0xffffffffu, hi = 0u;
+    for (int s = 0; s < n; ++s) {
+      uint32_t a, z;
+      memcpy(&a, &ps[s].znear, 4);
+      memcpy(&z, &ps[s].zfar, 4);
+      lo = std::min(lo, a);
+      hi = std::max(hi, z);
+    }
+    v.key_base = lo;
+    v.key_culled = hi - lo;
+    int bits = 1;
+    while (bits < 32 && (v.key_culled >> bits) != 0u) ++bits;
+    v.key_bits = bits;
+    v.sort_buf = ((bits + kDepthRadixBits - 1) / kDepthRadixBits) & 1;
+  }
   v.rec0 = reinterpret_cast<float4*>(b + L.rec0);
   v.rec1 = reinterpret_cast<float4*>(b + L.rec1);
   v.rec2 = reinterpret_cast<float4*>(b + L.rec2);

@@ -20,10 +20,10 @@ namespace pulsar {
 
 namespace {
 
-// Per warp: list positions of entries whose rectangle meets the warp's block,
+// Per warp: sphere indices of the entries whose rectangle meets the warp's block,
 // gathered into full batches, and the current batch's test bookkeeping.
 struct BlockListWarp {
-  int32_t pos[64];     // gathered list positions, in list order
+  uint32_t pos[64];    // gathered sphere indices, in list order
   float4 rec0[32];     // draw record (decision centre, R^2)
   int first[32];       // first test number of each entry
   uint32_t geom[32];   // overlap with the block: x0 | y0 << 8 | width << 16
@@ -35,13 +35,12 @@ struct BlockListWarp {
 // Tests the pixels of the first cnt gathered entries against the block and
 // appends the entries with hits, in order, to out (n entries so far).
 __device__ __forceinline__ void block_batch(BlockListWarp& W, int cnt, const WsView& v, const SceneDev& S,
-                                            const WarpRect& wr, const uint32_t* __restrict__ list,
-                                            uint2* out, int& n, uint32_t& hits) {
+                                            const WarpRect& wr, uint2* out, int& n, uint32_t& hits) {
   const int lane = threadIdx.x & 31;
   uint32_t id = 0u;
   int ntest = 0;
   if (lane < cnt) {
-    id = __ldg(list + W.pos[lane]);
+    id = W.pos[lane];
     const float4 b = __ldg(v.rec1 + id);
     const uint32_t bx = __float_as_uint(b.z), by = __float_as_uint(b.w);
     const int x0 = max((int)(bx & 0xffffu), wr.x0), x1 = min((int)(bx >> 16), wr.x1);
@@ -104,18 +103,21 @@ __global__ void __launch_bounds__(32 * kListWarps) block_lists_kernel(const WsVi
   const uint32_t mine = 1u << (kTileKeyBits + block);
   int n = 0, pending = 0;
   uint32_t hits = 0u;   // this lane's share of the unit's pixel hits
+  // the pair keys and sphere indices of the next 32 entries load while the current ones are used
   uint32_t key_next = it.b0 + lane < it.b1 ? __ldg(keys + it.b0 + lane) : 0u;
+  uint32_t id_next = it.b0 + lane < it.b1 ? __ldg(list + it.b0 + lane) : 0u;
   for (int base = it.b0; base < it.b1; base += 32) {
-    const uint32_t key = key_next;
+    const uint32_t key = key_next, id = id_next;
     key_next = base + 32 + lane < it.b1 ? __ldg(keys + base + 32 + lane) : 0u;
+    id_next = base + 32 + lane < it.b1 ? __ldg(list + base + 32 + lane) : 0u;
     // gather the entries whose rectangle meets this block (from the pair key)
     const bool ok = base + lane < it.b1 && (key & mine) != 0u;
     const uint32_t bal = __ballot_sync(0xffffffffu, ok);
-    if (ok) W.pos[pending + __popc(bal & lane_lt_mask())] = base + lane;
+    if (ok) W.pos[pending + __popc(bal & lane_lt_mask())] = id;
     pending += __popc(bal);
     if (pending >= 32) {
       __syncwarp();
-      block_batch(W, 32, v, S, wr, list, out, n, hits);
+      block_batch(W, 32, v, S, wr, out, n, hits);
       const int rest = pending - 32;
       if (lane < rest) W.pos[lane] = W.pos[32 + lane];
       pending = rest;
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(32 * kListWarps) block_lists_kernel(const WsVi
   }
   if (pending > 0) {
     __syncwarp();
-    block_batch(W, pending, v, S, wr, list, out, n, hits);
+    block_batch(W, pending, v, S, wr, out, n, hits);
   }
   hits = __reduce_add_sync(0xffffffffu, hits);
   if (lane == 0) {

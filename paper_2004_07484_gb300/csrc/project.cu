@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) project_kernel(WsView v) {
     v.rec0[i] = make_float4(pr.cx, pr.cy, pr.cz, pr.R2);
     v.rec1[i] = make_float4(pr.key, o, __uint_as_float(pack_range(pr.x0, pr.x1)),
                             __uint_as_float(pack_range(pr.y0, pr.y1)));
-    v.key[0][i] = __float_as_uint(pr.key);
+    v.key[0][i] = pr.visible ? __float_as_uint(pr.key) - v.key_base : v.key_culled;
     v.val[0][i] = (uint32_t)i;
     // value path: the centre to about 2^-46 relative (float-float), kept as
     // the float32 decision centre plus a float correction; the radius as
@@ -136,7 +136,10 @@ __global__ void __launch_bounds__(kThreads) project_kernel(WsView v) {
   // warp-aggregated maxima per scene (non-negative floats order as integers)
   const unsigned peers = __match_any_sync(0xffffffffu, live ? s : -1);
   const uint32_t om_w = __reduce_max_sync(peers, om);
-  if (live && (threadIdx.x & 31) == __ffs(peers) - 1 && om_w) atomicMax(&v.scenes[s].omax_bits, om_w);
+  // (a read first: once the scene's maximum is known, most warps need no atomic)
+  if (live && (threadIdx.x & 31) == __ffs(peers) - 1 && om_w &&
+      om_w > *reinterpret_cast<volatile uint32_t*>(&v.scenes[s].omax_bits))
+    atomicMax(&v.scenes[s].omax_bits, om_w);
 }
 
 // One thread per sphere of the batch: clears the per-sphere accumulators the

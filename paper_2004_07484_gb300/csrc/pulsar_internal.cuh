@@ -22,8 +22,10 @@ constexpr int kTile = 16;            // tile edge in pixels
 constexpr int kChunk = 256;          // spheres staged in shared memory per round
 constexpr int kSortItems = 8;        // keys per thread in one radix-sort tile
 constexpr int kSortTile = kThreads * kSortItems;   // 2048 keys per radix-sort CTA
-constexpr int kRadixBits = 8;
+constexpr int kRadixBits = 8;              // digit bits of the tile-key sort
 constexpr int kRadix = 1 << kRadixBits;
+constexpr int kDepthRadixBits = 9;         // digit bits of the depth-key sort
+constexpr int kDepthRadix = 1 << kDepthRadixBits;
 constexpr int kMaxScenes = 64;
 constexpr int kFinalizeThreads = 256;
 constexpr int kCamPartials = 16;     // floats per finalize-block camera partial (13 used)
@@ -124,14 +126,18 @@ struct WsView {
   int32_t persistent;        // render passes run as persistent kernels
   int32_t paper;             // the paper's gradient normalisations
   int32_t chain;             // render units walk a tile's segments in order (early termination)
+  uint32_t key_base;         // depth sort keys: float bits of the key minus key_base
+  uint32_t key_culled;       // the depth sort key of a culled sphere (above every visible one)
+  int32_t key_bits;          // significant bits of the depth sort keys
+  int32_t sort_buf;          // buffer holding the depth-sorted spheres
   float4* rec0;              // per sphere: c.x, c.y, c.z, R^2
   float4* rec1;              // per sphere: key, o, x-range (x0 | x1 << 16), y-range
   float4* rec2;              // per sphere: c - c.xyz (low-order part of the double centre), R
   uint32_t* key[2];          // radix sort keys (ping-pong)
   uint32_t* val[2];          // radix sort values (ping-pong)
-  uint32_t* hist;            // radix histograms [kRadix][sort_blocks]
+  uint32_t* hist;            // radix histograms [digits][sort_blocks]
   uint32_t* block_sums;      // scan partials [sort_blocks]
-  uint32_t* radix_tot;       // per digit: total count of one radix pass [kRadix]
+  uint32_t* radix_tot;       // per digit: total count of one radix pass
   uint32_t* pkey[2];         // pair tile ids (ping-pong)
   uint32_t* pval[2];         // pair sphere ids (ping-pong)
   int2* ranges;              // per tile [begin, end)

@@ -1,5 +1,7 @@
 // Binning (App. B, Step 0 sort and Step 1 region culling, re-designed):
-//   1. stable LSD radix sort of (earliest depth, sphere index),
+//   1. stable LSD radix sort of (earliest depth, sphere index): the depth
+//      key's float bits as an offset from the smallest near plane of the
+//      batch (visible keys lie between the planes), 9 bits per pass,
 //   2. exclusive scan of each sorted sphere's tile count,
 //   3. emission of one (tile, sphere) pair per overlapped tile, in depth order,
 //   4. stable LSD radix sort of the pairs by tile,
@@ -26,28 +28,38 @@ __device__ __forceinline__ int read_count(const int32_t* n_dev, int n_host) {
   return n_dev ? *n_dev : n_host;
 }
 
-// Per-CTA digit histogram of one radix pass (warp-aggregated shared atomics).
+// Per-CTA digit histogram of one radix pass of RB-bit digits (warp-aggregated
+// shared atomics).
+template <int RB>
 __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __restrict__ keys,
                                                           const int32_t* n_dev, int n_host, int shift,
                                                           uint32_t mask, uint32_t* __restrict__ hist,
                                                           int stride) {
-  __shared__ uint32_t h[kRadix];
+  constexpr int R = 1 << RB;
+  __shared__ uint32_t h[R];
   const int n = read_count(n_dev, n_host);
   const int base = blockIdx.x * kSortTile;
   if (base >= n) return;
-  h[threadIdx.x] = 0;
-  __syncthreads();
+  for (int i = threadIdx.x; i < R; i += kThreads) h[i] = 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // all of this thread's keys in flight at once, then the ranking
+  uint32_t kr[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int idx = base + warp * (kSortItems * 32) + k * 32 + lane;
+    kr[k] = idx < n ? __ldg(keys + idx) : 0u;
+  }
+  __syncthreads();
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     int idx = base + warp * (kSortItems * 32) + k * 32 + lane;
     bool valid = idx < n;
-    uint32_t d = valid ? (keys[idx] >> shift) & mask : 0xffffffffu;
+    uint32_t d = valid ? (kr[k] >> shift) & mask : 0xffffffffu;
     unsigned peers = __match_any_sync(0xffffffffu, d);
     if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
   __syncthreads();
-  hist[threadIdx.x * stride + blockIdx.x] = h[threadIdx.x];
+  for (int i = threadIdx.x; i < R; i += kThreads) hist[i * stride + blockIdx.x] = h[i];
 }
 
 // Exclusive scan, in place, of one digit's row of per-CTA counts
@@ -76,30 +88,40 @@ __global__ void __launch_bounds__(kThreads) scan_rows(uint32_t* __restrict__ dat
 // match.any in index order; warps are combined in warp order; items are first
 // placed in shared memory in their CTA-local sorted order and then written out
 // in coalesced runs per digit.
+template <int RB>
 __global__ void __launch_bounds__(kThreads) radix_downsweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int32_t* n_dev,
     int n_host, int shift, uint32_t mask, const uint32_t* __restrict__ hist,
     const uint32_t* __restrict__ row_tot, int stride) {
+  constexpr int R = 1 << RB;
+  constexpr int DPT = R / kThreads;   // digits per thread in the per-digit steps
+  static_assert(DPT >= 1 && DPT * kThreads == R, "digits a multiple of the threads");
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
-  __shared__ uint32_t warp_cnt[kThreads / 32][kRadix];
-  __shared__ uint32_t digit_local[kRadix];
-  __shared__ uint32_t digit_global[kRadix];
+  __shared__ uint32_t warp_cnt[kThreads / 32][R];
+  __shared__ uint32_t digit_local[R];
+  __shared__ uint32_t digit_global[R];
   __shared__ uint32_t warp_tot[33];
   const int n = read_count(n_dev, n_host);
   const int base = blockIdx.x * kSortTile;
   if (base >= n) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int w = 0; w < kThreads / 32; ++w) warp_cnt[w][threadIdx.x] = 0;
-  __syncthreads();
+  // all of this thread's keys and values in flight at once, then the ranking
   uint32_t k_reg[kSortItems], v_reg[kSortItems], rank[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int idx = base + warp * (kSortItems * 32) + k * 32 + lane;
+    k_reg[k] = idx < n ? __ldg(keys_in + idx) : 0u;
+    v_reg[k] = idx < n ? __ldg(vals_in + idx) : 0u;
+  }
+  for (int w = 0; w < kThreads / 32; ++w)
+    for (int i = threadIdx.x; i < R; i += kThreads) warp_cnt[w][i] = 0;
+  __syncthreads();
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     int idx = base + warp * (kSortItems * 32) + k * 32 + lane;
     bool valid = idx < n;
-    k_reg[k] = valid ? keys_in[idx] : 0u;
-    v_reg[k] = valid ? vals_in[idx] : 0u;
     uint32_t d = valid ? (k_reg[k] >> shift) & mask : 0xffffffffu;
     unsigned peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = 0;
@@ -110,21 +132,37 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
     __syncwarp();
   }
   __syncthreads();
-  // per digit: exclusive prefix over warps, then over digits
+  // per digit: exclusive prefix over warps, then over digits (thread t takes
+  // the DPT consecutive digits from t * DPT)
   {
-    const int d = threadIdx.x;
-    uint32_t tot = 0;
-    for (int w = 0; w < kThreads / 32; ++w) {
-      uint32_t c = warp_cnt[w][d];
-      warp_cnt[w][d] = tot;
-      tot += c;
+    uint32_t tot[DPT], rt[DPT];
+    uint32_t sum = 0, rsum = 0;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      const int d = threadIdx.x * DPT + q;
+      uint32_t t = 0;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        uint32_t c = warp_cnt[w][d];
+        warp_cnt[w][d] = t;
+        t += c;
+      }
+      tot[q] = t;
+      sum += t;
+      rt[q] = row_tot[d];
+      rsum += rt[q];
     }
     uint32_t all;
-    uint32_t ex = block_exclusive_scan<kThreads>(tot, warp_tot, all);
-    digit_local[d] = ex;
+    uint32_t ex = block_exclusive_scan<kThreads>(sum, warp_tot, all);
     // global start of digit d: all smaller digits, then earlier CTAs of d
-    const uint32_t base_d = block_exclusive_scan<kThreads>(row_tot[d], warp_tot, all);
-    digit_global[d] = base_d + hist[d * stride + blockIdx.x];
+    uint32_t base_d = block_exclusive_scan<kThreads>(rsum, warp_tot, all);
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      const int d = threadIdx.x * DPT + q;
+      digit_local[d] = ex;
+      digit_global[d] = base_d + hist[d * stride + blockIdx.x];
+      ex += tot[q];
+      base_d += rt[q];
+    }
   }
   __syncthreads();
 #pragma unroll
@@ -161,15 +199,21 @@ __global__ void __launch_bounds__(kThreads) count_reduce(WsView v) {
   __shared__ uint32_t warp_tot[33];
   const int n = (int)v.n_spheres;
   const int base = blockIdx.x * kSortTile;
-  uint32_t s = 0;
+  // every load of the thread's spheres in flight at once
+  uint32_t key[kSortItems], idx[kSortItems];
+#pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
-    int j = base + threadIdx.x * kSortItems + k;
-    if (j < n) {
-      uint32_t key = v.key[0][j];
-      bool visible = key != 0x7f800000u;
-      if (visible) s += tile_count(v.rec1[v.val[0][j]], true);
-    }
+    const int j = base + threadIdx.x * kSortItems + k;
+    key[k] = j < n ? __ldg(v.key[v.sort_buf] + j) : v.key_culled;
+    idx[k] = j < n ? __ldg(v.val[v.sort_buf] + j) : 0u;
   }
+  float4 r1[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) r1[k] = key[k] != v.key_culled ? __ldg(v.rec1 + idx[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k)
+    if (key[k] != v.key_culled) s += tile_count(r1[k], true);
   uint32_t tot;
   block_exclusive_scan<kThreads>(s, warp_tot, tot);
   if (threadIdx.x == 0) v.block_sums[blockIdx.x] = tot;
@@ -206,16 +250,23 @@ __global__ void __launch_bounds__(kThreads) emit_pairs(WsView v) {
   const int n = (int)v.n_spheres;
   if (v.hdr->overflow) return;
   const int base = blockIdx.x * kSortTile;
+  // every load of the thread's spheres in flight at once
+  uint32_t key[kSortItems], idx[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int j = base + threadIdx.x * kSortItems + k;
+    key[k] = j < n ? __ldg(v.key[v.sort_buf] + j) : v.key_culled;
+    idx[k] = j < n ? __ldg(v.val[v.sort_buf] + j) : 0u;
+  }
+  float4 r1s[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k)
+    r1s[k] = key[k] != v.key_culled ? __ldg(v.rec1 + idx[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
   uint32_t cnt[kSortItems];
   uint32_t s = 0;
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
-    int j = base + threadIdx.x * kSortItems + k;
-    cnt[k] = 0;
-    if (j < n) {
-      uint32_t key = v.key[0][j];
-      if (key != 0x7f800000u) cnt[k] = tile_count(v.rec1[v.val[0][j]], true);
-    }
+    cnt[k] = key[k] != v.key_culled ? tile_count(r1s[k], true) : 0u;
     s += cnt[k];
   }
   uint32_t tot;
@@ -223,9 +274,8 @@ __global__ void __launch_bounds__(kThreads) emit_pairs(WsView v) {
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     if (cnt[k] == 0) continue;
-    int j = base + threadIdx.x * kSortItems + k;
-    uint32_t i = v.val[0][j];
-    float4 r1 = v.rec1[i];
+    const uint32_t i = idx[k];
+    const float4 r1 = r1s[k];
     int sc = scene_of_sphere(v.scenes, v.n_scenes, i);
     const SceneDev& S = v.scenes[sc];
     uint32_t bx = __float_as_uint(r1.z), by = __float_as_uint(r1.w);
@@ -328,18 +378,21 @@ __global__ void __launch_bounds__(1024) make_items(WsView v) {
   for (uint32_t i = threadIdx.x; i < tot; i += 1024) v.item_order[atomicAdd(&bucket[cls(i)], 1u)] = (int32_t)i;
 }
 
+// Stable LSD radix sort of (key, value) by the low `bits` key bits, RB bits
+// per pass; buf is the buffer holding the input and, on return, the output.
+template <int RB>
 cudaError_t radix_sort(const WsView& v, uint32_t* keys[2], uint32_t* vals[2], const int32_t* n_dev,
                        int n_host, int max_items, int bits, int& buf, cudaStream_t st) {
   const int blocks = (max_items + kSortTile - 1) / kSortTile;
   if (blocks == 0) return cudaSuccess;
-  for (int shift = 0; shift < bits; shift += kRadixBits) {
-    uint32_t mask = (uint32_t)((1u << min(kRadixBits, bits - shift)) - 1u);
-    radix_upsweep<<<blocks, kThreads, 0, st>>>(keys[buf], n_dev, n_host, shift, mask, v.hist,
-                                               v.sort_blocks);
-    scan_rows<<<kRadix, kThreads, 0, st>>>(v.hist, v.radix_tot, n_dev, n_host, v.sort_blocks);
-    radix_downsweep<<<blocks, kThreads, 0, st>>>(keys[buf], vals[buf], keys[buf ^ 1], vals[buf ^ 1],
-                                                 n_dev, n_host, shift, mask, v.hist, v.radix_tot,
-                                                 v.sort_blocks);
+  for (int shift = 0; shift < bits; shift += RB) {
+    uint32_t mask = (uint32_t)((1u << min(RB, bits - shift)) - 1u);
+    radix_upsweep<RB><<<blocks, kThreads, 0, st>>>(keys[buf], n_dev, n_host, shift, mask, v.hist,
+                                                   v.sort_blocks);
+    scan_rows<<<1 << RB, kThreads, 0, st>>>(v.hist, v.radix_tot, n_dev, n_host, v.sort_blocks);
+    radix_downsweep<RB><<<blocks, kThreads, 0, st>>>(keys[buf], vals[buf], keys[buf ^ 1], vals[buf ^ 1],
+                                                     n_dev, n_host, shift, mask, v.hist, v.radix_tot,
+                                                     v.sort_blocks);
     buf ^= 1;
   }
   return cudaGetLastError();
@@ -357,10 +410,10 @@ cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st) {
   if (M > 0) {
     uint32_t* k[2] = {v.key[0], v.key[1]};
     uint32_t* val[2] = {v.val[0], v.val[1]};
-    e = radix_sort(v, k, val, nullptr, M, M, 32, buf, st);
+    e = radix_sort<kDepthRadixBits>(v, k, val, nullptr, M, M, v.key_bits, buf, st);
     if (e != cudaSuccess) return e;
   }
-  // 32 bits = 4 passes: the result is back in buffer 0
+  // the sorted spheres are in buffer v.sort_buf (the parity of the pass count)
   const int nb = (M + kSortTile - 1) / kSortTile;
   if (nb > 0) count_reduce<<<nb, kThreads, 0, st>>>(v);
   count_scan<<<1, 1024, 0, st>>>(v, nb);
@@ -370,7 +423,7 @@ cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st) {
   if (v.capacity > 0) {
     uint32_t* k[2] = {v.pkey[0], v.pkey[1]};
     uint32_t* val[2] = {v.pval[0], v.pval[1]};
-    e = radix_sort(v, k, val, &v.hdr->n_pairs, 0, (int)v.capacity, tile_bits, pbuf, st);
+    e = radix_sort<kRadixBits>(v, k, val, &v.hdr->n_pairs, 0, (int)v.capacity, tile_bits, pbuf, st);
     if (e != cudaSuccess) return e;
   }
   // 5. ranges
