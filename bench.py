@@ -47,7 +47,7 @@ N_SMS = 152
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only
 # for the kernel sources with this digest, reported as null otherwise.
 FWD_KERNEL_SOURCES = ("render_fwd.cu", "render_common.cuh", "pulsar_internal.cuh")
-FWD_TRAFFIC = {"sha256": "74b4536860a41723283f7598f982e4266ec8399069f5086fb7e107978ce87c46", "bytes": 211327488 + 10581760}
+FWD_TRAFFIC = {"sha256": "a44d12a70ea2fdb52d5e28f1546a6284eb4cb4b18ce6525610b87d6fc5685598", "bytes": 240630528 + 23080448}
 
 
 def fwd_kernel_digest() -> str:
