@@ -64,7 +64,12 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __rest
 
 // Exclusive scan, in place, of one digit's row of per-CTA counts
 // (row r = blockIdx.x, cols = ceil(n / kSortTile) entries at data[r * stride]),
-// and the row's total into row_tot[r].  One CTA per digit.
+// and the row's total into row_tot[r].  One CTA per digit; each thread takes
+// kScanPer consecutive columns per sweep, all loaded before the scan, so a
+// row of up to kThreads * kScanPer columns is one load round trip and one
+// block scan.
+constexpr int kScanPer = 8;
+
 __global__ void __launch_bounds__(kThreads) scan_rows(uint32_t* __restrict__ data,
                                                       uint32_t* __restrict__ row_tot,
                                                       const int32_t* n_dev, int n_host, int stride) {
@@ -73,12 +78,23 @@ __global__ void __launch_bounds__(kThreads) scan_rows(uint32_t* __restrict__ dat
   const int cols = (n + kSortTile - 1) / kSortTile;
   uint32_t* row = data + (size_t)blockIdx.x * stride;
   uint32_t carry = 0;
-  for (int c0 = 0; c0 < cols; c0 += kThreads) {
-    const int c = c0 + threadIdx.x;
-    const uint32_t x = c < cols ? row[c] : 0u;
+  for (int c0 = 0; c0 < cols; c0 += kThreads * kScanPer) {
+    const int cb = c0 + threadIdx.x * kScanPer;
+    uint32_t x[kScanPer];
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) x[k] = cb + k < cols ? row[cb + k] : 0u;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      const uint32_t t = x[k];
+      x[k] = sum;
+      sum += t;
+    }
     uint32_t tot;
-    const uint32_t ex = block_exclusive_scan<kThreads>(x, warp_tot, tot);
-    if (c < cols) row[c] = carry + ex;
+    const uint32_t ex = block_exclusive_scan<kThreads>(sum, warp_tot, tot);
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k)
+      if (cb + k < cols) row[cb + k] = carry + ex + x[k];
     carry += tot;
   }
   if (threadIdx.x == 0) row_tot[blockIdx.x] = carry;
@@ -107,13 +123,21 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
   const int base = blockIdx.x * kSortTile;
   if (base >= n) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // all of this thread's keys and values in flight at once, then the ranking
+  // all of this thread's keys and values in flight at once, with its digits'
+  // global counts (row totals and this CTA's prefix), then the ranking
   uint32_t k_reg[kSortItems], v_reg[kSortItems], rank[kSortItems];
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     const int idx = base + warp * (kSortItems * 32) + k * 32 + lane;
     k_reg[k] = idx < n ? __ldg(keys_in + idx) : 0u;
     v_reg[k] = idx < n ? __ldg(vals_in + idx) : 0u;
+  }
+  uint32_t rt[DPT], hcta[DPT];
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) {
+    const int d = threadIdx.x * DPT + q;
+    rt[q] = row_tot[d];
+    hcta[q] = hist[d * stride + blockIdx.x];
   }
   for (int w = 0; w < kThreads / 32; ++w)
     for (int i = threadIdx.x; i < R; i += kThreads) warp_cnt[w][i] = 0;
@@ -135,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
   // per digit: exclusive prefix over warps, then over digits (thread t takes
   // the DPT consecutive digits from t * DPT)
   {
-    uint32_t tot[DPT], rt[DPT];
+    uint32_t tot[DPT];
     uint32_t sum = 0, rsum = 0;
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
@@ -148,7 +172,6 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
       }
       tot[q] = t;
       sum += t;
-      rt[q] = row_tot[d];
       rsum += rt[q];
     }
     uint32_t all;
@@ -159,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
     for (int q = 0; q < DPT; ++q) {
       const int d = threadIdx.x * DPT + q;
       digit_local[d] = ex;
-      digit_global[d] = base_d + hist[d * stride + blockIdx.x];
+      digit_global[d] = base_d + hcta[q];
       ex += tot[q];
       base_d += rt[q];
     }
