@@ -840,7 +840,8 @@ def main():
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if rank == 0:
-            print(json.dumps({"profile_step": "done", "pairs": pairs_needed, "hits": hits, "tests": tests}))
+            print(json.dumps({"profile_step": "done", "pairs": pairs_needed, "hits": hits, "tests": tests,
+                              "segment": tuned.segment, "persistent": tuned.persistent}))
         return
     if world > 1:
         dist.barrier()

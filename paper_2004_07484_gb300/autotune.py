@@ -64,12 +64,27 @@ def pairs_per_scene(settings: list[RenderSettings], inputs) -> list[int]:
     return out
 
 
-def time_step(settings, inputs, grads, capacities, reps: int = 3) -> float:
-    """Median milliseconds of one batched forward + backward (CUDA events)."""
+L2_FLUSH_BYTES = 256 << 20   # more than the GPU's L2
+_flush: dict = {}
+
+
+def _flush_l2(dev):
+    """Overwrites a buffer larger than L2, so that each timed step starts with
+    the cold cache a training step meets after its optimiser update."""
+    buf = _flush.get(dev)
+    if buf is None:
+        buf = _flush[dev] = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    buf.zero_()
+
+
+def time_step(settings, inputs, grads, capacities, reps: int = 5) -> float:
+    """Median milliseconds of one batched forward + backward (CUDA events),
+    each started with a flushed L2."""
     dev = inputs[0][0].device
     stream = torch.cuda.current_stream(dev)
     times = []
     for i in range(reps + 1):
+        _flush_l2(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         fr, images, log_norms = forward_batch(settings, inputs, capacities, check_overflow=False)
@@ -82,7 +97,7 @@ def time_step(settings, inputs, grads, capacities, reps: int = 3) -> float:
     return times[len(times) // 2]
 
 
-def tune(settings: list[RenderSettings], inputs, grads, reps: int = 3, use_cache: bool = True) -> Choice:
+def tune(settings: list[RenderSettings], inputs, grads, reps: int = 5, use_cache: bool = True) -> Choice:
     """Picks segment length and kernel form for this batch; returns the choice
     (the settings themselves are not modified: apply it with ``apply``)."""
     key = signature(settings, [int(x[0].shape[0]) for x in inputs])
