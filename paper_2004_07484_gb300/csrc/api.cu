@@ -49,25 +49,11 @@ cudaError_t side_stream(SideStream*& out) {   // call with g_side_mutex held
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// Resident one-warp render CTAs of the current device (16 per SM, the render
-// kernels' launch bound), cached per device; the unit-splitting threshold
-// divides a pass's total cost by it.
-int render_slots() {
-  static int cache[64] = {0};
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 16 * 152;
-  if (cache[dev] == 0) {
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-    cache[dev] = 16 * sms;
-  }
-  return cache[dev];
-}
-
 struct Layout {
   size_t hdr, scenes, rec0, rec1, rec2, key0, key1, val0, val1, hist, block_sums, pkey0, pkey1, pval0,
-      pval1, radix_tot, ranges, item_begin, item_desc, item_order, unit_list, unit_count, unit_cost, unit_order, unit_parts, unit_xslot, unit_tests, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
+      pval1, radix_tot, ranges, item_begin, item_desc, item_order, unit_list, unit_count, unit_cost, unit_order, unit_tests, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
       gacc, pg_cnt, pg_opa, pg_feat, fin_part, red_part, total;
-  int64_t n_spheres, n_tiles, n_pixels, capacity, max_items, max_extra;
+  int64_t n_spheres, n_tiles, n_pixels, capacity, max_items;
   int32_t sort_blocks, fin_blocks, tile_bits, segment, part_fields;
 };
 
@@ -126,7 +112,6 @@ Layout make_layout(const pulsar_params* ps, int n) {
   L.segment = ps[0].segment > 0 ? ps[0].segment : kDefaultSegment;
   L.max_items = NT + (cap + L.segment - 1) / L.segment;
   L.part_fields = 6 + C + 2 * K;
-  L.max_extra = std::min<int64_t>(8 * L.max_items, kMaxExtraParts);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -157,15 +142,12 @@ Layout make_layout(const pulsar_params* ps, int n) {
   L.unit_list = take(8 * 8 * (size_t)cap);
   L.unit_count = take(4 * 8 * (size_t)L.max_items);
   L.unit_cost = take(4 * 8 * (size_t)L.max_items);
-  L.unit_order = take(4 * (8 * (size_t)L.max_items + (size_t)L.max_extra));
-  L.unit_parts = take(4 * 8 * (size_t)L.max_items);
-  L.unit_xslot = take(4 * 8 * (size_t)L.max_items);
+  L.unit_order = take(4 * 8 * (size_t)L.max_items);
   L.unit_tests = take(4 * 8 * 32 * (size_t)L.max_items);
   // per (tile or work item) x 8 pixel blocks of 32 pixels
   L.tile_done = take(4 * 8 * (size_t)NT);
-  // per work piece: the unit's own slot (item x 8 + block), then the extra parts' slots
-  L.partial = take(4 * (8 * (size_t)L.max_items + (size_t)L.max_extra) * 32 * L.part_fields);
-  L.item_kappa = take(4 * (8 * (size_t)L.max_items + (size_t)L.max_extra));
+  L.partial = take(4 * 8 * (size_t)L.max_items * 32 * L.part_fields);
+  L.item_kappa = take(4 * 8 * (size_t)L.max_items);
   L.tile_bg = take(4 * 8 * (size_t)NT * C);
   L.pix_aux = take(16 * (size_t)P);
   L.fres = take(4 * (size_t)P * C);
@@ -199,9 +181,6 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.pair_buf = ((L.tile_bits + kRadixBits - 1) / kRadixBits) & 1;
   v.segment = L.segment;
   v.max_items = (int32_t)L.max_items;
-  v.extra_base = (int32_t)(8 * L.max_items);
-  v.max_extra = (int32_t)L.max_extra;
-  v.split_slots = render_slots();
   v.part_fields = L.part_fields;
   v.persistent = (ps[0].flags & PULSAR_FLAG_PERSISTENT) ? 1 : 0;
   v.paper = (ps[0].flags & PULSAR_FLAG_PAPER_GRADIENTS) ? 1 : 0;
@@ -250,8 +229,6 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.unit_count = reinterpret_cast<int32_t*>(b + L.unit_count);
   v.unit_cost = reinterpret_cast<uint32_t*>(b + L.unit_cost);
   v.unit_order = reinterpret_cast<int32_t*>(b + L.unit_order);
-  v.unit_parts = reinterpret_cast<int32_t*>(b + L.unit_parts);
-  v.unit_xslot = reinterpret_cast<int32_t*>(b + L.unit_xslot);
   v.unit_tests = reinterpret_cast<int32_t*>(b + L.unit_tests);
   v.tile_done = reinterpret_cast<int32_t*>(b + L.tile_done);
   v.partial = reinterpret_cast<float*>(b + L.partial);
@@ -335,9 +312,6 @@ pulsar_status validate_batch(int n, const pulsar_params* ps) {
     nt += (int64_t)tx * ty;
   }
   if (nt > ((int64_t)1 << kTileKeyBits)) return PULSAR_ERR_UNSUPPORTED;   // tile index bits of a pair key
-  // a work piece is coded unit << 3 | part in an int32
-  const int64_t seg = ps[0].segment > 0 ? ps[0].segment : kDefaultSegment;
-  if (8 * (nt + (cap + seg - 1) / seg) >= ((int64_t)1 << 28)) return PULSAR_ERR_UNSUPPORTED;
   return PULSAR_OK;
 }
 

@@ -135,14 +135,10 @@ __global__ void __launch_bounds__(32 * kListWarps) block_lists_kernel(const WsVi
   }
 }
 
-// Launch order of the render passes' work pieces: decreasing modelled cost,
-// by a counting sort over kCostClasses logarithmic cost classes (four per
-// octave; the order within a class is arbitrary).
+// Launch order of the render passes' work units: decreasing cost (block-list
+// length plus pixel hits), by a counting sort over kCostClasses logarithmic
+// cost classes (four per octave; the order within a class is arbitrary).
 constexpr int kCostClasses = 64;
-// Modelled render time of a unit, in pixel hits: a fixed set-up (the first
-// batch's latency, the epilogue), about 1.5 hits per block-list entry (its
-// staging and the per-batch bounds), and its pixel hits.
-constexpr uint32_t kUnitSetupCost = 384;
 
 __device__ __forceinline__ int cost_class(uint32_t c) {
   if (c < 4u) return kCostClasses - 1 - (int)c;
@@ -151,66 +147,23 @@ __device__ __forceinline__ int cost_class(uint32_t c) {
   return max(kCostClasses - 1 - cls, 0);
 }
 
-__device__ __forceinline__ uint32_t unit_model(const WsView& v, uint32_t u) {
-  return kUnitSetupCost + v.unit_cost[u] + ((uint32_t)v.unit_count[u] >> 1);
-}
-
 // Cost of unit u as the render passes see it: with a chained walk the first
 // segment's unit renders all segments of its tile and the others none.
 __device__ __forceinline__ uint32_t walk_cost(const WsView& v, uint32_t u) {
-  if (!v.chain) return unit_model(v, u);
+  if (!v.chain) return v.unit_cost[u];
   const ItemDesc d = v.item_desc[u / kBlocksPerTile];
   if (d.seg != 0) return 0u;
   uint32_t c = 0;
-  for (int k = d.first; k < d.first + d.nseg; ++k) c += unit_model(v, k * kBlocksPerTile + u % kBlocksPerTile);
+  for (int k = d.first; k < d.first + d.nseg; ++k) c += v.unit_cost[k * kBlocksPerTile + u % kBlocksPerTile];
   return c;
 }
 
-// Splits the units that would outlast a balanced pass and orders the pieces.
-// A unit whose modelled cost exceeds the pass's total over the resident
-// render CTAs (one CTA's share of a balanced pass) is cut into
-// ceil(cost / share) parts (at most kMaxParts, of at least kMinPartEntries
-// entries, while the workspace has extra slots), so that no piece is longer
-// than a share; chained walks stay whole.  Pieces are coded unit << 3 | part.
 __global__ void __launch_bounds__(1024) order_units_kernel(const WsView v) {
   __shared__ uint32_t bucket[kCostClasses];
-  __shared__ unsigned long long total;
-  __shared__ int extra_taken, extra_used;
   const uint32_t n = (uint32_t)v.hdr->n_items * kBlocksPerTile;
   if (threadIdx.x < kCostClasses) bucket[threadIdx.x] = 0u;
-  if (threadIdx.x == 0) {
-    total = 0ull;
-    extra_taken = 0;
-    extra_used = 0;
-  }
   __syncthreads();
-  unsigned long long mine = 0ull;
-  for (uint32_t u = threadIdx.x; u < n; u += 1024) mine += walk_cost(v, u);
-  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&total, mine);
-  __syncthreads();
-  const unsigned long long share = total / (unsigned long long)max(v.split_slots, 1);
-  const uint32_t thr = (uint32_t)max((unsigned long long)kSplitMinCost, min(share, 0xffffffffull));
-  for (uint32_t u = threadIdx.x; u < n; u += 1024) {
-    const uint32_t c = walk_cost(v, u);
-    int parts = 1, xs = 0;
-    if (!v.chain && c > thr) {
-      parts = (int)min((c + thr - 1) / thr, (uint32_t)kMaxParts);
-      parts = min(parts, max(v.unit_count[u] / kMinPartEntries, 1));
-      if (parts > 1) {
-        xs = atomicAdd(&extra_taken, parts - 1);
-        if (xs + parts - 1 > v.max_extra) {
-          parts = 1;
-          xs = 0;
-        } else {
-          atomicAdd(&extra_used, parts - 1);
-        }
-      }
-    }
-    v.unit_parts[u] = parts;
-    v.unit_xslot[u] = xs;
-    atomicAdd(&bucket[cost_class(c / (uint32_t)parts)], (uint32_t)parts);
-  }
+  for (uint32_t u = threadIdx.x; u < n; u += 1024) atomicAdd(&bucket[cost_class(walk_cost(v, u))], 1u);
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t run = 0;
@@ -219,14 +172,10 @@ __global__ void __launch_bounds__(1024) order_units_kernel(const WsView v) {
       bucket[b] = run;
       run += c;
     }
-    v.hdr->n_pieces = (int32_t)n + extra_used;
   }
   __syncthreads();
-  for (uint32_t u = threadIdx.x; u < n; u += 1024) {
-    const int parts = v.unit_parts[u];
-    const uint32_t at = atomicAdd(&bucket[cost_class(walk_cost(v, u) / (uint32_t)parts)], (uint32_t)parts);
-    for (int k = 0; k < parts; ++k) v.unit_order[at + k] = (int32_t)((u << 3) | (uint32_t)k);
-  }
+  for (uint32_t u = threadIdx.x; u < n; u += 1024)
+    v.unit_order[atomicAdd(&bucket[cost_class(walk_cost(v, u))], 1u)] = (int32_t)u;
 }
 
 // The n_tests diagnostic: per work unit and pixel, the spheres of the

@@ -301,8 +301,8 @@ constexpr int kRedParts = 64;   // CTAs per scene in the first reduction stage
 constexpr int kRedValues = 13 + 32;
 
 // First stage of the camera and background reduction: CTA (scene, part)
-// sums its share of the per-block camera partials, the per-work-piece pitch
-// partials and the per-(tile, pixel block) background partials.
+// sums its share of the per-block camera partials, the per-(item, pixel
+// block) pitch partials and the per-(tile, pixel block) background partials.
 __global__ void __launch_bounds__(256) camera_partials_kernel(WsView v, uint32_t mask) {
   __shared__ float red[8][kRedValues];
   const SceneDev& S = v.scenes[blockIdx.x];
@@ -321,11 +321,7 @@ __global__ void __launch_bounds__(256) camera_partials_kernel(WsView v, uint32_t
       for (int k = 0; k < 13; ++k) acc[k] += fp[k];
     }
     const int i0 = 8 * v.item_begin[S.tile_begin], i1 = 8 * v.item_begin[S.tile_begin + nt];
-    for (int i = i0 + start; i < i1; i += stride) {
-      acc[12] += v.item_kappa[i];
-      // the extra parts of a split unit keep their partials in slots of their own
-      for (int k = 1; k < v.unit_parts[i]; ++k) acc[12] += v.item_kappa[v.extra_base + v.unit_xslot[i] + k - 1];
-    }
+    for (int i = i0 + start; i < i1; i += stride) acc[12] += v.item_kappa[i];
   }
   if (mask & PULSAR_GRAD_BG) {
     const float* rows = v.tile_bg + (size_t)S.tile_begin * 8 * C;

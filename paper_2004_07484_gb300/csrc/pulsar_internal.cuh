@@ -30,14 +30,6 @@ constexpr int kMaxScenes = 64;
 constexpr int kFinalizeThreads = 256;
 constexpr int kCamPartials = 16;     // floats per finalize-block camera partial (13 used)
 constexpr int kDefaultSegment = 1024;  // list entries one CTA processes per work item
-// Work-unit splitting: a unit whose block list is expensive next to the whole
-// pass (cost above the pass's total over the resident render CTAs) is rendered
-// as up to kMaxParts pieces of at least kMinPartEntries entries each, merged
-// like segments; the workspace holds at most kMaxExtraParts extra pieces.
-constexpr int kMaxParts = 8;
-constexpr int kMinPartEntries = 32;
-constexpr int kMaxExtraParts = 2048;
-constexpr uint32_t kSplitMinCost = 64;  // no unit below this cost is split
 constexpr int kTileKeyBits = 24;        // pair keys: tile index bits (the block set above them)
 constexpr uint32_t kTileKeyMask = (1u << kTileKeyBits) - 1u;
 
@@ -100,8 +92,7 @@ struct WsHeader {
   int32_t timeout;           // a bounded device loop gave up
   int32_t n_items;           // (tile, segment) work items of the render passes
   int32_t work_next;         // next work unit of a persistent render launch
-  int32_t n_pieces;          // render-pass work pieces (units, long ones split in parts)
-  int32_t pad_[6];
+  int32_t pad_[7];
 };
 
 // One work item of the render passes: a segment [b0, b1) of a tile's list.
@@ -131,9 +122,6 @@ struct WsView {
   int32_t pair_buf;          // ping-pong buffer holding the tile-sorted pairs
   int32_t segment;           // list entries per work item (a multiple of kChunk)
   int32_t max_items;         // bound on work items: n_tiles + capacity / segment
-  int32_t extra_base;        // first partial / pitch slot of the extra parts (8 max_items)
-  int32_t max_extra;         // extra parts the workspace holds slots for
-  int32_t split_slots;       // resident render CTAs of the device: sets the split threshold
   int32_t part_fields;       // floats per pixel of a partial forward state
   int32_t persistent;        // render passes run as persistent kernels
   int32_t paper;             // the paper's gradient normalisations
@@ -159,13 +147,11 @@ struct WsView {
   uint2* unit_list;          // block lists: [pixel block][capacity] (sphere, hit mask)
   int32_t* unit_count;       // per work unit (item x 8 + block): block-list length
   uint32_t* unit_cost;       // per work unit: block-list length + pixel hits in its masks
-  int32_t* unit_order;       // work pieces by decreasing cost: unit << 3 | part (render-pass order)
-  int32_t* unit_parts;       // per work unit: the parts its block list is split into (1..8)
-  int32_t* unit_xslot;       // per work unit: extra slot of its part 1 (parts k >= 1 take xslot + k - 1)
+  int32_t* unit_order;       // work units by decreasing cost (render-pass launch order)
   int32_t* unit_tests;       // per work unit x 32 pixels: rectangle tests made
   int32_t* tile_done;        // per tile: finished segments (last-finisher merge)
-  float* partial;            // per work piece slot: partial forward state, [field][pixel]
-  float* item_kappa;         // per work piece slot: d L / d kappa partial
+  float* partial;            // per work item: partial forward state, [field][pixel]
+  float* item_kappa;         // per work item: d L / d kappa partial
   float* tile_bg;            // per (tile, pixel block) x C background-gradient partials
   float4* pix_aux;           // per pixel: (t_K, id_K bits, reference sphere bits, 0)
   float* fres;               // per pixel x C: F - f_ref, the image relative to its reference feature

@@ -4,9 +4,8 @@
 // tracked hit.  That threshold is kept per pixel by the forward pass (store
 // mode, App. B "Preparing for the Backward Pass") or recomputed before this
 // pass by the forward traversal without blending (recompute mode).  Work is
-// split into the same one-warp pieces as the forward pass (a segment's pixel
-// block, or a part of an expensive block list); gradients are sums, so pieces
-// need no merge.  As in the forward
+// split into the same one-warp (segment, pixel block) CTAs as the forward
+// pass; gradients are sums, so segments need no merge.  As in the forward
 // pass, each batch of staged spheres is first hit-tested by every lane, then
 // each lane walks its own tracked hits and adds their gradients with (vector)
 // atomics, so lanes never wait on one another's hits.  A pixel stops at the
@@ -72,7 +71,7 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
   const bool cam = (mask & PULSAR_GRAD_CAM) != 0;
   // a chained walk handles the tile's later segments from its first
   if (CHAIN && it.seg != 0) {
-    if (cam && threadIdx.x == 0) v.item_kappa[it.piece_slot] = 0.0f;
+    if (cam && threadIdx.x == 0) v.item_kappa[it.slot] = 0.0f;
     return;
   }
   const SceneDev& S = v.scenes[it.scene];
@@ -138,8 +137,8 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
       if (c < C) Gref = fmaf(G[c], __ldg(fref + c), Gref);
   }
 
-  // background gradient: sum over the block of w_B G (first piece of the first segment only)
-  if (bgw && it.seg == 0 && it.part == 0) {
+  // background gradient: sum over the block of w_B G (first segment only)
+  if (bgw && it.seg == 0) {
     const float wB = pc.inside ? __expf(S.eps * inv_gamma - logD) : 0.0f;
     float* dst = v.tile_bg + ((size_t)it.tile * kBlocksPerTile + it.block) * C;
 #pragma unroll
@@ -149,7 +148,7 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
     }
   }
   if (!per_hit) {
-    if (cam && lane == 0) v.item_kappa[it.piece_slot] = 0.0f;
+    if (cam && lane == 0) v.item_kappa[it.slot] = 0.0f;
     return;
   }
 
@@ -269,7 +268,7 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
   ws.drain();
   if (cam) {
     const float x = warp_sum(gk_sum);
-    if (lane == 0) v.item_kappa[it.piece_slot] = x;
+    if (lane == 0) v.item_kappa[it.slot] = x;
   }
 }
 
@@ -283,10 +282,10 @@ __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v, uint
     bwd_unit<CMAX, CHAIN>(v, mask, blockIdx.x, sb);
     return;
   }
-  const int n_pieces = v.hdr->n_pieces;
+  const int n_units = v.hdr->n_items * kBlocksPerTile;
   for (;;) {
     const int w = next_unit(v);
-    if (w >= n_pieces) break;
+    if (w >= n_units) break;
     bwd_unit<CMAX, CHAIN>(v, mask, w, sb);
     __syncwarp();
   }
@@ -297,7 +296,7 @@ cudaError_t launch_bwd_t(const WsView& v, uint32_t mask, cudaStream_t st) {
   const size_t smem = sizeof(StageBuf<CMAX, kBwdBuffers>);
   // the paper's early termination walks a tile's segments in order
   auto kern = v.chain ? render_bwd_kernel<CMAX, true> : render_bwd_kernel<CMAX, false>;
-  unsigned grid = (unsigned)v.max_items * kBlocksPerTile + (unsigned)v.max_extra;
+  unsigned grid = (unsigned)v.max_items * kBlocksPerTile;
   if (v.persistent) {
     const unsigned slots = resident_slots(kern, 32, smem);
     if (slots == 0) return cudaErrorLaunchOutOfResources;

@@ -32,10 +32,7 @@ constexpr int kBlocksPerTile = 8;   // 8 x 4 pixel blocks (warps) per 16 x 16 ti
 struct ItemCtx {
   int item;          // work-item index
   int block;         // pixel block of the tile (0..7)
-  int slot;          // item * 8 + block: the work unit
-  int part, nparts;  // this piece of the unit's block list and the unit's pieces
-  int e0, e1;        // block-list range [e0, e1) of this piece
-  int piece_slot;    // partial-state and pitch-partial slot of this piece
+  int slot;          // item * 8 + block: partial-state and partial-sum slot
   int64_t tile;      // global tile index
   int seg, nseg;     // segment index and segment count of the tile
   int first;         // first work item of the tile
@@ -51,11 +48,6 @@ __device__ __forceinline__ bool item_ctx_direct(const WsView& v, int item, int b
   c.item = item;
   c.block = block;
   c.slot = item * kBlocksPerTile + block;
-  c.part = 0;
-  c.nparts = 1;
-  c.e0 = 0;
-  c.e1 = 0x7fffffff;
-  c.piece_slot = c.slot;
   c.tile = d.tile;
   c.first = d.first;
   c.nseg = d.nseg;
@@ -66,36 +58,13 @@ __device__ __forceinline__ bool item_ctx_direct(const WsView& v, int item, int b
   return true;
 }
 
-// Partial-state slot of piece k of unit u.
-__device__ __forceinline__ int piece_slot(const WsView& v, int u, int k) {
-  return k == 0 ? u : v.extra_base + v.unit_xslot[u] + k - 1;
-}
-
-// Work piece w of a render pass: the w-th most costly piece by its block
-// list, so that the longest pieces start first and the passes end with short
-// ones.  A piece is a whole (item, pixel block) unit, or one of the nparts
-// equal parts of the block list of an expensive unit (split when the binning
-// pass ordered the units); parts are merged like segments.
+// Work unit w of a render pass: the w-th most costly (item, pixel block)
+// unit by its block list (length plus pixel hits), so that the longest units
+// start first and the passes end with short ones.
 __device__ __forceinline__ bool item_ctx(const WsView& v, int w, ItemCtx& c) {
-  if (w >= v.hdr->n_pieces) return false;
-  const int code = v.unit_order[w];
-  const int u = code >> 3, k = code & 7;
-  if (!item_ctx_direct(v, u / kBlocksPerTile, u % kBlocksPerTile, c)) return false;
-  c.part = k;
-  c.nparts = v.unit_parts[u];
-  const int64_t n = v.unit_count[u];
-  c.e0 = (int)(n * k / c.nparts);
-  c.e1 = (int)(n * (k + 1) / c.nparts);
-  c.piece_slot = piece_slot(v, u, k);
-  return true;
-}
-
-// Pieces of pixel block `block` over all segments of a tile (first item
-// `first`, nseg segments): the partial states its last finisher merges.
-__device__ __forceinline__ int block_pieces(const WsView& v, int first, int nseg, int block) {
-  int n = 0;
-  for (int o = first; o < first + nseg; ++o) n += v.unit_parts[o * kBlocksPerTile + block];
-  return n;
+  if (w >= v.hdr->n_items * kBlocksPerTile) return false;
+  const int u = v.unit_order[w];
+  return item_ctx_direct(v, u / kBlocksPerTile, u % kBlocksPerTile, c);
 }
 
 // Next work unit of a persistent render kernel (one atomic per warp).
@@ -325,11 +294,8 @@ struct UnitStream {
       n = 0;
       for (int k = it.first; k < it.first + it.nseg; ++k) n += counts[k * kBlocksPerTile + block];
     } else {
-      // this piece's part of the unit's block list
-      const int cnt = v.unit_count[it.slot];
-      const int e0 = min(it.e0, cnt), e1 = min(it.e1, cnt);
-      src = v.unit_list + (size_t)it.block * v.capacity + it.b0 + e0;
-      n = e1 - e0;
+      src = v.unit_list + (size_t)it.block * v.capacity + it.b0;
+      n = v.unit_count[it.slot];
     }
     base = 0;
     buf = 0;

@@ -8,9 +8,6 @@
 // per-part closest, so segments are combined afterwards: the warp that
 // finishes a block's segments last (a per-block atomic counter) merges the
 // partial states the others left in the workspace and writes the pixels.
-// A unit whose block list would outlast a balanced launch is cut the same
-// way into up to eight parts of its block list (the binning pass decides),
-// and its parts are merged with the segments.
 //
 // Each batch of up to 32 staged spheres is handled in two phases: every lane
 // first runs the cheap float32 hit test of its pixel against all of them and
@@ -133,7 +130,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   bs.fref = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(&sb) + sizeof(StageBuf<CMAX>)) +
             lane * StageBuf<CMAX>::FS;
   bs.m = S.eps * inv_gamma;
-  bs.den = it.seg == 0 && it.part == 0 ? 1.0f : 0.0f;
+  bs.den = it.seg == 0 ? 1.0f : 0.0f;
   bs.adom = bs.den;
   bs.dom = -1;
 #pragma unroll
@@ -154,7 +151,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   float kstop3 = pstop ? paper_bound() : __int_as_float(0x7f800000);
   int stop_pos = 0x7fffffff;
 
-  if (S.n_tests && it.part == 0) {
+  if (S.n_tests) {
     ntest = v.unit_tests[(size_t)it.slot * 32 + lane];
     if (CHAIN)
       for (int k = it.first + 1; k < it.first + it.nseg; ++k)
@@ -239,11 +236,11 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   }
   ws.drain();
 
-  if ((it.nseg > 1 || it.nparts > 1) && !CHAIN) {
-    // leave this piece's state, then let the block's last finished piece merge
+  if (it.nseg > 1 && !CHAIN) {
+    // leave this block's segment state, then let the block's last segment merge
     const int F = v.part_fields;
     const int q0 = kPRes + C;
-    float* P = v.partial + (size_t)it.piece_slot * F * 32 + lane;
+    float* P = v.partial + (size_t)it.slot * F * 32 + lane;
     if (BLEND) {
       P[kPM * 32] = bs.m;
       P[kPDen * 32] = bs.den;
@@ -265,61 +262,54 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
     __threadfence();
     __syncwarp();
     int last = 0;
-    if (lane == 0) {
-      const int pieces = it.nseg > 1 ? block_pieces(v, it.first, it.nseg, it.block) : it.nparts;
-      last = atomicAdd(&v.tile_done[it.tile * kBlocksPerTile + it.block], 1) == pieces - 1;
-    }
+    if (lane == 0)
+      last = atomicAdd(&v.tile_done[it.tile * kBlocksPerTile + it.block], 1) == it.nseg - 1;
     last = __shfl_sync(0xffffffffu, last, 0);
     if (!last) return;
     __threadfence();
-    // every other piece of this pixel block, segment by segment
     for (int o = it.first; o < it.first + it.nseg; ++o) {
-      const int u = o * kBlocksPerTile + it.block;
-      for (int k = 0; k < v.unit_parts[u]; ++k) {
-        const int qs = piece_slot(v, u, k);
-        if (qs == it.piece_slot) continue;
-        const float* Q = v.partial + (size_t)qs * F * 32 + lane;
-        if (BLEND) {
-          const float mB = __ldcg(Q + kPM * 32);
-          float denB = __ldcg(Q + kPDen * 32);
-          float adomB = __ldcg(Q + kPAdom * 32);
-          const int domB = __float_as_int(__ldcg(Q + kPDom * 32));
-          ntest += __float_as_int(__ldcg(Q + kPTests * 32));
-          const float m = fmaxf(bs.m, mB);
-          const float sa = __expf(bs.m - m), sb = __expf(mB - m);
-          bs.den *= sa;
-          bs.adom *= sa;
-          denB *= sb;
-          adomB *= sb;
-          const float* fB = ref_feature(S, domB);
-          if (adomB > bs.adom) {
-            // the other piece's reference carries more weight: re-express ours
+      if (o == it.item) continue;
+      const float* Q = v.partial + ((size_t)o * kBlocksPerTile + it.block) * F * 32 + lane;
+      if (BLEND) {
+        const float mB = __ldcg(Q + kPM * 32);
+        float denB = __ldcg(Q + kPDen * 32);
+        float adomB = __ldcg(Q + kPAdom * 32);
+        const int domB = __float_as_int(__ldcg(Q + kPDom * 32));
+        ntest += __float_as_int(__ldcg(Q + kPTests * 32));
+        const float m = fmaxf(bs.m, mB);
+        const float sa = __expf(bs.m - m), sb = __expf(mB - m);
+        bs.den *= sa;
+        bs.adom *= sa;
+        denB *= sb;
+        adomB *= sb;
+        const float* fB = ref_feature(S, domB);
+        if (adomB > bs.adom) {
+          // the other segment's reference carries more weight: re-express ours
 #pragma unroll
-            for (int c = 0; c < CMAX; ++c)
-              if (c < C) {
-                const float fb = fB[c];
-                bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * 32),
-                                 fmaf(bs.den, bs.fref[c] - fb, bs.res[c] * sa));
-                bs.fref[c] = fb;
-              }
-            bs.adom = adomB;
-            bs.dom = domB;
-          } else {
+          for (int c = 0; c < CMAX; ++c)
+            if (c < C) {
+              const float fb = fB[c];
+              bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * 32),
+                               fmaf(bs.den, bs.fref[c] - fb, bs.res[c] * sa));
+              bs.fref[c] = fb;
+            }
+          bs.adom = adomB;
+          bs.dom = domB;
+        } else {
 #pragma unroll
-            for (int c = 0; c < CMAX; ++c)
-              if (c < C)
-                bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * 32),
-                                 fmaf(denB, fB[c] - bs.fref[c], bs.res[c] * sa));
-          }
-          bs.den += denB;
-          bs.m = m;
+          for (int c = 0; c < CMAX; ++c)
+            if (c < C)
+              bs.res[c] = fmaf(sb, __ldcg(Q + (kPRes + c) * 32),
+                               fmaf(denB, fB[c] - bs.fref[c], bs.res[c] * sa));
         }
-        nhit += __float_as_int(__ldcg(Q + kPHits * 32));
-        for (int j = 0; j < K; ++j) {
-          const uint64_t key = hit_key(__ldcg(Q + (q0 + j) * 32), __float_as_int(__ldcg(Q + (q0 + K + j) * 32)));
-          if (key < q[KMAX - 1]) queue_insert<KMAX>(q, key);
-          else break;   // the other piece's entries ascend
-        }
+        bs.den += denB;
+        bs.m = m;
+      }
+      nhit += __float_as_int(__ldcg(Q + kPHits * 32));
+      for (int j = 0; j < K; ++j) {
+        const uint64_t key = hit_key(__ldcg(Q + (q0 + j) * 32), __float_as_int(__ldcg(Q + (q0 + K + j) * 32)));
+        if (key < q[KMAX - 1]) queue_insert<KMAX>(q, key);
+        else break;   // the other segment's entries ascend
       }
     }
     if (lane == 0) v.tile_done[it.tile * kBlocksPerTile + it.block] = 0;   // ready for the next launch
@@ -388,10 +378,10 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v, int pe
     traverse_unit<KMAX, CMAX, BLEND, CHAIN>(v, blockIdx.x, sb);
     return;
   }
-  const int n_pieces = v.hdr->n_pieces;
+  const int n_units = v.hdr->n_items * kBlocksPerTile;
   for (;;) {
     const int w = next_unit(v);
-    if (w >= n_pieces) break;
+    if (w >= n_units) break;
     traverse_unit<KMAX, CMAX, BLEND, CHAIN>(v, w, sb);
     __syncwarp();
   }
@@ -402,7 +392,7 @@ cudaError_t launch_t(const WsView& v, cudaStream_t st) {
   // staging buffers, then (blending) every lane's reference feature
   const size_t smem = sizeof(StageBuf<CMAX>) + (BLEND ? sizeof(float) * 32 * StageBuf<CMAX>::FS : 0);
   auto kern = traverse_kernel<KMAX, CMAX, BLEND, CHAIN>;
-  unsigned grid = (unsigned)v.max_items * kBlocksPerTile + (unsigned)v.max_extra;
+  unsigned grid = (unsigned)v.max_items * kBlocksPerTile;
   if (v.persistent) {
     const unsigned slots = resident_slots(kern, 32, smem);
     if (slots == 0) return cudaErrorLaunchOutOfResources;

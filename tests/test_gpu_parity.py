@@ -150,29 +150,6 @@ def test_backward_matches_oracle(orc, cache, variant, store):
     assert_grads_close(got, want, scene=sc)
 
 
-def _header_counts(frame):
-    """(work items, work pieces) from the workspace header (int32 fields at
-    byte offsets 28 and 36 of the library's device header)."""
-    h = frame.ws[:64].cpu().numpy().view(np.int32)
-    return int(h[7]), int(h[9])
-
-
-@pytest.mark.parametrize("persistent", [False, True], ids=["per-piece", "persistent"])
-def test_split_units_match_oracle(orc, persistent):
-    """Long block lists are rendered as several pieces merged like segments:
-    the same images, tracked hits and gradients as the oracle."""
-    sc = dense_c16()
-    gpu = gpu_forward(sc, segment=4096, persistent=persistent)
-    items, pieces = _header_counts(gpu["frame"])
-    assert pieces > 8 * items, (items, pieces)   # some unit was split
-    ref = orc.render(sc)
-    img = gpu["image"].cpu().numpy().astype(np.float64)
-    assert np.abs(img - ref.image).max() <= 1e-4
-    np.testing.assert_array_equal(gpu["tracked"].cpu().numpy(), ref.tracked)
-    G = S.grad_image(7, sc.height, sc.width, sc.n_channels)
-    assert_grads_close(gpu_backward(gpu, G), orc.render_backward(sc, G), scene=sc)
-
-
 def test_store_and_recompute_agree(orc):
     sc = dense_c16()
     G = S.grad_image(5, sc.height, sc.width, sc.n_channels)
