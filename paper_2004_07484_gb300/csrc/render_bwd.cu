@@ -130,7 +130,7 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
     thr_t = aux.x;
     thr_i = __float_as_int(aux.y);
     dom = __float_as_int(aux.z);
-    if (S.flags & PULSAR_FLAG_PAPER_STOP) stop_pos = __float_as_int(aux.w);
+    if (CHAIN && (S.flags & PULSAR_FLAG_PAPER_STOP)) stop_pos = __float_as_int(aux.w);
     const float* fref = dom < 0 ? S.bg : S.feat + (int64_t)(dom - S.sphere_begin) * C;
 #pragma unroll
     for (int c = 0; c < CMAX; ++c)

@@ -144,7 +144,8 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   bool done = !pc.inside;
   float kstop1 = __int_as_float(0x7f800000);   // tracked-set bound (i)
   // the paper's early termination: its key bound and where the pixel stopped
-  const bool pstop = BLEND && (S.flags & PULSAR_FLAG_PAPER_STOP) != 0 && omax > 0.0f;
+  // (the paper's rule comes with the chained walk: other instantiations never take it)
+  const bool pstop = CHAIN && BLEND && (S.flags & PULSAR_FLAG_PAPER_STOP) != 0 && omax > 0.0f;
   const float pscale = range * gamma / omax;
   const float log_ratio = S.stop_log_ratio;
   auto paper_bound = [&]() { return zfar - pscale * ((bs.m + __logf(bs.den)) + log_ratio); };
