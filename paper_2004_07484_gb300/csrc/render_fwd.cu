@@ -109,8 +109,7 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   // a chained walk renders the tile's later segments from its first
   if (CHAIN && it.seg != 0) return;
   const SceneDev& S = v.scenes[it.scene];
-  const PixelCtx pc = pixel_ctx(S, it.tile, it.block);
-  const WarpRect wr = warp_rect(pc, it.block);
+  PixelCtx pc = pixel_ctx(S, it.tile, it.block);
   const int C = S.n_channels;
   const int K = S.n_track;
   const float gamma = S.gamma, zfar = S.zfar, znear = S.znear;
@@ -151,13 +150,11 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
   auto paper_bound = [&]() { return zfar - pscale * ((bs.m + __logf(bs.den)) + log_ratio); };
   float kstop3 = pstop ? paper_bound() : __int_as_float(0x7f800000);
   int stop_pos = 0x7fffffff;
+  // the n_tests diagnostic of a chained walk: every segment's tests
+  if (CHAIN && S.n_tests)
+    for (int k = it.first; k < it.first + it.nseg; ++k)
+      ntest += v.unit_tests[((size_t)k * kBlocksPerTile + it.block) * 32 + lane];
 
-  if (S.n_tests) {
-    ntest = v.unit_tests[(size_t)it.slot * 32 + lane];
-    if (CHAIN)
-      for (int k = it.first + 1; k < it.first + it.nseg; ++k)
-        ntest += v.unit_tests[((size_t)k * kBlocksPerTile + it.block) * 32 + lane];
-  }
   for (; ws.base < ws.n; ws.advance()) {
     if (__all_sync(0xffffffffu, done)) break;
     // remaining-mass bound (ii), from the state at the start of this batch;
@@ -236,6 +233,15 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
     }
   }
   ws.drain();
+
+  // the unit's descriptors and pixel are reloaded here rather than kept in
+  // registers through the walk (the chained walk's register allocation
+  // measured better without)
+  if (!CHAIN) {
+    item_ctx(v, w, it);
+    pc = pixel_ctx(S, it.tile, it.block);
+    if (S.n_tests) ntest = v.unit_tests[(size_t)it.slot * 32 + lane];
+  }
 
   if (it.nseg > 1 && !CHAIN) {
     // leave this block's segment state, then let the block's last segment merge
