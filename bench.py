@@ -47,7 +47,7 @@ N_SMS = 152
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only
 # for the kernel sources with this digest, reported as null otherwise.
 FWD_KERNEL_SOURCES = ("render_fwd.cu", "render_common.cuh", "pulsar_internal.cuh")
-FWD_TRAFFIC = {"sha256": "a44d12a70ea2fdb52d5e28f1546a6284eb4cb4b18ce6525610b87d6fc5685598", "bytes": 240630528 + 23080448}
+FWD_TRAFFIC = {"sha256": "6d43b312479360f8895f8e4692504a879b87f83cb4609659b84655ea7a041dc3", "bytes": 214258944 + 8154880}
 
 
 def fwd_kernel_digest() -> str:
@@ -102,7 +102,7 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int, period_ms: int = 50):
+    def __init__(self, gpu_index: int, period_ms: int = 10):
         self.gpu = gpu_index
         self.period_ms = period_ms
         self.proc = None
