@@ -249,9 +249,9 @@ pulsar_status pulsar_last_overflow(const pulsar_params* params, void* workspace,
  *   The array is shared by every call in the process and keeps the last
  *   call's contents; calls that overlap on the GPU (other streams, other
  *   threads) race on it and must be serialised by the caller.
- *   Its device address is looked up once per device, by the first call made
- *   with that device current; make that first call before any stream
- *   capture.  The address is stale after cudaDeviceReset of that device.
+ *   Its device address is looked up in the current context on every call
+ *   (valid across device resets); the first call on a device loads the
+ *   library's module there, so make it before any stream capture.
  *   A list_capacity overflow (the image is then background only) is read
  *   back with pulsar_static_read_status. */
 pulsar_status pulsar_render_fwd_static(const pulsar_params* params, const pulsar_scene* scene,

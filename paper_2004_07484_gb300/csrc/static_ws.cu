@@ -9,41 +9,19 @@
 // a file-scope device array instead and allocates nothing itself.
 //
 // Set-up: the array's device address is looked up with cudaGetSymbolAddress
-// once per device, on the first call made while that device is current.  In
-// host code the array's name is only a host-side stand-in, so the kernels are
-// always given the looked-up address.  The address belongs to the device's
-// context: after cudaDeviceReset it is stale, so a process that resets a
-// device must not call these entry points on it again.
-#include <mutex>
-
+// on every call, in the context current at the call (the lookup is cheap once
+// the module is loaded), so a device reset or a new context never leaves a
+// stale address behind.  In host code the array's name is only a host-side
+// stand-in, so the kernels are always given the looked-up address.
 #include "pulsar_internal.cuh"
 
 namespace pulsar {
 namespace {
 
-constexpr int kMaxDevices = 64;
-
 static __device__ __align__(256) unsigned char g_static_ws[PULSAR_STATIC_WORKSPACE_BYTES];
 
-std::mutex g_addr_mutex;
-void* g_addr[kMaxDevices] = {nullptr};
-
-// Device address of g_static_ws on the current device (looked up once).
-cudaError_t static_ws_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_ws);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
-  return cudaSuccess;
-}
+// Device address of g_static_ws in the current context.
+cudaError_t static_ws_address(void** out) { return cudaGetSymbolAddress(out, g_static_ws); }
 
 }  // namespace
 }  // namespace pulsar
