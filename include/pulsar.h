@@ -53,7 +53,7 @@ typedef enum {
   PULSAR_ERR_CAPACITY = 2,     /* workspace or pair list too small */
   PULSAR_ERR_CUDA = 3,         /* a CUDA runtime call failed */
   PULSAR_ERR_TIMEOUT = 4,      /* a bounded device loop gave up */
-  PULSAR_ERR_UNSUPPORTED = 5   /* valid request this build does not handle */
+  PULSAR_ERR_UNSUPPORTED = 5   /* valid request the library does not handle */
 } pulsar_status;
 
 /* pulsar_params.flags */
