@@ -245,6 +245,33 @@ def test_1m_spheres_1024_sampled(orc):
         assert_grads_close(gpu_backward(out, G), want, scene=sc)
 
 
+_bench_ref = {}
+
+
+@pytest.mark.parametrize("segment,persistent", [(2048, False), (2048, True), (4096, True)],
+                         ids=["seg2048", "seg2048-persistent", "seg4096-persistent"])
+def test_1m_spheres_1024_bench_schedules(orc, segment, persistent):
+    """The 1M-sphere workload in the launch configurations the benchmark's
+    autotuner picks between: sampled pixels bit-exact in their tracked hits and
+    within the image bar, and a gradient crop within the gradient bar."""
+    sc = S.config_scene(2)
+    gpu = gpu_forward(sc, capacity=2 << 20, segment=segment, persistent=persistent)
+    if not _bench_ref:
+        g = np.random.default_rng(17)
+        busy = np.argwhere(gpu["n_hits"].cpu().numpy() > 0)
+        pix = busy[g.choice(len(busy), 96, replace=False)][:, ::-1]
+        v, u = busy[g.integers(len(busy))]
+        v0, u0 = min(max(v - 8, 0), 1024 - 16), min(max(u - 8, 0), 1024 - 16)
+        G = np.zeros((1024, 1024, 16))
+        G[v0:v0 + 16, u0:u0 + 16] = S.grad_image(8, 16, 16, 16)
+        _bench_ref.update(pix=pix, ref=orc.render_pixels(sc, pix), G=G, want=orc.render_backward(sc, G))
+    pix, ref = _bench_ref["pix"], _bench_ref["ref"]
+    img = gpu["image"].cpu().numpy()[pix[:, 1], pix[:, 0]]
+    assert np.abs(img - ref.image).max() <= 1e-4
+    np.testing.assert_array_equal(gpu["tracked"].cpu().numpy()[pix[:, 1], pix[:, 0]], ref.tracked)
+    assert_grads_close(gpu_backward(gpu, _bench_ref["G"]), _bench_ref["want"], scene=sc)
+
+
 def test_5m_spheres_1920x1080_sampled(orc):
     """The largest single-scene workload (5M spheres on ellipsoid surfaces,
     1920x1080, C=3, n_track 8) at sampled pixels, with a gradient crop."""
