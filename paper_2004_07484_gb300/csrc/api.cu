@@ -52,7 +52,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
   size_t hdr, scenes, rec0, rec1, rec2, key0, key1, val0, val1, hist, block_sums, pkey0, pkey1, pval0,
       pval1, radix_tot, ranges, item_begin, item_desc, item_order, unit_list, unit_count, unit_cost, unit_order, unit_tests, tile_done, partial, item_kappa, tile_bg, pix_aux, fres,
-      gacc, pg_cnt, pg_opa, pg_feat, fin_part, red_part, total;
+      gacc, pg_cnt, pg_opa, pg_feat, fin_part, red_part, cam_done, total;
   int64_t n_spheres, n_tiles, n_pixels, capacity, max_items;
   int32_t sort_blocks, fin_blocks, tile_bits, segment, part_fields;
 };
@@ -159,6 +159,7 @@ Layout make_layout(const pulsar_params* ps, int n) {
   L.pg_feat = take(paper ? 4 * (size_t)M * C : 0);
   L.fin_part = take(4 * (size_t)kCamPartials * std::max(fin, 1));
   L.red_part = take(4 * (size_t)n * 64 * 45);
+  L.cam_done = take(4 * (size_t)kMaxScenes);
   L.total = off;
   return L;
 }
@@ -242,6 +243,7 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.pg_feat = reinterpret_cast<float*>(b + L.pg_feat);
   v.fin_part = reinterpret_cast<float*>(b + L.fin_part);
   v.red_part = reinterpret_cast<float*>(b + L.red_part);
+  v.cam_done = reinterpret_cast<int32_t*>(b + L.cam_done);
   return v;
 }
 

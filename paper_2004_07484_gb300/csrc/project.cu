@@ -66,6 +66,7 @@ __global__ void setup_kernel(WsView v, const SetupPack<N> pk) {
     }
     v.scenes[i] = d;
   }
+  if (i < pk.n && pk.full) v.cam_done[i] = 0;
   if (i == 0 && pk.full) {
     v.hdr->n_scenes = pk.n;
     v.hdr->n_sort = (int32_t)pk.n_spheres;
@@ -300,63 +301,18 @@ __device__ __forceinline__ float dot3(const float* a, const float* b) {
 constexpr int kRedParts = 64;   // CTAs per scene in the first reduction stage
 constexpr int kRedValues = 13 + 32;
 
-// First stage of the camera and background reduction: CTA (scene, part)
-// sums its share of the per-block camera partials, the per-(item, pixel
-// block) pitch partials and the per-(tile, pixel block) background partials.
-__global__ void __launch_bounds__(256) camera_partials_kernel(WsView v, uint32_t mask) {
-  __shared__ float red[8][kRedValues];
-  const SceneDev& S = v.scenes[blockIdx.x];
-  const int part = blockIdx.y;
-  const int C = S.n_channels;
-  const int64_t nt = (int64_t)S.tiles_x * S.tiles_y;
-  const int stride = kRedParts * blockDim.x;
-  const int start = part * blockDim.x + threadIdx.x;
-  float acc[kRedValues];
-#pragma unroll
-  for (int k = 0; k < kRedValues; ++k) acc[k] = 0.0f;
-  if (mask & PULSAR_GRAD_CAM) {
-    for (int b = start; b < S.fin_blocks; b += stride) {
-      const float* fp = v.fin_part + (size_t)(S.fin_block_begin + b) * kCamPartials;
-#pragma unroll
-      for (int k = 0; k < 13; ++k) acc[k] += fp[k];
-    }
-    const int i0 = 8 * v.item_begin[S.tile_begin], i1 = 8 * v.item_begin[S.tile_begin + nt];
-    for (int i = i0 + start; i < i1; i += stride) acc[12] += v.item_kappa[i];
-  }
-  if (mask & PULSAR_GRAD_BG) {
-    const float* rows = v.tile_bg + (size_t)S.tile_begin * 8 * C;
-    for (int64_t t = start; t < 8 * nt; t += stride) {
-#pragma unroll
-      for (int c = 0; c < 32; ++c)
-        if (c < C) acc[13 + c] += rows[t * C + c];
-    }
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 0; k < kRedValues; ++k) {
-    const float x = warp_sum(acc[k]);
-    if (lane == 0) red[warp][k] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < kRedValues) {
-    float x = 0.0f;
-    for (int w = 0; w < 8; ++w) x += red[w][threadIdx.x];
-    v.red_part[((size_t)blockIdx.x * kRedParts + part) * kRedValues + threadIdx.x] = x;
-  }
-}
-
-// Second stage, one CTA per scene: sums the first stage's partials in a fixed
-// order, then chains the camera sums through the pixel pitch kappa = s / (W f)
-// and the Gram-Schmidt map of the 6D rotation.
-__global__ void __launch_bounds__(64) camera_reduce_kernel(WsView v, uint32_t mask) {
+// Second stage, run by the scene's last first-stage CTA to finish: sums the
+// first stage's partials in a fixed order, then chains the camera sums through
+// the pixel pitch kappa = s / (W f) and the Gram-Schmidt map of the 6D rotation.
+__device__ __forceinline__ void camera_finish(const WsView& v, uint32_t mask, int scene) {
   __shared__ float tot[kRedValues];
   __shared__ float gcam[11];
-  const SceneDev& S = v.scenes[blockIdx.x];
+  const SceneDev& S = v.scenes[scene];
   const int C = S.n_channels;
   if (threadIdx.x < kRedValues) {
     float x = 0.0f;
     for (int p = 0; p < kRedParts; ++p)
-      x += v.red_part[((size_t)blockIdx.x * kRedParts + p) * kRedValues + threadIdx.x];
+      x += __ldcg(v.red_part + ((size_t)scene * kRedParts + p) * kRedValues + threadIdx.x);
     tot[threadIdx.x] = x;
     if ((mask & PULSAR_GRAD_BG) && threadIdx.x >= 13 && threadIdx.x < 13 + C) {
       if (S.flags & PULSAR_FLAG_ACCUMULATE)
@@ -423,6 +379,62 @@ __global__ void __launch_bounds__(64) camera_reduce_kernel(WsView v, uint32_t ma
   }
 }
 
+// First stage of the camera and background reduction: CTA (scene, part)
+// sums its share of the per-block camera partials, the per-(item, pixel
+// block) pitch partials and the per-(tile, pixel block) background partials.
+__global__ void __launch_bounds__(256) camera_partials_kernel(WsView v, uint32_t mask) {
+  __shared__ float red[8][kRedValues];
+  const SceneDev& S = v.scenes[blockIdx.x];
+  const int part = blockIdx.y;
+  const int C = S.n_channels;
+  const int64_t nt = (int64_t)S.tiles_x * S.tiles_y;
+  const int stride = kRedParts * blockDim.x;
+  const int start = part * blockDim.x + threadIdx.x;
+  float acc[kRedValues];
+#pragma unroll
+  for (int k = 0; k < kRedValues; ++k) acc[k] = 0.0f;
+  if (mask & PULSAR_GRAD_CAM) {
+    for (int b = start; b < S.fin_blocks; b += stride) {
+      const float* fp = v.fin_part + (size_t)(S.fin_block_begin + b) * kCamPartials;
+#pragma unroll
+      for (int k = 0; k < 13; ++k) acc[k] += fp[k];
+    }
+    const int i0 = 8 * v.item_begin[S.tile_begin], i1 = 8 * v.item_begin[S.tile_begin + nt];
+    for (int i = i0 + start; i < i1; i += stride) acc[12] += v.item_kappa[i];
+  }
+  if (mask & PULSAR_GRAD_BG) {
+    const float* rows = v.tile_bg + (size_t)S.tile_begin * 8 * C;
+    for (int64_t t = start; t < 8 * nt; t += stride) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < C) acc[13 + c] += rows[t * C + c];
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < kRedValues; ++k) {
+    const float x = warp_sum(acc[k]);
+    if (lane == 0) red[warp][k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < kRedValues) {
+    float x = 0.0f;
+    for (int w = 0; w < 8; ++w) x += red[w][threadIdx.x];
+    v.red_part[((size_t)blockIdx.x * kRedParts + part) * kRedValues + threadIdx.x] = x;
+  }
+  // the scene's last CTA to finish sums every CTA's partials (its own stores
+  // are made visible before it counts itself)
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(v.cam_done + blockIdx.x, 1) == kRedParts - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  camera_finish(v, mask, blockIdx.x);
+  if (threadIdx.x == 0) v.cam_done[blockIdx.x] = 0;   // ready for the next backward pass
+}
+
 static_assert(sizeof(SetupPack<kMaxScenes>) + sizeof(WsView) <= 32000,
               "scene descriptors must fit the kernel parameter space");
 
@@ -473,7 +485,6 @@ cudaError_t launch_finalize(const WsView& v, uint32_t mask, cudaStream_t st) {
 cudaError_t launch_camera_reduce(const WsView& v, uint32_t mask, cudaStream_t st) {
   if (mask & (PULSAR_GRAD_CAM | PULSAR_GRAD_BG)) {
     camera_partials_kernel<<<dim3(v.n_scenes, kRedParts), 256, 0, st>>>(v, mask);
-    camera_reduce_kernel<<<v.n_scenes, 64, 0, st>>>(v, mask);
   }
   return cudaGetLastError();
 }

@@ -161,6 +161,7 @@ struct WsView {
   float* pg_feat;            // paper gradients: per sphere x C, dL/df before averaging
   float* fin_part;           // per finalize block: camera partials
   float* red_part;           // per scene x 64: first-stage camera / background sums (45)
+  int32_t* cam_done;         // per scene: first-stage reduction CTAs finished (the last one finishes the sum)
 };
 
 // ----------------------------------------------------------------------------
