@@ -72,6 +72,7 @@ __global__ void setup_kernel(WsView v, const SetupPack<N> pk) {
     v.hdr->n_sort = (int32_t)pk.n_spheres;
     v.hdr->overflow = 0;
     v.hdr->timeout = 0;
+    v.hdr->count_done = 0;
   }
 }
 

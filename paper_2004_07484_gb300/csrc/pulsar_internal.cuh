@@ -92,7 +92,8 @@ struct WsHeader {
   int32_t timeout;           // a bounded device loop gave up
   int32_t n_items;           // (tile, segment) work items of the render passes
   int32_t work_next;         // next work unit of a persistent render launch
-  int32_t pad_[7];
+  int32_t count_done;        // tile-count CTAs finished (the last one scans their sums)
+  int32_t pad_[6];
 };
 
 // One work item of the render passes: a segment [b0, b1) of a tile's list.

@@ -217,9 +217,45 @@ __device__ __forceinline__ uint32_t tile_count(const float4& r1, bool visible) {
   return (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
 }
 
-// Sum of the tile counts of each 2048-key tile of the depth-sorted spheres.
+// Exclusive scan of the n_blocks tile-count sums (CTA of NT threads); records
+// the pair total and the overflow flag.
+template <int NT>
+__device__ __forceinline__ void scan_block_sums(const WsView& v, int n_blocks, uint32_t* warp_tot) {
+  unsigned long long carry = 0;
+  for (int b0 = 0; b0 < n_blocks; b0 += NT) {
+    int b = b0 + threadIdx.x;
+    uint32_t x = b < n_blocks ? __ldcg(v.block_sums + b) : 0u;
+    uint32_t tot;
+    uint32_t ex = block_exclusive_scan<NT>(x, warp_tot, tot);
+    if (b < n_blocks) v.block_sums[b] = (uint32_t)(carry + ex);
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    long long total = (long long)carry;
+    v.hdr->pairs_needed = total;
+    bool over = total > v.capacity;
+    v.hdr->overflow = over ? 1 : 0;
+    v.hdr->n_pairs = over ? 0 : (int32_t)total;
+  }
+}
+
+// Clears every tile's list range and merge counters (the kernel's threads in
+// a grid-stride loop); the tile-key sort's range pass then fills the ranges of
+// the tiles that have pairs.
+__device__ __forceinline__ void clear_tile_state(const WsView& v) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < v.n_tiles; t += stride) {
+    v.ranges[t] = make_int2(0, 0);
+    reinterpret_cast<int4*>(v.tile_done)[2 * t] = make_int4(0, 0, 0, 0);
+    reinterpret_cast<int4*>(v.tile_done)[2 * t + 1] = make_int4(0, 0, 0, 0);
+  }
+}
+
+// Sum of the tile counts of each kSortTile-key tile of the depth-sorted
+// spheres; also clears the per-tile state.
 __global__ void __launch_bounds__(kThreads) count_reduce(WsView v) {
   __shared__ uint32_t warp_tot[33];
+  clear_tile_state(v);
   const int n = (int)v.n_spheres;
   const int base = blockIdx.x * kSortTile;
   // every load of the thread's spheres in flight at once
@@ -240,27 +276,25 @@ __global__ void __launch_bounds__(kThreads) count_reduce(WsView v) {
   uint32_t tot;
   block_exclusive_scan<kThreads>(s, warp_tot, tot);
   if (threadIdx.x == 0) v.block_sums[blockIdx.x] = tot;
+  // the last CTA to finish scans every CTA's sum (its own store is made
+  // visible before it counts itself)
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&v.hdr->count_done, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  scan_block_sums<kThreads>(v, (int)gridDim.x, warp_tot);
+  if (threadIdx.x == 0) v.hdr->count_done = 0;   // ready for the next binning
 }
 
-// Exclusive scan of the block sums; records the pair total and the overflow flag.
+// The same scan as its own kernel, for a binning with no sphere (and so no
+// tile-count CTA): records a pair total of zero.
 __global__ void __launch_bounds__(1024) count_scan(WsView v, int n_blocks) {
   __shared__ uint32_t warp_tot[33];
-  unsigned long long carry = 0;
-  for (int b0 = 0; b0 < n_blocks; b0 += 1024) {
-    int b = b0 + threadIdx.x;
-    uint32_t x = b < n_blocks ? v.block_sums[b] : 0u;
-    uint32_t tot;
-    uint32_t ex = block_exclusive_scan<1024>(x, warp_tot, tot);
-    if (b < n_blocks) v.block_sums[b] = (uint32_t)(carry + ex);
-    carry += tot;
-  }
-  if (threadIdx.x == 0) {
-    long long total = (long long)carry;
-    v.hdr->pairs_needed = total;
-    bool over = total > v.capacity;
-    v.hdr->overflow = over ? 1 : 0;
-    v.hdr->n_pairs = over ? 0 : (int32_t)total;
-  }
+  clear_tile_state(v);
+  scan_block_sums<1024>(v, n_blocks, warp_tot);
 }
 
 // Emits the (tile, sphere) pairs of each depth-sorted sphere at its scanned
@@ -438,8 +472,10 @@ cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st) {
   }
   // the sorted spheres are in buffer v.sort_buf (the parity of the pass count)
   const int nb = (M + kSortTile - 1) / kSortTile;
-  if (nb > 0) count_reduce<<<nb, kThreads, 0, st>>>(v);
-  count_scan<<<1, 1024, 0, st>>>(v, nb);
+  if (nb > 0)
+    count_reduce<<<nb, kThreads, 0, st>>>(v);   // its last CTA scans the sums
+  else
+    count_scan<<<1, 1024, 0, st>>>(v, 0);
   if (nb > 0) emit_pairs<<<nb, kThreads, 0, st>>>(v);
   // 4. pairs by tile
   int pbuf = 0;
@@ -449,18 +485,14 @@ cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st) {
     e = radix_sort<kRadixBits>(v, k, val, &v.hdr->n_pairs, 0, (int)v.capacity, tile_bits, pbuf, st);
     if (e != cudaSuccess) return e;
   }
-  // 5. ranges
-  e = cudaMemsetAsync(v.ranges, 0, sizeof(int2) * (size_t)v.n_tiles, st);
-  if (e != cudaSuccess) return e;
+  // 5. ranges (cleared with the tile counts)
   if (v.capacity > 0) {
     const int64_t want = (v.capacity + kThreads - 1) / kThreads;
     const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
     tile_ranges<<<blocks, kThreads, 0, st>>>(v, pbuf);
   }
-  // 6. work items of the render passes (and cleared merge counters)
+  // 6. work items of the render passes (the merge counters were cleared with the tile counts)
   if (v.n_tiles > 0) {
-    e = cudaMemsetAsync(v.tile_done, 0, sizeof(int32_t) * 8 * (size_t)v.n_tiles, st);
-    if (e != cudaSuccess) return e;
     make_items<<<1, 1024, 0, st>>>(v);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
