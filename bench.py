@@ -791,18 +791,19 @@ def main():
         """One pass of the hot path through the C ABI; marks (three events), when
         given, are recorded after project, bin and the forward render."""
         s = settings(store, paper_stop)
+        cs = torch.cuda.current_stream(dev)   # the launch stream (a capture stream inside a graph capture)
         fr = Frame(s, sc.n_spheres, capacity, dev)
         sa = scene_args(t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"])
-        _lib.project(fr.params, sa, fr.ws.data_ptr(), fr.ws_bytes, stream.cuda_stream)
+        _lib.project(fr.params, sa, fr.ws.data_ptr(), fr.ws_bytes, cs.cuda_stream)
         if marks:
-            marks[0].record(stream)
-        _lib.bin(fr.params, fr.ws.data_ptr(), fr.ws_bytes, stream.cuda_stream)
+            marks[0].record(cs)
+        _lib.bin(fr.params, fr.ws.data_ptr(), fr.ws_bytes, cs.cuda_stream)
         if marks:
-            marks[1].record(stream)
+            marks[1].record(cs)
         image = torch.empty((H, W, C), dtype=torch.float32, device=dev)
         log_norm = torch.empty((H, W), dtype=torch.float32, device=dev)
         _lib.render_fwd(fr.params, sa, fr.ws.data_ptr(), fr.ws_bytes, image.data_ptr(), log_norm.data_ptr(),
-                        None, None, None, stream.cuda_stream)
+                        None, None, None, cs.cuda_stream)
         if marks:
             marks[2].record(stream)
         grads = backward_frame(fr, t["pos"], t["feat"], t["rad"], t["opa"], t["cam"], t["bg"], image,
@@ -856,6 +857,26 @@ def main():
         ms_ps, _ = timed_steps(True, max(3, args.steps // 2), True)
         t_wall = time.perf_counter() - t_wall
     gc.enable()
+    # the same step (store mode) as a CUDA-graph replay: the four C-ABI calls captured once
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        step(True)
+    stream.wait_stream(side)
+    step_graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(step_graph):
+        step(True)
+    ms_graph = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        step_graph.replay()
+        g1.record(stream)
+        ms_graph.append((g0, g1))
+    torch.cuda.synchronize()
+    ms_graph = [a.elapsed_time(b) for a, b in ms_graph]
+    graph_total_ms = max_over_ranks(sum(ms_graph), world, dev)
     st, _ = _lib.read_status(fr_last.ws.data_ptr(), fr_last.ws_bytes, stream.cuda_stream)
     assert st == _lib.OK, f"pair list overflow during timing (status {st})"
     if world > 1:
@@ -970,6 +991,9 @@ def main():
                        "l2": "flushed between steps (256 MB write, untimed)",
                        "hit_lists": "recompute" if args.recompute else "store"},
             "recompute_ms_per_step" if not args.recompute else "store_ms_per_step": statistics.mean(ms_rec),
+            "graph": {"value": job_throughput(world, args.steps, graph_total_ms), "unit": UNIT,
+                      "ms_per_step": graph_total_ms / args.steps,
+                      "what": "the same step (store mode) as a CUDA-graph replay of the four C-ABI calls"},
             "paper_stop": {"value": job_throughput(world, len(ms_ps), ps_total_ms),
                            "unit": UNIT, "ms_per_step": statistics.mean(ms_ps),
                            "what": "the paper's 1% early termination on top of the exact one "
