@@ -47,7 +47,7 @@ N_SMS = 152
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only
 # for the kernel sources with this digest, reported as null otherwise.
 FWD_KERNEL_SOURCES = ("render_fwd.cu", "render_common.cuh", "pulsar_internal.cuh")
-FWD_TRAFFIC = {"sha256": "6d43b312479360f8895f8e4692504a879b87f83cb4609659b84655ea7a041dc3", "bytes": 214258944 + 8154880}
+FWD_TRAFFIC = {"sha256": "d35475ad929c0af0a20c2fd5b069df4fe71e67d473c9dcbe37a21dc9f24731e2", "bytes": 239572736 + 19182848}
 
 
 def fwd_kernel_digest() -> str:
