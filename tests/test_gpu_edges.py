@@ -122,6 +122,41 @@ def test_decisions_are_deterministic(orc):
     assert np.array_equal(ia[:n], ib[:n])
 
 
+def test_repeated_calls_on_one_workspace(orc):
+    """Binning twice after one projection, and two backward passes of one
+    forward pass, give the single calls' results: the counters the kernels'
+    last CTAs use to finish a scan or a reduction are ready again after each
+    call.  (The single calls' parity with the oracle is tested elsewhere.)"""
+    import torch
+    from paper_2004_07484_gb300 import _lib
+    from paper_2004_07484_gb300.renderer import scene_args
+    sc = S.config_scene(1, n=20000, res=128)
+    gpu = gpu_forward(sc)
+    fr, d = gpu["frame"], gpu["dev"]
+    ranges0, ids0 = gpu_tile_lists(fr)
+    stream = torch.cuda.current_stream().cuda_stream
+    _lib.bin(fr.params, fr.ws.data_ptr(), fr.ws_bytes, stream)   # again, on the same projection
+    ranges1, ids1 = gpu_tile_lists(fr)
+    assert np.array_equal(ranges0, ranges1)
+    n = int(ranges0[:, 1].max())
+    assert np.array_equal(ids0[:n], ids1[:n])
+    image = torch.empty_like(gpu["image"])
+    log_norm = torch.empty_like(gpu["log_norm"])
+    sa = scene_args(d["pos"], d["feat"], d["rad"], d["opa"], d["cam"], d["bg"])
+    _lib.render_fwd(fr.params, sa, fr.ws.data_ptr(), fr.ws_bytes, image.data_ptr(), log_norm.data_ptr(),
+                    None, None, None, stream)
+    torch.cuda.synchronize()
+    assert torch.equal(image, gpu["image"]) or (image - gpu["image"]).abs().max().item() <= 1e-6
+    G = S.grad_image(12, sc.height, sc.width, sc.n_channels)
+    g1 = gpu_backward(gpu, G)
+    g2 = gpu_backward(gpu, G)
+    for k in g1:
+        if g1[k] is None:
+            continue
+        scale = max(np.abs(g1[k]).max(), 1e-30)
+        assert np.abs(g1[k] - g2[k]).max() <= 1e-5 * scale, k   # float atomics may add in another order
+
+
 def test_module_autograd_matches_oracle(orc):
     import torch
     from paper_2004_07484_gb300 import Renderer
