@@ -3,13 +3,14 @@
 // A 16 x 16 screen tile is rendered as eight 8 x 4 pixel blocks, one warp
 // each, and each thread renders one pixel, so parallelism is over pixels as
 // the paper prescribes (Sec. 3.2, App. B).  Every warp is its own CTA and
-// walks one segment of its tile's depth-ordered sphere list independently:
-// it stages 32 list entries at a time in shared memory, marks those whose
-// pixel rectangle overlaps its block (a ballot over the lanes) and gathers
-// only their value records and features (App. B, Step 1: block-wise
-// intersection search with cooperative filtering).  A
-// warp with few candidates therefore never waits for a busy neighbour and
-// frees its slot as soon as it is done.
+// walks the block list of one segment of its tile's depth-ordered sphere
+// list (built by the binning pass: the spheres that hit at least one of the
+// block's pixels, each with its 32-bit hit mask; App. B, Step 1's
+// intersection search done once for all passes): it stages 32 entries at a
+// time in shared memory with their draw records, value records and features,
+// and each lane walks the entries that hit its pixel.  A warp with few
+// entries never waits for a busy neighbour and frees its slot as soon as it
+// is done.
 #pragma once
 
 #include "pulsar_internal.cuh"
