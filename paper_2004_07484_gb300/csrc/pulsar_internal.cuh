@@ -20,8 +20,8 @@ namespace pulsar {
 constexpr int kThreads = 256;        // threads per CTA for the per-tile kernels (16 x 16 pixels)
 constexpr int kTile = 16;            // tile edge in pixels
 constexpr int kChunk = 256;          // spheres staged in shared memory per round
-constexpr int kSortItems = 4;        // keys per thread in one radix-sort tile
-constexpr int kSortTile = kThreads * kSortItems;   // 1024 keys per radix-sort CTA
+constexpr int kSortItems = 8;        // keys per thread in one radix-sort tile
+constexpr int kSortTile = kThreads * kSortItems;   // 2048 keys per radix-sort CTA
 constexpr int kRadixBits = 8;              // digit bits of the tile-key sort
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kDepthRadixBits = 9;         // digit bits of the depth-key sort
