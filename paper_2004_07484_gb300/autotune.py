@@ -22,7 +22,7 @@ import torch
 from . import _lib
 from .renderer import RenderSettings, backward_batch, forward_batch
 
-SEGMENTS = (512, 1024, 2048, 4096, 8192)
+SEGMENTS = (512, 1024, 2048, 2560, 3072, 4096, 8192)
 FORMS = (False, True)          # persistent
 CAPACITY_MARGIN = 1.25
 

@@ -248,8 +248,8 @@ def test_1m_spheres_1024_sampled(orc):
 _bench_ref = {}
 
 
-@pytest.mark.parametrize("segment,persistent", [(2048, False), (2048, True), (4096, True)],
-                         ids=["seg2048", "seg2048-persistent", "seg4096-persistent"])
+@pytest.mark.parametrize("segment,persistent", [(2048, False), (2048, True), (3072, False), (4096, True)],
+                         ids=["seg2048", "seg2048-persistent", "seg3072", "seg4096-persistent"])
 def test_1m_spheres_1024_bench_schedules(orc, segment, persistent):
     """The 1M-sphere workload in the launch configurations the benchmark's
     autotuner picks between: sampled pixels bit-exact in their tracked hits and
