@@ -192,9 +192,10 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(WsView v, ui
     const float4 g = v.gacc[i];
     const float* p = S.pos + 3 * li;
     const float r = S.rad[li];
-    Projected pr = project_sphere(S.rows, S.cam, S.kappa, p[0], p[1], p[2], r, S.width, S.height,
-                                  S.znear, S.zfar, !(S.flags & PULSAR_FLAG_NO_MIN_SIZE),
-                                  (S.flags & PULSAR_FLAG_ORTHOGRAPHIC) != 0);
+    // the centre and radius exactly as the projection formed them (no rectangle needed)
+    Projected pr;
+    sphere_centre_radius(S.rows, S.cam, S.kappa, p[0], p[1], p[2], r, !(S.flags & PULSAR_FLAG_NO_MIN_SIZE),
+                         (S.flags & PULSAR_FLAG_ORTHOGRAPHIC) != 0, pr);
     float gc0 = g.x, gc1 = g.y, gc2 = g.z;
     float gk = 0.0f, grad_r = 0.0f;
     const bool clamped = pr.R != r;

@@ -232,11 +232,11 @@ __device__ __forceinline__ void axis_range_ortho(float cx, float R, float kappa,
 
 // Step 0 for one sphere: camera-space centre, effective radius (one-pixel
 // minimum size), culling, rectangle and sort key.
-__device__ __forceinline__ Projected project_sphere(const float* B, const float* cam, float kappa,
-                                                    float px, float py, float pz, float r,
-                                                    int width, int height, float znear, float zfar,
-                                                    bool min_size, bool ortho) {
-  Projected o;
+// The camera-space centre and the radius after the minimum-size rule: the
+// first part of project_sphere, for passes that need no rectangle.
+__device__ __forceinline__ void sphere_centre_radius(const float* B, const float* cam, float kappa,
+                                                     float px, float py, float pz, float r,
+                                                     bool min_size, bool ortho, Projected& o) {
   float dx = __fsub_rn(px, cam[0]), dy = __fsub_rn(py, cam[1]), dz = __fsub_rn(pz, cam[2]);
   o.cx = __fmaf_rn(B[0], dx, __fmaf_rn(B[1], dy, __fmul_rn(B[2], dz)));
   o.cy = __fmaf_rn(B[3], dx, __fmaf_rn(B[4], dy, __fmul_rn(B[5], dz)));
@@ -253,6 +253,15 @@ __device__ __forceinline__ Projected project_sphere(const float* B, const float*
     if (rmin > r) R = rmin;
   }
   o.R = R;
+}
+
+__device__ __forceinline__ Projected project_sphere(const float* B, const float* cam, float kappa,
+                                                    float px, float py, float pz, float r,
+                                                    int width, int height, float znear, float zfar,
+                                                    bool min_size, bool ortho) {
+  Projected o;
+  sphere_centre_radius(B, cam, kappa, px, py, pz, r, min_size, ortho, o);
+  const float R = o.R;
   o.R2 = __fmul_rn(R, R);
   o.key = __int_as_float(0x7f800000);
   o.visible = false;
