@@ -179,7 +179,8 @@ WsView make_view(void* ws, const Layout& L, const pulsar_params* ps, int n) {
   v.fin_blocks = L.fin_blocks;
   v.n_channels = ps[0].n_channels;
   v.n_track = ps[0].n_track;
-  v.pair_buf = ((L.tile_bits + kRadixBits - 1) / kRadixBits) & 1;
+  const int tile_rb = tile_radix_bits(L.tile_bits);
+  v.pair_buf = ((L.tile_bits + tile_rb - 1) / tile_rb) & 1;
   v.segment = L.segment;
   v.max_items = (int32_t)L.max_items;
   v.part_fields = L.part_fields;

@@ -24,6 +24,10 @@ constexpr int kSortItems = 8;        // keys per thread in one radix-sort tile
 constexpr int kSortTile = kThreads * kSortItems;   // 2048 keys per radix-sort CTA
 constexpr int kRadixBits = 8;              // digit bits of the tile-key sort
 constexpr int kRadix = 1 << kRadixBits;
+// Digit bits of the tile-key sort for a key of `bits` bits: 6 where that
+// takes no more passes than 8 (9 to 12 bits: two passes either way, and
+// 6-bit digits leave longer runs of equal digits to scatter), else 8.
+inline int tile_radix_bits(int bits) { return bits > 8 && bits <= 12 ? 6 : kRadixBits; }
 constexpr int kDepthRadixBits = 9;         // digit bits of the depth-key sort
 constexpr int kDepthRadix = 1 << kDepthRadixBits;
 constexpr int kMaxScenes = 64;

@@ -4,7 +4,7 @@
 //      batch (visible keys lie between the planes), 9 bits per pass,
 //   2. exclusive scan of each sorted sphere's tile count,
 //   3. emission of one (tile, sphere) pair per overlapped tile, in depth order,
-//   4. stable LSD radix sort of the pairs by tile,
+//   4. stable LSD radix sort of the pairs by tile (6- or 8-bit digits),
 //   5. per-tile [begin, end) ranges,
 //   6. work items (list segments) in decreasing length,
 //   7. block lists: per segment and 8 x 4 pixel block, the hitting spheres
@@ -111,8 +111,10 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
     int n_host, int shift, uint32_t mask, const uint32_t* __restrict__ hist,
     const uint32_t* __restrict__ row_tot, int stride) {
   constexpr int R = 1 << RB;
-  constexpr int DPT = R / kThreads;   // digits per thread in the per-digit steps
-  static_assert(DPT >= 1 && DPT * kThreads == R, "digits a multiple of the threads");
+  // digits per thread in the per-digit steps (with fewer digits than
+  // threads, thread t takes digit t and the others none)
+  constexpr int DPT = R >= kThreads ? R / kThreads : 1;
+  static_assert(R < kThreads || DPT * kThreads == R, "digits a multiple of the threads");
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
   __shared__ uint32_t warp_cnt[kThreads / 32][R];
@@ -136,8 +138,8 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
 #pragma unroll
   for (int q = 0; q < DPT; ++q) {
     const int d = threadIdx.x * DPT + q;
-    rt[q] = row_tot[d];
-    hcta[q] = hist[d * stride + blockIdx.x];
+    rt[q] = d < R ? row_tot[d] : 0u;
+    hcta[q] = d < R ? hist[d * stride + blockIdx.x] : 0u;
   }
   for (int w = 0; w < kThreads / 32; ++w)
     for (int i = threadIdx.x; i < R; i += kThreads) warp_cnt[w][i] = 0;
@@ -165,11 +167,12 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
     for (int q = 0; q < DPT; ++q) {
       const int d = threadIdx.x * DPT + q;
       uint32_t t = 0;
-      for (int w = 0; w < kThreads / 32; ++w) {
-        uint32_t c = warp_cnt[w][d];
-        warp_cnt[w][d] = t;
-        t += c;
-      }
+      if (d < R)
+        for (int w = 0; w < kThreads / 32; ++w) {
+          uint32_t c = warp_cnt[w][d];
+          warp_cnt[w][d] = t;
+          t += c;
+        }
       tot[q] = t;
       sum += t;
       rsum += rt[q];
@@ -181,8 +184,10 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
       const int d = threadIdx.x * DPT + q;
-      digit_local[d] = ex;
-      digit_global[d] = base_d + hcta[q];
+      if (d < R) {
+        digit_local[d] = ex;
+        digit_global[d] = base_d + hcta[q];
+      }
       ex += tot[q];
       base_d += rt[q];
     }
@@ -482,7 +487,9 @@ cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st) {
   if (v.capacity > 0) {
     uint32_t* k[2] = {v.pkey[0], v.pkey[1]};
     uint32_t* val[2] = {v.pval[0], v.pval[1]};
-    e = radix_sort<kRadixBits>(v, k, val, &v.hdr->n_pairs, 0, (int)v.capacity, tile_bits, pbuf, st);
+    e = tile_radix_bits(tile_bits) == 6
+            ? radix_sort<6>(v, k, val, &v.hdr->n_pairs, 0, (int)v.capacity, tile_bits, pbuf, st)
+            : radix_sort<kRadixBits>(v, k, val, &v.hdr->n_pairs, 0, (int)v.capacity, tile_bits, pbuf, st);
     if (e != cudaSuccess) return e;
   }
   // 5. ranges (cleared with the tile counts)
