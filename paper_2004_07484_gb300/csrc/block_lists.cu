@@ -86,6 +86,8 @@ constexpr int kListWarps = 2;
 __global__ void __launch_bounds__(32 * kListWarps) block_lists_kernel(const WsView v,
                                                                        const uint32_t* __restrict__ keys,
                                                                        const uint32_t* __restrict__ list) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ BlockListWarp warps[kListWarps];
   constexpr int kCtasPerItem = kBlocksPerTile / kListWarps;
   const int rank = blockIdx.x / kCtasPerItem;   // longest items first
@@ -159,6 +161,8 @@ __device__ __forceinline__ uint32_t walk_cost(const WsView& v, uint32_t u) {
 }
 
 __global__ void __launch_bounds__(1024) order_units_kernel(const WsView v) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t bucket[kCostClasses];
   const uint32_t n = (uint32_t)v.hdr->n_items * kBlocksPerTile;
   if (threadIdx.x < kCostClasses) bucket[threadIdx.x] = 0u;
@@ -183,6 +187,8 @@ __global__ void __launch_bounds__(1024) order_units_kernel(const WsView v) {
 // made), counted through a warp bit-matrix transpose.  Run only when a
 // forward pass asks for n_tests.
 __global__ void __launch_bounds__(256) count_tests_kernel(const WsView v, const uint32_t* __restrict__ list) {
+  pdl_wait();
+  pdl_trigger();
   const int item = blockIdx.x;
   const int lane = threadIdx.x & 31;
   ItemCtx it;
@@ -212,16 +218,15 @@ __global__ void __launch_bounds__(256) count_tests_kernel(const WsView v, const 
 
 cudaError_t launch_block_lists(const WsView& v, cudaStream_t st) {
   if (v.max_items == 0) return cudaSuccess;
-  block_lists_kernel<<<(unsigned)v.max_items * (kBlocksPerTile / kListWarps), 32 * kListWarps, 0, st>>>(
-      v, v.pkey[v.pair_buf], v.pval[v.pair_buf]);
-  order_units_kernel<<<1, 1024, 0, st>>>(v);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(block_lists_kernel, dim3((unsigned)v.max_items * (kBlocksPerTile / kListWarps)),
+                             dim3(32 * kListWarps), 0, st, v, v.pkey[v.pair_buf], v.pval[v.pair_buf]);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(order_units_kernel, dim3(1), dim3(1024), 0, st, v);
 }
 
 cudaError_t launch_count_tests(const WsView& v, cudaStream_t st) {
   if (v.max_items == 0) return cudaSuccess;
-  count_tests_kernel<<<(unsigned)v.max_items, 256, 0, st>>>(v, v.pval[v.pair_buf]);
-  return cudaGetLastError();
+  return launch_pdl(count_tests_kernel, dim3((unsigned)v.max_items), dim3(256), 0, st, v, v.pval[v.pair_buf]);
 }
 
 }  // namespace pulsar

@@ -33,6 +33,8 @@ __device__ __forceinline__ void rows_from_rot6_f64(const float* a, double* B) {
 
 template <int N>
 __global__ void setup_kernel(WsView v, const SetupPack<N> pk) {
+  pdl_wait();
+  pdl_trigger();
   const int i = threadIdx.x;
   if (i < pk.n) {
     SceneDev d = pk.s[i];
@@ -73,12 +75,15 @@ __global__ void setup_kernel(WsView v, const SetupPack<N> pk) {
     v.hdr->overflow = 0;
     v.hdr->timeout = 0;
     v.hdr->count_done = 0;
+    v.hdr->work_next = 0;
   }
 }
 
 // One thread per sphere: draw record, sort key and value, and the scene-wide
 // maximum of |o| (used by the exact early-termination bound).
 __global__ void __launch_bounds__(kThreads) project_kernel(WsView v) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   const bool live = i < v.n_spheres;
   const int s = live ? scene_of_sphere(v.scenes, v.n_scenes, i) : 0;
@@ -148,6 +153,8 @@ __global__ void __launch_bounds__(kThreads) project_kernel(WsView v) {
 // backward pass adds into (dL/dc, dL/dR in the workspace; dL/do and dL/df in
 // the caller's buffers).
 __global__ void __launch_bounds__(kThreads) zero_grads_kernel(WsView v, uint32_t mask) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (i >= v.n_spheres) return;
   v.gacc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -178,6 +185,8 @@ __global__ void __launch_bounds__(kThreads) zero_grads_kernel(WsView v, uint32_t
 // dL/dr and the sphere's camera contribution (App. B: camera gradients are
 // gathered per sphere and reduced device-wide afterwards).
 __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(WsView v, uint32_t mask) {
+  pdl_wait();
+  pdl_trigger();
   const int blk = blockIdx.x;
   int s = 0;
   for (int k = 1; k < v.n_scenes; ++k)
@@ -385,6 +394,8 @@ __device__ __forceinline__ void camera_finish(const WsView& v, uint32_t mask, in
 // sums its share of the per-block camera partials, the per-(item, pixel
 // block) pitch partials and the per-(tile, pixel block) background partials.
 __global__ void __launch_bounds__(256) camera_partials_kernel(WsView v, uint32_t mask) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float red[8][kRedValues];
   const SceneDev& S = v.scenes[blockIdx.x];
   const int part = blockIdx.y;
@@ -447,8 +458,7 @@ cudaError_t setup_n(const WsView& v, const SceneDev* hs, int n, int full, cudaSt
   pk.full = full;
   pk.n_spheres = v.n_spheres;
   for (int i = 0; i < n; ++i) pk.s[i] = hs[i];
-  setup_kernel<N><<<1, N < 32 ? 32 : N, 0, st>>>(v, pk);
-  return cudaGetLastError();
+  return launch_pdl(setup_kernel<N>, dim3(1), dim3(N < 32 ? 32 : N), 0, st, v, pk);
 }
 
 }  // namespace
@@ -465,30 +475,27 @@ cudaError_t launch_setup(const WsView& v, const SceneDev* hs, int n, cudaStream_
 cudaError_t launch_project(const WsView& v, cudaStream_t st) {
   if (v.n_spheres == 0) return cudaSuccess;
   const int64_t blocks = (v.n_spheres + kThreads - 1) / kThreads;
-  project_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(v);
-  return cudaGetLastError();
+  return launch_pdl(project_kernel, dim3((unsigned)blocks), dim3(kThreads), 0, st, v);
 }
 
 cudaError_t launch_zero_grads(const WsView& v, uint32_t mask, cudaStream_t st) {
   if (v.n_spheres == 0) return cudaSuccess;
   const int64_t blocks = (v.n_spheres + kThreads - 1) / kThreads;
-  zero_grads_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(v, mask);
-  return cudaGetLastError();
+  return launch_pdl(zero_grads_kernel, dim3((unsigned)blocks), dim3(kThreads), 0, st, v, mask);
 }
 
 cudaError_t launch_finalize(const WsView& v, uint32_t mask, cudaStream_t st) {
   const uint32_t fin_mask = PULSAR_GRAD_POS | PULSAR_GRAD_RAD | PULSAR_GRAD_CAM |
                             (v.paper ? (PULSAR_GRAD_OPA | PULSAR_GRAD_FEAT) : 0u);
   if (v.fin_blocks > 0 && (mask & fin_mask))
-    finalize_kernel<<<v.fin_blocks, kFinalizeThreads, 0, st>>>(v, mask);
-  return cudaGetLastError();
+    return launch_pdl(finalize_kernel, dim3(v.fin_blocks), dim3(kFinalizeThreads), 0, st, v, mask);
+  return cudaSuccess;
 }
 
 cudaError_t launch_camera_reduce(const WsView& v, uint32_t mask, cudaStream_t st) {
-  if (mask & (PULSAR_GRAD_CAM | PULSAR_GRAD_BG)) {
-    camera_partials_kernel<<<dim3(v.n_scenes, kRedParts), 256, 0, st>>>(v, mask);
-  }
-  return cudaGetLastError();
+  if (mask & (PULSAR_GRAD_CAM | PULSAR_GRAD_BG))
+    return launch_pdl(camera_partials_kernel, dim3(v.n_scenes, kRedParts), dim3(256), 0, st, v, mask);
+  return cudaSuccess;
 }
 
 }  // namespace pulsar

@@ -17,6 +17,42 @@
 
 namespace pulsar {
 
+// Programmatic dependent launch (sm_90 and later).  The kernels of a step are
+// launched with programmatic stream serialisation: a kernel may be scheduled
+// while the one before it in the stream is still finishing, so its launch and
+// CTA rasterisation overlap that kernel's tail.  Every such kernel calls
+// pdl_wait() before it touches global memory; it returns once the previous
+// grid has completed and its writes are visible (at once when the kernel was
+// launched without the attribute).  pdl_trigger() lets the next kernel be
+// scheduled as soon as every CTA of this one has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launches `kernel` on `st` with programmatic stream serialisation (a plain
+// launch where the runtime does not offer it on that stream); the kernel must
+// start with pdl_wait().
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              const A&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+  if (e == cudaErrorNotSupported) {
+    (void)cudaGetLastError();
+    cfg.numAttrs = 0;
+    e = cudaLaunchKernelEx(&cfg, kernel, args...);
+  }
+  return e;
+}
+
 constexpr int kThreads = 256;        // threads per CTA for the per-tile kernels (16 x 16 pixels)
 constexpr int kTile = 16;            // tile edge in pixels
 constexpr int kChunk = 256;          // spheres staged in shared memory per round

@@ -276,6 +276,8 @@ __device__ __forceinline__ void bwd_unit(const WsView& v, uint32_t mask, int w, 
 // units from the workspace counter.
 template <int CMAX, bool CHAIN>
 __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v, uint32_t mask) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageBuf<CMAX, kBwdBuffers>& sb = *reinterpret_cast<StageBuf<CMAX, kBwdBuffers>*>(smem_raw);
   if (!v.persistent) {
@@ -285,7 +287,10 @@ __global__ void __launch_bounds__(32, 16) render_bwd_kernel(const WsView v, uint
   const int n_units = v.hdr->n_items * kBlocksPerTile;
   for (;;) {
     const int w = next_unit(v);
-    if (w >= n_units) break;
+    if (w >= n_units) {
+      done_units(v, w, n_units);
+      break;
+    }
     bwd_unit<CMAX, CHAIN>(v, mask, w, sb);
     __syncwarp();
   }
@@ -301,11 +306,8 @@ cudaError_t launch_bwd_t(const WsView& v, uint32_t mask, cudaStream_t st) {
     const unsigned slots = resident_slots(kern, 32, smem);
     if (slots == 0) return cudaErrorLaunchOutOfResources;
     if (slots < grid) grid = slots;
-    cudaError_t e = cudaMemsetAsync(&v.hdr->work_next, 0, sizeof(int32_t), st);
-    if (e != cudaSuccess) return e;
   }
-  kern<<<grid, 32, smem, st>>>(v, mask);
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3(grid), dim3(32), smem, st, v, mask);
 }
 
 }  // namespace

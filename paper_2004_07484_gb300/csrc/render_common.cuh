@@ -75,6 +75,14 @@ __device__ __forceinline__ int next_unit(const WsView& v) {
   return __shfl_sync(0xffffffffu, w, 0);
 }
 
+// A persistent CTA's fetch past the last unit.  Every CTA of the launch makes
+// exactly one such fetch, drawing n_units .. n_units + gridDim.x - 1; the CTA
+// that draws the largest knows every other CTA has fetched for the last time
+// and resets the counter for the next persistent launch.
+__device__ __forceinline__ void done_units(const WsView& v, int w, int n_units) {
+  if ((threadIdx.x & 31) == 0 && w == n_units + (int)gridDim.x - 1) v.hdr->work_next = 0;
+}
+
 // Resident one-warp CTAs of a kernel on the current device: the grid of a
 // persistent launch.
 template <typename Kernel>

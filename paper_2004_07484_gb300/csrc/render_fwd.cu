@@ -379,6 +379,8 @@ __device__ __forceinline__ void traverse_unit(const WsView& v, int w, StageBuf<C
 // units from the workspace counter.
 template <int KMAX, int CMAX, bool BLEND, bool CHAIN>
 __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v, int persistent) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StageBuf<CMAX>& sb = *reinterpret_cast<StageBuf<CMAX>*>(smem_raw);
   if (!persistent) {
@@ -388,7 +390,10 @@ __global__ void __launch_bounds__(32, 16) traverse_kernel(const WsView v, int pe
   const int n_units = v.hdr->n_items * kBlocksPerTile;
   for (;;) {
     const int w = next_unit(v);
-    if (w >= n_units) break;
+    if (w >= n_units) {
+      done_units(v, w, n_units);
+      break;
+    }
     traverse_unit<KMAX, CMAX, BLEND, CHAIN>(v, w, sb);
     __syncwarp();
   }
@@ -404,11 +409,8 @@ cudaError_t launch_t(const WsView& v, cudaStream_t st) {
     const unsigned slots = resident_slots(kern, 32, smem);
     if (slots == 0) return cudaErrorLaunchOutOfResources;
     if (slots < grid) grid = slots;
-    cudaError_t e = cudaMemsetAsync(&v.hdr->work_next, 0, sizeof(int32_t), st);
-    if (e != cudaSuccess) return e;
   }
-  kern<<<grid, 32, smem, st>>>(v, v.persistent);
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3(grid), dim3(32), smem, st, v, v.persistent);
 }
 
 template <int KMAX, bool BLEND>

@@ -35,6 +35,8 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __rest
                                                           const int32_t* n_dev, int n_host, int shift,
                                                           uint32_t mask, uint32_t* __restrict__ hist,
                                                           int stride) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int R = 1 << RB;
   __shared__ uint32_t h[R];
   const int n = read_count(n_dev, n_host);
@@ -73,6 +75,8 @@ constexpr int kScanPer = 8;
 __global__ void __launch_bounds__(kThreads) scan_rows(uint32_t* __restrict__ data,
                                                       uint32_t* __restrict__ row_tot,
                                                       const int32_t* n_dev, int n_host, int stride) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t warp_tot[33];
   const int n = read_count(n_dev, n_host);
   const int cols = (n + kSortTile - 1) / kSortTile;
@@ -110,6 +114,8 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int32_t* n_dev,
     int n_host, int shift, uint32_t mask, const uint32_t* __restrict__ hist,
     const uint32_t* __restrict__ row_tot, int stride) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int R = 1 << RB;
   // digits per thread in the per-digit steps (with fewer digits than
   // threads, thread t takes digit t and the others none)
@@ -259,6 +265,8 @@ __device__ __forceinline__ void clear_tile_state(const WsView& v) {
 // Sum of the tile counts of each kSortTile-key tile of the depth-sorted
 // spheres; also clears the per-tile state.
 __global__ void __launch_bounds__(kThreads) count_reduce(WsView v) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t warp_tot[33];
   clear_tile_state(v);
   const int n = (int)v.n_spheres;
@@ -297,6 +305,8 @@ __global__ void __launch_bounds__(kThreads) count_reduce(WsView v) {
 // The same scan as its own kernel, for a binning with no sphere (and so no
 // tile-count CTA): records a pair total of zero.
 __global__ void __launch_bounds__(1024) count_scan(WsView v, int n_blocks) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t warp_tot[33];
   clear_tile_state(v);
   scan_block_sums<1024>(v, n_blocks, warp_tot);
@@ -308,6 +318,8 @@ __global__ void __launch_bounds__(1024) count_scan(WsView v, int n_blocks) {
 // sphere's rectangle meets (bit 2 r + c for block column c, row r).  The sort
 // by tile reads only the low bits, so the block set rides along.
 __global__ void __launch_bounds__(kThreads) emit_pairs(WsView v) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t warp_tot[33];
   const int n = (int)v.n_spheres;
   if (v.hdr->overflow) return;
@@ -363,6 +375,8 @@ __global__ void __launch_bounds__(kThreads) emit_pairs(WsView v) {
 
 // Tile ranges from the tile-sorted pairs (ranges are zeroed beforehand).
 __global__ void __launch_bounds__(kThreads) tile_ranges(WsView v, int buf) {
+  pdl_wait();
+  pdl_trigger();
   const int n = v.hdr->n_pairs;
   const uint32_t* keys = v.pkey[buf];
   for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
@@ -381,6 +395,8 @@ __global__ void __launch_bounds__(kThreads) tile_ranges(WsView v, int buf) {
 constexpr int kOrderBuckets = 64;
 
 __global__ void __launch_bounds__(1024) make_items(WsView v) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t warp_tot[33];
   __shared__ uint32_t bucket[kOrderBuckets];
   const int64_t nt = v.n_tiles;
@@ -449,15 +465,19 @@ cudaError_t radix_sort(const WsView& v, uint32_t* keys[2], uint32_t* vals[2], co
   if (blocks == 0) return cudaSuccess;
   for (int shift = 0; shift < bits; shift += RB) {
     uint32_t mask = (uint32_t)((1u << min(RB, bits - shift)) - 1u);
-    radix_upsweep<RB><<<blocks, kThreads, 0, st>>>(keys[buf], n_dev, n_host, shift, mask, v.hist,
-                                                   v.sort_blocks);
-    scan_rows<<<1 << RB, kThreads, 0, st>>>(v.hist, v.radix_tot, n_dev, n_host, v.sort_blocks);
-    radix_downsweep<RB><<<blocks, kThreads, 0, st>>>(keys[buf], vals[buf], keys[buf ^ 1], vals[buf ^ 1],
-                                                     n_dev, n_host, shift, mask, v.hist, v.radix_tot,
-                                                     v.sort_blocks);
+    cudaError_t e = launch_pdl(radix_upsweep<RB>, dim3(blocks), dim3(kThreads), 0, st, keys[buf], n_dev,
+                               n_host, shift, mask, v.hist, v.sort_blocks);
+    if (e == cudaSuccess)
+      e = launch_pdl(scan_rows, dim3(1 << RB), dim3(kThreads), 0, st, v.hist, v.radix_tot, n_dev, n_host,
+                     v.sort_blocks);
+    if (e == cudaSuccess)
+      e = launch_pdl(radix_downsweep<RB>, dim3(blocks), dim3(kThreads), 0, st, keys[buf], vals[buf],
+                     keys[buf ^ 1], vals[buf ^ 1], n_dev, n_host, shift, mask, v.hist, v.radix_tot,
+                     v.sort_blocks);
+    if (e != cudaSuccess) return e;
     buf ^= 1;
   }
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -478,10 +498,11 @@ cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st) {
   // the sorted spheres are in buffer v.sort_buf (the parity of the pass count)
   const int nb = (M + kSortTile - 1) / kSortTile;
   if (nb > 0)
-    count_reduce<<<nb, kThreads, 0, st>>>(v);   // its last CTA scans the sums
+    e = launch_pdl(count_reduce, dim3(nb), dim3(kThreads), 0, st, v);   // its last CTA scans the sums
   else
-    count_scan<<<1, 1024, 0, st>>>(v, 0);
-  if (nb > 0) emit_pairs<<<nb, kThreads, 0, st>>>(v);
+    e = launch_pdl(count_scan, dim3(1), dim3(1024), 0, st, v, 0);
+  if (e == cudaSuccess && nb > 0) e = launch_pdl(emit_pairs, dim3(nb), dim3(kThreads), 0, st, v);
+  if (e != cudaSuccess) return e;
   // 4. pairs by tile
   int pbuf = 0;
   if (v.capacity > 0) {
@@ -496,12 +517,12 @@ cudaError_t launch_bin(const WsView& v, int tile_bits, cudaStream_t st) {
   if (v.capacity > 0) {
     const int64_t want = (v.capacity + kThreads - 1) / kThreads;
     const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
-    tile_ranges<<<blocks, kThreads, 0, st>>>(v, pbuf);
+    e = launch_pdl(tile_ranges, dim3(blocks), dim3(kThreads), 0, st, v, pbuf);
+    if (e != cudaSuccess) return e;
   }
   // 6. work items of the render passes (the merge counters were cleared with the tile counts)
   if (v.n_tiles > 0) {
-    make_items<<<1, 1024, 0, st>>>(v);
-    e = cudaGetLastError();
+    e = launch_pdl(make_items, dim3(1), dim3(1024), 0, st, v);
     if (e != cudaSuccess) return e;
   }
   // 7. per pixel block: the spheres hitting it, with their hit masks
