@@ -29,6 +29,8 @@ __global__ void __launch_bounds__(kLossThreads) loss_partials_kernel(int kind, c
                                                                      const float* __restrict__ target, int64_t n,
                                                                      float scale, float* __restrict__ grad,
                                                                      float* __restrict__ scratch, int vec) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float sh[kLossThreads / 32];
   float acc = 0.0f;
   const int64_t stride = (int64_t)gridDim.x * kLossThreads;
@@ -69,6 +71,8 @@ __global__ void __launch_bounds__(kLossThreads) loss_partials_kernel(int kind, c
 // One CTA: the partials summed in a fixed order (FP64), times scale.
 __global__ void __launch_bounds__(kLossBlocks) loss_total_kernel(const float* __restrict__ scratch, int parts,
                                                                  float scale, float* __restrict__ loss) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[kLossBlocks];
   sh[threadIdx.x] = threadIdx.x < (unsigned)parts ? (double)scratch[threadIdx.x] : 0.0;
   __syncthreads();
@@ -93,6 +97,8 @@ struct AdamPack {
 
 // One thread: t += 1 and the bias-corrected step factors of the new step.
 __global__ void adam_tick_kernel(pulsar_adam_state* st, float lr, float beta1, float beta2) {
+  pdl_wait();
+  pdl_trigger();
   const int t = st->t + 1;
   st->t = t;
   const double bc1 = 1.0 - pow((double)beta1, (double)t);
@@ -105,6 +111,8 @@ __global__ void adam_tick_kernel(pulsar_adam_state* st, float lr, float beta1, f
 // holds b; each thread takes every kAdamThreads-th element of the chunk.
 __global__ void __launch_bounds__(kAdamThreads) adam_update_kernel(const AdamPack pk,
                                                                    const pulsar_adam_state* __restrict__ st) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t b = blockIdx.x;
   int k = 0;
   while (k + 1 < pk.n && pk.block_begin[k + 1] <= b) ++k;
@@ -153,9 +161,11 @@ extern "C" pulsar_status pulsar_image_loss(int kind, const float* image, const f
   const int per_sm = kLossBlocks / (sms > 0 ? sms : 1);   // whole waves of CTAs over the SMs
   const int cap = per_sm > 0 ? per_sm * sms : kLossBlocks;
   const int blocks = (int)(want < cap ? want : cap);
-  loss_partials_kernel<<<blocks, kLossThreads, 0, st>>>(kind, image, target, n, scale, grad, scratch, vec);
-  if (loss) loss_total_kernel<<<1, kLossBlocks, 0, st>>>(scratch, blocks, scale, loss);
-  return cudaGetLastError() == cudaSuccess ? PULSAR_OK : PULSAR_ERR_CUDA;
+  cudaError_t e = launch_pdl(loss_partials_kernel, dim3(blocks), dim3(kLossThreads), 0, st, kind, image, target,
+                             n, scale, grad, scratch, vec);
+  if (e == cudaSuccess && loss)
+    e = launch_pdl(loss_total_kernel, dim3(1), dim3(kLossBlocks), 0, st, (const float*)scratch, blocks, scale, loss);
+  return e == cudaSuccess ? PULSAR_OK : PULSAR_ERR_CUDA;
 }
 
 extern "C" pulsar_status pulsar_adam_step(int n_tensors, const pulsar_adam_tensor* tensors,
@@ -185,7 +195,9 @@ extern "C" pulsar_status pulsar_adam_step(int n_tensors, const pulsar_adam_tenso
   pk.block_begin[n_tensors] = blocks;
   if (blocks > 0x7fffffff) return PULSAR_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  adam_tick_kernel<<<1, 1, 0, st>>>(state, h.lr, h.beta1, h.beta2);
-  if (blocks > 0) adam_update_kernel<<<(unsigned)blocks, kAdamThreads, 0, st>>>(pk, state);
-  return cudaGetLastError() == cudaSuccess ? PULSAR_OK : PULSAR_ERR_CUDA;
+  cudaError_t e = launch_pdl(adam_tick_kernel, dim3(1), dim3(1), 0, st, state, h.lr, h.beta1, h.beta2);
+  if (e == cudaSuccess && blocks > 0)
+    e = launch_pdl(adam_update_kernel, dim3((unsigned)blocks), dim3(kAdamThreads), 0, st, pk,
+                   (const pulsar_adam_state*)state);
+  return e == cudaSuccess ? PULSAR_OK : PULSAR_ERR_CUDA;
 }
