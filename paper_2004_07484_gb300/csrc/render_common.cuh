@@ -409,16 +409,37 @@ __device__ __forceinline__ void queue_init(uint64_t (&q)[KMAX], int K) {
   for (int k = 0; k < KMAX; ++k) q[k] = k < KMAX - K ? 0ull : kEmptyKey;
 }
 
+// Sorted insertion into q[B, B + N); the largest key falls off the end.
+template <int B, int N, int KMAX>
+__device__ __forceinline__ void queue_insert_range(uint64_t (&q)[KMAX], uint64_t key) {
+  bool lt[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) lt[k] = key < q[B + k];
+#pragma unroll
+  for (int k = N - 1; k >= 1; --k) q[B + k] = lt[k - 1] ? q[B + k - 1] : (lt[k] ? key : q[B + k]);
+  q[B] = lt[0] ? key : q[B];
+}
+
 // Sorted insertion; the largest key falls off the end.  Every index is a
-// compile-time constant so the queue stays in registers.
+// compile-time constant so the queue stays in registers.  Queues of 16 and
+// more are two halves: a key enters the lower half only if it is below the
+// lower half's largest entry, which then moves on to the upper half, and the
+// upper half is touched only by a key (or displaced entry) below its largest.
+// While a pixel holds at most half the queue's capacity, the upper half is
+// all empty keys and its network is skipped.
 template <int KMAX>
 __device__ __forceinline__ void queue_insert(uint64_t (&q)[KMAX], uint64_t key) {
-  bool lt[KMAX];
-#pragma unroll
-  for (int k = 0; k < KMAX; ++k) lt[k] = key < q[k];
-#pragma unroll
-  for (int k = KMAX - 1; k >= 1; --k) q[k] = lt[k - 1] ? q[k - 1] : (lt[k] ? key : q[k]);
-  q[0] = lt[0] ? key : q[0];
+  if constexpr (KMAX >= 16) {
+    constexpr int H = KMAX / 2;
+    if (key < q[H - 1]) {
+      const uint64_t up = q[H - 1];
+      queue_insert_range<0, H>(q, key);
+      key = up;
+    }
+    if (key < q[KMAX - 1]) queue_insert_range<H, KMAX - H>(q, key);
+  } else {
+    queue_insert_range<0, KMAX>(q, key);
+  }
 }
 
 // Next float after a positive depth (+inf stays +inf): spheres whose key is
