@@ -21,6 +21,7 @@ import json
 from dataclasses import replace
 import os
 import statistics
+import struct
 import subprocess
 import sys
 import time
@@ -57,6 +58,30 @@ def fwd_kernel_digest() -> str:
         with open(os.path.join(ROOT, "paper_2004_07484_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
+
+
+def kernels_per_step(znear: float, zfar: float, n_tiles: int, recompute: bool) -> int:
+    """Kernels one fwd + bwd step of one scene launches (all gradients, no diagnostics).
+
+    The sort pass counts follow the library's rules: depth keys are float-bit
+    offsets from the near plane, as many bits as zfar's offset needs, sorted in
+    9-bit digits; tile keys take ceil(log2 tiles) bits, in 6-bit digits for 9 to
+    12 bits and 8-bit digits otherwise; every pass is upsweep, row scan and
+    downsweep."""
+    span = struct.unpack("<I", struct.pack("<f", zfar))[0] - struct.unpack("<I", struct.pack("<f", znear))[0]
+    key_bits = 1
+    while key_bits < 32 and (span >> key_bits) != 0:
+        key_bits += 1
+    tile_bits = 1
+    while tile_bits < 32 and (1 << tile_bits) < n_tiles:
+        tile_bits += 1
+    rb = 6 if 8 < tile_bits <= 12 else 8
+    project = 2                                   # set-up, projection
+    binning = (3 * -(-key_bits // 9) + 2          # depth passes, tile counts (+ scan), pair emission
+               + 3 * -(-tile_bits // rb) + 4)     # tile passes, ranges, work items, block lists, unit order
+    forward = 3                                   # set-up, render, background
+    backward = 6 + (1 if recompute else 0)        # set-up, zeroing, render, background, finalize, camera
+    return project + binning + forward + backward   # (+ the track pass when recomputing)
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
@@ -975,13 +1000,9 @@ def main():
                "sample": f"{CPU_WINDOW}x{CPU_WINDOW}-pixel window at the image centre, fwd + bwd, FP64 brute "
                          f"force over all {sc.n_spheres} spheres; the calls' fixed set-up ({setup:.3f} s, "
                          f"an empty window) subtracted"}
-    # kernels per step: project 2 (setup, project); binning 24 (four 8-bit radix
-    # passes of the 32-bit depth keys and two of the 12-bit tile keys, 3 kernels
-    # each, then count, scan, emit, ranges, items, block lists); forward 3
-    # (setup, render, background); backward 7 (setup, zeroing, render,
-    # background, finalize, camera partials, camera reduce); plus the track pass
-    # in recompute mode
-    launches_store, launches_rec = 36, 37
+    n_tiles = -(-W // 16) * -(-H // 16)
+    launches_store = kernels_per_step(sc.znear, sc.zfar, n_tiles, False)
+    launches_rec = kernels_per_step(sc.znear, sc.zfar, n_tiles, True)
     line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step,
             "ms_per_step_median": ms_sorted[len(ms_sorted) // 2], "ms_per_step_max": ms_sorted[-1], "higher_is_better": True, "scaling": "weak",

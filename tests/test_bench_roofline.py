@@ -37,3 +37,12 @@ def test_step_roofline_is_the_sum_of_stage_bounds():
     # binning is the depth sort and the pair stages together
     b = w["depth sort"][0] + w["binning"][0]
     assert r["per_call"]["pulsar_bin"]["hbm_frac"] == pytest.approx(b / 0.320e-3 / bw)
+
+
+def test_kernels_per_step_matches_the_launch_list():
+    # depths in [1, 20]: 26-bit offset keys, three 9-bit passes; 4,096 tiles:
+    # 12-bit tile keys, two 6-bit passes (the launch list of one step shows 32 kernels)
+    assert bench.kernels_per_step(1.0, 20.0, 4096, False) == 2 + (9 + 2 + 6 + 4) + 3 + 6 == 32
+    assert bench.kernels_per_step(1.0, 20.0, 4096, True) == 33
+    # 256 tiles: one 8-bit tile pass
+    assert bench.kernels_per_step(1.0, 20.0, 256, False) == 32 - 3
