@@ -60,8 +60,8 @@ def fwd_kernel_digest() -> str:
     return h.hexdigest()
 
 
-def kernels_per_step(znear: float, zfar: float, n_tiles: int, recompute: bool) -> int:
-    """Kernels one fwd + bwd step of one scene launches (all gradients, no diagnostics).
+def binning_kernels(znear: float, zfar: float, n_tiles: int) -> int:
+    """Kernels one binning call launches (one scene, or a batch with these planes and tiles).
 
     The sort pass counts follow the library's rules: depth keys are float-bit
     offsets from the near plane, as many bits as zfar's offset needs, sorted in
@@ -76,12 +76,16 @@ def kernels_per_step(znear: float, zfar: float, n_tiles: int, recompute: bool) -
     while tile_bits < 32 and (1 << tile_bits) < n_tiles:
         tile_bits += 1
     rb = 6 if 8 < tile_bits <= 12 else 8
+    return (3 * -(-key_bits // 9) + 2          # depth passes, tile counts (+ scan), pair emission
+            + 3 * -(-tile_bits // rb) + 4)     # tile passes, ranges, work items, block lists, unit order
+
+
+def kernels_per_step(znear: float, zfar: float, n_tiles: int, recompute: bool) -> int:
+    """Kernels one fwd + bwd step of one scene launches (all gradients, no diagnostics)."""
     project = 2                                   # set-up, projection
-    binning = (3 * -(-key_bits // 9) + 2          # depth passes, tile counts (+ scan), pair emission
-               + 3 * -(-tile_bits // rb) + 4)     # tile passes, ranges, work items, block lists, unit order
     forward = 3                                   # set-up, render, background
     backward = 6 + (1 if recompute else 0)        # set-up, zeroing, render, background, finalize, camera
-    return project + binning + forward + backward   # (+ the track pass when recomputing)
+    return project + binning_kernels(znear, zfar, n_tiles) + forward + backward   # (+ track pass)
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
@@ -574,7 +578,13 @@ FIT_METRIC = "scene-fit steps/sec (4 views fwd+bwd + Adam) at 5M spheres 1920x10
 FIT_WORKLOAD = ("scene fit: 5M spheres on 20 ellipsoid surfaces (hidden scene), 1920x1080, C=3 U[0,1], "
                 "gamma=1e-2, n_track=8, 4 views at random rotations about the centroid (distance 8), "
                 "start = hidden + N(0, 0.05^2) positions and radii x U[0.7, 1.3], Adam lr 1e-3, L2 loss")
-FIT_LAUNCHES_PER_STEP = 37   # render 29 (project 2, binning 24, forward 3), loss 2, backward 4, Adam 2
+
+
+def fit_kernels_per_step(znear: float, zfar: float, n_tiles: int) -> int:
+    """Kernels of one scene-fit step: the batched render (project 2, binning, forward 3), the
+    image loss 2, the accumulating backward without camera or background gradients (set-up,
+    zeroing, render, finalize) and Adam 2."""
+    return 2 + binning_kernels(znear, zfar, n_tiles) + 3 + 2 + 4 + 2
 
 
 def bench_fit(args):
@@ -716,7 +726,8 @@ def bench_fit(args):
                     "how": "start parameters and targets copied in from pinned host memory once (counted per "
                            "step), then eager ViewFit.step() calls, each loss read back to the host",
                     "final_l2_eager": float(vf.evaluate().item()), "first_loss": losses[0]},
-            "cpu_baseline": cpu, "clocks": clk.summary(), "gpu_launches": FIT_LAUNCHES_PER_STEP * args.steps}
+            "cpu_baseline": cpu, "clocks": clk.summary(), "gpu_launches": fit_kernels_per_step(hidden.znear, hidden.zfar,
+                                                 V * -(-W // 16) * -(-H // 16)) * args.steps}
     print(json.dumps(line))
     if world > 1:
         dist.barrier()

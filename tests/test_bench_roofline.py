@@ -46,3 +46,9 @@ def test_kernels_per_step_matches_the_launch_list():
     assert bench.kernels_per_step(1.0, 20.0, 4096, True) == 33
     # 256 tiles: one 8-bit tile pass
     assert bench.kernels_per_step(1.0, 20.0, 256, False) == 32 - 3
+
+
+def test_fit_kernels_per_step():
+    # 4 views of 1920x1080: 32,640 tiles, 15-bit tile keys in two 8-bit passes; depths in [1, 20]
+    assert bench.binning_kernels(1.0, 20.0, 4 * 120 * 68) == 9 + 2 + 6 + 4
+    assert bench.fit_kernels_per_step(1.0, 20.0, 4 * 120 * 68) == 2 + 21 + 3 + 2 + 4 + 2 == 34

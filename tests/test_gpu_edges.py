@@ -122,16 +122,20 @@ def test_decisions_are_deterministic(orc):
     assert np.array_equal(ia[:n], ib[:n])
 
 
-def test_repeated_calls_on_one_workspace(orc):
-    """Binning twice after one projection, and two backward passes of one
-    forward pass, give the single calls' results: the counters the kernels'
-    last CTAs use to finish a scan or a reduction are ready again after each
-    call.  (The single calls' parity with the oracle is tested elsewhere.)"""
+@pytest.mark.parametrize("store,persistent", [(True, False), (True, True), (False, True)])
+def test_repeated_calls_on_one_workspace(orc, store, persistent):
+    """Binning twice after one projection, a second forward pass, and two
+    backward passes of one forward pass give the single calls' results: the
+    counters the kernels' last CTAs use to finish a scan or a reduction, and
+    the work counter a persistent launch resets itself (shared, in recompute
+    mode, by the track pass and the backward render of one call), are ready
+    again after each call.  (The single calls' parity with the oracle is
+    tested elsewhere.)"""
     import torch
     from paper_2004_07484_gb300 import _lib
     from paper_2004_07484_gb300.renderer import scene_args
     sc = S.config_scene(1, n=20000, res=128)
-    gpu = gpu_forward(sc)
+    gpu = gpu_forward(sc, store=store, persistent=persistent, segment=256)
     fr, d = gpu["frame"], gpu["dev"]
     ranges0, ids0 = gpu_tile_lists(fr)
     stream = torch.cuda.current_stream().cuda_stream
@@ -154,6 +158,7 @@ def test_repeated_calls_on_one_workspace(orc):
         if g1[k] is None:
             continue
         scale = max(np.abs(g1[k]).max(), 1e-30)
+        assert scale > 1e-30, k   # a launch that found its work counter spent would leave zeros
         assert np.abs(g1[k] - g2[k]).max() <= 1e-5 * scale, k   # float atomics may add in another order
 
 
