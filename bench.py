@@ -526,16 +526,18 @@ def bench_shading(dev, sc, t, tuned, capacity: int, steps: int, warmup: int, flu
     k = max(3, min(steps, 10))
 
     def timed(fn):
-        ms = []
+        # events around each step and no host synchronisation between steps, as in the
+        # headline loop: the host enqueues ahead of the GPU as a training loop does
+        ev = []
         for i in range(k):
             flush.fill_(i & 0xff)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn()
             e1.record(stream)
-            torch.cuda.synchronize(dev)
-            ms.append(e0.elapsed_time(e1))
-        return statistics.median(ms)
+            ev.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        return statistics.median(a.elapsed_time(b) for a, b in ev)
 
     out = {"workload": "render -> conv 3x3 " + f"{C}->32->32->3 (ReLU, FP32, TF32 off) -> mean L2 to zero -> "
                        "loss.backward() through the renderer's torch.autograd.Function",

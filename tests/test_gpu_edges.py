@@ -154,11 +154,14 @@ def test_repeated_calls_on_one_workspace(orc, store, persistent):
     G = S.grad_image(12, sc.height, sc.width, sc.n_channels)
     g1 = gpu_backward(gpu, G)
     g2 = gpu_backward(gpu, G)
+    # every tracked hit adds to its sphere's feature gradient: a backward launch that found its
+    # work counter spent would leave them zero (radius gradients can be zero throughout here:
+    # spheres enlarged to the minimum projected size have none)
+    assert np.abs(g1["feat"]).max() > 0 and np.abs(g2["feat"]).max() > 0
     for k in g1:
         if g1[k] is None:
             continue
         scale = max(np.abs(g1[k]).max(), 1e-30)
-        assert scale > 1e-30, k   # a launch that found its work counter spent would leave zeros
         assert np.abs(g1[k] - g2[k]).max() <= 1e-5 * scale, k   # float atomics may add in another order
 
 
